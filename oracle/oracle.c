@@ -1,0 +1,213 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU oracle for the receive beamformer of
+ * SUPRA (Goebl, Navab, Hennersperger, "SUPRA: Open Source Software Defined
+ * Ultrasound Processing for Real-Time Applications", arXiv:1711.06127).
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py load this library.  It shares no source,
+ * header, table or helper with the CUDA path, and nothing here is reachable
+ * from the product library.
+ *
+ * The paper names the steps of the pipeline (Sec. 1, step list "receive
+ * beamforming", Sec. 2 method list items 1-2: dynamic receive beamforming for
+ * a flexible scanline layout and multi-line acquisitions, delay-and-sum of raw
+ * channel data after A/D conversion, citing Shattuck et al. 1984) but prints no
+ * formula.  What follows is the textbook delay-and-sum written out directly:
+ *
+ *   For scanline l (origin o_l, unit direction d_l, transmit event t = line_tx[l]
+ *   with transmit origin o_t) and depth r_i = depth0 + i*depth_step, the image
+ *   point is p = o_l + r_i d_l.  Element e at x_e receives the echo of p after
+ *       tau_e = (|p - o_t| + |p - x_e|) / c - t0          (two-way path)
+ *   which is channel sample s = tau_e * fs, read by linear interpolation
+ *   between floor(s) and floor(s)+1 (samples outside [0, n_s-1] read as 0).
+ *   Dynamic aperture (F-number): centre q = (p_x, p_y) clamped to the array's
+ *   extent, half width a = max(p_z / (2F), min_half_aperture); e is active iff
+ *   |x_e - q| <= a on each lateral axis.  Apodization is the product over the
+ *   two lateral axes of the window evaluated at u = (x_e - q)/a.
+ *       RF(l, i) = sum_active w_e v_e / sum_active w_e      (0 if sum w = 0)
+ *
+ * Readings taken where the paper is silent: spherical transmit delay from the
+ * transmit origin, normalisation by the weight sum, linear interpolation, a
+ * separable square aperture, zero padding outside the record.
+ *
+ * The minimum-variance (Capon) beamformer below is not in the paper; it is the
+ * textbook spatially smoothed MV estimator with diagonal loading.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_WINDOW_RECT 0
+#define OR_WINDOW_HANN 1
+#define OR_WINDOW_HAMMING 2
+
+typedef struct {
+    int32_t n_el;
+    const double *elem;        /* [n_el][3] element positions, metres         */
+    int32_t n_tx;
+    const double *tx_origin;   /* [n_tx][3]                                   */
+    int32_t n_lines;
+    const double *line_origin; /* [n_lines][3]                                */
+    const double *line_dir;    /* [n_lines][3], unit vectors                  */
+    const int32_t *line_tx;    /* [n_lines] transmit event of each line       */
+    int32_t n_depth;
+    double depth0, depth_step; /* r_i = depth0 + i * depth_step               */
+    double c, fs, t0;          /* speed of sound, sampling rate, record start */
+    double fnumber, min_half_aperture;
+    int32_t window;            /* OR_WINDOW_*                                 */
+    int32_t n_s;               /* samples per channel                         */
+} or_geom;
+
+static double dist3(const double *a, const double *b)
+{
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+/* apodization window on u in [-1, 1] (u = 0 at the aperture centre) */
+static double window_at(int window, double u)
+{
+    const double pi = 3.14159265358979323846;
+    if (window == OR_WINDOW_HANN) return 0.5 * (1.0 + cos(pi * u));
+    if (window == OR_WINDOW_HAMMING) return 0.54 + 0.46 * cos(pi * u);
+    return 1.0;
+}
+
+/* channel sample j of one element's record; zero outside the record */
+static double sample_at(const int16_t *rec, int32_t n_s, long j)
+{
+    if (j < 0 || j >= n_s) return 0.0;
+    return (double)rec[j];
+}
+
+static void array_extent(const or_geom *g, double ext[4])
+{
+    ext[0] = ext[2] = INFINITY;
+    ext[1] = ext[3] = -INFINITY;
+    for (int e = 0; e < g->n_el; ++e) {
+        const double *x = g->elem + 3 * e;
+        if (x[0] < ext[0]) ext[0] = x[0];
+        if (x[0] > ext[1]) ext[1] = x[0];
+        if (x[1] < ext[2]) ext[2] = x[1];
+        if (x[1] > ext[3]) ext[3] = x[1];
+    }
+}
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/*
+ * The image point, aperture centre and aperture half width of (line, i).
+ */
+static void point_and_aperture(const or_geom *g, const double ext[4], int32_t line, int32_t i,
+                               double p[3], double q[2], double *a)
+{
+    const double *o = g->line_origin + 3 * line;
+    const double *d = g->line_dir + 3 * line;
+    double r = g->depth0 + (double)i * g->depth_step;
+    for (int k = 0; k < 3; ++k) p[k] = o[k] + r * d[k];
+    q[0] = clampd(p[0], ext[0], ext[1]);
+    q[1] = clampd(p[1], ext[2], ext[3]);
+    double a_f = p[2] / (2.0 * g->fnumber);
+    *a = a_f > g->min_half_aperture ? a_f : g->min_half_aperture;
+}
+
+/* delay-and-sum value at (line, depth index i); ch_tx = records of the line's
+ * transmit event, [n_el][n_s] */
+static double das_point(const or_geom *g, const double ext[4], const int16_t *ch_tx,
+                        int32_t line, int32_t i)
+{
+    double p[3], q[2], a;
+    point_and_aperture(g, ext, line, i, p, q, &a);
+    const double *o_t = g->tx_origin + 3 * g->line_tx[line];
+    double tx_path = dist3(p, o_t);
+    double num = 0.0, den = 0.0;
+    for (int e = 0; e < g->n_el; ++e) {
+        const double *x = g->elem + 3 * e;
+        double ux = (x[0] - q[0]) / a, uy = (x[1] - q[1]) / a;
+        if (fabs(ux) > 1.0 || fabs(uy) > 1.0) continue;     /* outside the aperture */
+        double w = window_at(g->window, ux) * window_at(g->window, uy);
+        double tau = (tx_path + dist3(p, x)) / g->c - g->t0;
+        double s = tau * g->fs;
+        double k = floor(s);
+        double phi = s - k;
+        const int16_t *rec = ch_tx + (long)e * g->n_s;
+        double v = (1.0 - phi) * sample_at(rec, g->n_s, (long)k) + phi * sample_at(rec, g->n_s, (long)k + 1);
+        num += w * v;
+        den += w;
+    }
+    return den > 0.0 ? num / den : 0.0;
+}
+
+/* Whole frame: ch [n_tx][n_el][n_s] -> rf [n_lines][n_depth]. */
+void oracle_das(const or_geom *g, const int16_t *ch, double *rf)
+{
+    double ext[4];
+    array_extent(g, ext);
+    long rec_tx = (long)g->n_el * g->n_s;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t l = 0; l < g->n_lines; ++l) {
+        const int16_t *ch_tx = ch + rec_tx * g->line_tx[l];
+        for (int32_t i = 0; i < g->n_depth; ++i)
+            rf[(long)l * g->n_depth + i] = das_point(g, ext, ch_tx, l, i);
+    }
+}
+
+/* Selected points only: point k is (lines[k], depths[k]); its transmit
+ * event's records are at ch_tx[k] ([n_el][n_s]).  Used for sampled checks of
+ * frames too large for a full CPU pass. */
+void oracle_das_points(const or_geom *g, int32_t n_pts, const int32_t *lines, const int32_t *depths,
+                       const int16_t *const *ch_tx, double *out)
+{
+    double ext[4];
+    array_extent(g, ext);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int32_t k = 0; k < n_pts; ++k)
+        out[k] = das_point(g, ext, ch_tx[k], lines[k], depths[k]);
+}
+
+/* The aperture of (line, i): active-element mask and weights (diagnostics for
+ * tests: weight sums, element counts, distance of each element to the aperture
+ * edge).  mask[e] = 1 if active; w[e] = window weight (0 if inactive);
+ * margin[e] = a - max(|x_e - q|) in metres (negative = outside). */
+void oracle_aperture(const or_geom *g, int32_t line, int32_t i, int32_t *mask, double *w, double *margin)
+{
+    double ext[4], p[3], q[2], a;
+    array_extent(g, ext);
+    point_and_aperture(g, ext, line, i, p, q, &a);
+    for (int e = 0; e < g->n_el; ++e) {
+        const double *x = g->elem + 3 * e;
+        double ux = (x[0] - q[0]) / a, uy = (x[1] - q[1]) / a;
+        double m = fabs(x[0] - q[0]) > fabs(x[1] - q[1]) ? fabs(x[0] - q[0]) : fabs(x[1] - q[1]);
+        margin[e] = a - m;
+        int on = !(fabs(ux) > 1.0 || fabs(uy) > 1.0);
+        mask[e] = on;
+        w[e] = on ? window_at(g->window, ux) * window_at(g->window, uy) : 0.0;
+    }
+}
+
+/* Delayed, interpolated samples of the active elements at (line, i), in
+ * element order; returns the count.  x[] must hold n_el values.  This is the
+ * vector the minimum-variance beamformer and the apodization network consume. */
+int32_t oracle_delayed_samples(const or_geom *g, const int16_t *ch_tx, int32_t line, int32_t i, double *x,
+                               int32_t *elems)
+{
+    double ext[4], p[3], q[2], a;
+    array_extent(g, ext);
+    point_and_aperture(g, ext, line, i, p, q, &a);
+    const double *o_t = g->tx_origin + 3 * g->line_tx[line];
+    double tx_path = dist3(p, o_t);
+    int32_t m = 0;
+    for (int e = 0; e < g->n_el; ++e) {
+        const double *xe = g->elem + 3 * e;
+        double ux = (xe[0] - q[0]) / a, uy = (xe[1] - q[1]) / a;
+        if (fabs(ux) > 1.0 || fabs(uy) > 1.0) continue;
+        double s = ((tx_path + dist3(p, xe)) / g->c - g->t0) * g->fs;
+        double k = floor(s), phi = s - k;
+        const int16_t *rec = ch_tx + (long)e * g->n_s;
+        x[m] = (1.0 - phi) * sample_at(rec, g->n_s, (long)k) + phi * sample_at(rec, g->n_s, (long)k + 1);
+        if (elems) elems[m] = e;
+        ++m;
+    }
+    return m;
+}
