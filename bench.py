@@ -1,0 +1,365 @@
+"""Benchmark of the fused B-mode chain on one B300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the 2D full pipeline -- 128-element linear array, 256 scanlines,
+2048 int16 samples per channel, DAS -> IQ envelope -> 60 dB log compression ->
+scan conversion to 512x512 -- on a batch of 64 seeded synthetic phantom frames
+per step (one batched launch per stage).  A step reads 64 x 128 MiB of channel
+data, far larger than L2, so no flush is needed between steps.
+
+Metric: beamformed samples*channels per second (n_tx * n_el * n_samples per
+frame, all frames of all ranks) with frames/s and the p50/p99 step latency
+(frames of a batch complete together).  One JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle of the same chain (the only
+reference this repository has) on the host cores, one full frame per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "beamformed samples·channels/s and frames/s (2D and 3D); p50/p99 frame latency"
+UNIT = "samples*channels/s"
+BATCH = 64
+SEED0 = 1000
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons through NVML while active."""
+
+    REASONS = {
+        "gpu_idle": 0x1, "applications_clocks_setting": 0x2, "sw_power_cap": 0x4, "hw_slowdown": 0x8,
+        "sync_boost": 0x10, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+        "hw_power_brake_slowdown": 0x80, "display_clock_setting": 0x100,
+    }
+
+    def __init__(self, device_index=0, period=0.005):
+        self.period = period
+        self.samples = []
+        self.reasons = 0
+        self.max_mhz = None
+        self.ok = False
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            import torch
+
+            handle = None
+            try:
+                props = torch.cuda.get_device_properties(device_index)
+                bus = "%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+                handle = pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+            except Exception:
+                handle = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.nv = pynvml
+            self.h = handle
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(handle, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception as e:  # no NVML: report no clocks
+            self.err = str(e)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                self.reasons |= int(self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self._stop = threading.Event()
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0}
+        names = [k for k, v in self.REASONS.items() if self.reasons & v and k != "gpu_idle"]
+        return {"sm_mhz": float(statistics.median(self.samples)), "sm_max_mhz": self.max_mhz, "reasons": names,
+                "samples": len(self.samples)}
+
+
+def kernel_traffic():
+    """DRAM traffic per launch of the beamforming kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "das_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1711_06127_b300", "csrc", "das_kernel.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec.get("bytes_per_launch_full_workload")
+
+
+def workload():
+    import phantom
+
+    s = phantom.config2()
+    return s
+
+
+def cpu_oracle_rate(s, chs_host, budget_s=12.0, max_frames=None):
+    """Times the FP64 oracle's whole chain on whole frames until budget_s."""
+    import oracle
+
+    p = s.params()
+    per_frame = s.n_tx * s.n_el * s.n_samples
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.bmode(p, chs_host[done % len(chs_host)])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_frames and done >= max_frames):
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": per_frame * done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done} whole frame(s) of the 128-element/256-line/2048-sample workload through the "
+                      f"FP64 oracle chain (DAS in C/OpenMP, envelope/log/scan conversion in numpy), {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import phantom
+    import torch
+
+    s = workload()
+    chs = [phantom.synth_channels(s, phantom.default_phantom(s, SEED0), SEED0).numpy()]
+    import oracle
+
+    p = s.params()
+    for _ in range(args.warmup):
+        oracle.bmode(p, chs[0])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bmode(p, chs[0])
+        times.append(time.perf_counter() - t0)
+    per_frame = s.n_tx * s.n_el * s.n_samples
+    total = sum(times)
+    value = per_frame * len(times) / total
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": s.name, "frames_per_step": 1, "note": "one whole frame per step on the host cores"},
+        "frames_per_s": len(times) / total,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "one whole frame per step of the same workload through the FP64 oracle chain"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1711_06127_b300 import build
+
+    build.build()
+    import paper_1711_06127_b300 as supra
+    import phantom
+
+    s = workload()
+    p = s.params()
+    plan = supra.Plan(**p)
+    p_lines = dict(p, grid=None)
+    plan_lines = supra.Plan(**p_lines)          # same beamforming kernel, log-compressed lines out
+    info = plan.info
+    # synthetic frames: distinct seeds per rank
+    seeds = [SEED0 + rank * BATCH + k for k in range(BATCH)]
+    chs = [phantom.synth_channels(s, phantom.default_phantom(s, sd), sd, device=dev) for sd in seeds]
+    outs = [torch.empty(plan.out_shape, dtype=torch.uint8, device=dev) for _ in range(BATCH)]
+    lines_out = [torch.empty(plan.line_shape, dtype=torch.uint8, device=dev) for _ in range(BATCH)]
+    ws = torch.empty(max(1, supra.workspace_size([plan] * BATCH)), dtype=torch.uint8, device=dev)
+    plans = [plan] * BATCH
+    stream = torch.cuda.current_stream()
+
+    def step():
+        supra.bmode_batched(plans, chs, outs, ws, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert supra.device_status() == 0
+
+    # ---- timed region: exactly K steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            step()
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    per_frame = s.n_tx * s.n_el * s.n_samples
+    frames = BATCH * args.steps * world
+    value = per_frame * frames / (total_ms * 1e-3)
+
+    # ---- the dominant kernel alone: beamforming + envelope + log compression, same launch shape
+    for _ in range(3):
+        supra.bmode_batched([plan_lines] * BATCH, chs, lines_out, None, stream)
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ke[0].record(stream)
+    for _ in range(args.steps):
+        supra.bmode_batched([plan_lines] * BATCH, chs, lines_out, None, stream)
+    ke[1].record(stream)
+    torch.cuda.synchronize()
+    das_ms = ke[0].elapsed_time(ke[1]) / args.steps
+    alg_bytes = BATCH * (info["aperture_bytes"] + info["bmode_bytes"])
+    peaks, peak_src = measured_peaks()
+    achieved = alg_bytes / (das_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI from pinned host memory
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    host_in = [c.cpu().pin_memory() for c in chs]
+    host_out = [torch.empty(plan.out_shape, dtype=torch.uint8).pin_memory() for _ in range(BATCH)]
+    dev_in = [torch.empty_like(c) for c in chs]
+
+    def e2e_step():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        supra.bmode_batched(plans, dev_in, outs, ws, stream)
+        for o, h in zip(outs, host_out):
+            h.copy_(o, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = per_frame * BATCH * e2e_steps * world / e2e_s
+    h2d = sum(c.numel() * c.element_size() for c in chs)
+    d2h = sum(o.numel() for o in outs)
+    assert supra.device_status() == 0
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_oracle_rate(s, [host_in[0].numpy()], budget_s=args.cpu_budget)
+        srt = sorted(step_ms)
+        p50 = srt[len(srt) // 2]
+        p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i16-in/f32", "data": "synthetic",
+            "config": {"workload": s.name, "frames_per_step": BATCH, "n_el": s.n_el, "n_lines": s.n_lines,
+                       "n_samples": s.n_samples, "grid": "512x512", "parallelism": f"replicas x{world}",
+                       "l2": "inputs 8 GiB per step > L2, no flush"},
+            "frames_per_s": frames / (total_ms * 1e-3),
+            "latency_ms": {"p50": p50, "p99": p99, "note": "per step; the 64 frames of a step complete together"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": kernel_traffic(),
+                         "kernel": "das_kernel<8,1> (beamform + envelope + log)", "kernel_ms": das_ms,
+                         "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
+            "full_array_gbs": BATCH * info["channel_bytes"] / (das_ms * 1e-3) / 1e9,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

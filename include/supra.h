@@ -1,0 +1,227 @@
+/*
+ * supra.h -- C ABI of a B300-native (sm_103a) implementation of the real-time
+ * processing chain of SUPRA (Goebl, Navab, Hennersperger, arXiv:1711.06127):
+ * receive delay-and-sum beamforming of raw channel data, IQ demodulation and
+ * envelope detection, log compression and 2D/3D scan conversion.
+ *
+ * Paper passages:
+ *   Sec. 1, pipeline step list: receive beamforming -> RF, envelope detection,
+ *       log-compression, scan conversion of lines that need not be parallel.
+ *   Sec. 2, method list items 1-5: dynamic receive beamforming for a flexible
+ *       scanline layout and multi-line acquisition; delay-and-sum of raw
+ *       channel data after A/D conversion; envelope detection by IQ
+ *       demodulation; log compression to a target dynamic range; scan
+ *       conversion in 2D and 3D.
+ *   Sec. 2: transmit parameters are computed once for a fixed acquisition --
+ *       here supra_plan_create builds every geometry-dependent table once.
+ *   Table 1: the four nodes Beamformer / Envelope / Log comp. / Scan conv.
+ *       -- one entry point each, plus the fused chain supra_bmode.
+ *
+ * Units: metres, seconds, Hz.  Probe frame: the array lies in the z = 0 plane,
+ * x lateral, y elevation, z depth.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (SUPRA_OK) or a negative SUPRA_E* code; nothing is thrown.
+ *   - Data pointers passed to compute entry points are caller-owned DEVICE
+ *     pointers of the current CUDA device; `stream` is a cudaStream_t (NULL =
+ *     legacy default stream).  Calls are asynchronous and stream-ordered; a
+ *     SUPRA_ECUDA return reports a launch error seen at call time only.
+ *   - Host arrays passed to supra_plan_create are copied; the caller may free
+ *     them when it returns.
+ *   - A plan is immutable after creation and may be used concurrently from
+ *     several host threads and streams.
+ *   - Device-side failures (a bounded wait that ran out, a staging window
+ *     overflow) set a device status word read by supra_device_status().
+ */
+#ifndef SUPRA_H
+#define SUPRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SUPRA_API __attribute__((visibility("default")))
+#else
+#define SUPRA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define SUPRA_OK 0
+#define SUPRA_EINVAL (-1)      /* bad argument, shape or parameter range         */
+#define SUPRA_ENOMEM (-2)      /* device or host allocation failed               */
+#define SUPRA_ECUDA (-3)       /* CUDA runtime error at call time                */
+#define SUPRA_ETIMEOUT (-4)    /* a bounded device-side wait ran out             */
+#define SUPRA_EINTERNAL (-5)   /* internal consistency check failed              */
+#define SUPRA_EWORKSPACE (-6)  /* workspace missing, misaligned or too small     */
+
+/* ---- apodization windows (evaluated at u = offset / half-aperture in [-1,1]) */
+#define SUPRA_WINDOW_RECT 0    /* 1                                              */
+#define SUPRA_WINDOW_HANN 1    /* (1 + cos(pi u)) / 2                            */
+#define SUPRA_WINDOW_HAMMING 2 /* 0.54 + 0.46 cos(pi u)                          */
+
+/* ---- scanline layouts known to scan conversion ---------------------------- */
+#define SUPRA_GEOM_LINEAR 0    /* parallel lines along +z from evenly spaced x on z = 0            */
+#define SUPRA_GEOM_SECTOR 1    /* lines in the xz plane from one apex at evenly spaced angles       */
+#define SUPRA_GEOM_PYRAMID 2   /* lines from one apex along normalize(tan tx, tan ty, 1), tx and ty
+                                  evenly spaced; line index = iy * lines_x + ix                     */
+
+/* Probe: element positions, [n_el][3] doubles (host). */
+typedef struct supra_probe {
+    int32_t n_el;
+    const double *elem_pos;
+} supra_probe;
+
+/* Transmit/receive scan geometry (Sec. 2 item 1: fully flexible scanline
+ * layout; multi-line acquisition = several lines sharing a transmit event). */
+typedef struct supra_scan {
+    int32_t n_tx;               /* transmit events per frame                          */
+    const double *tx_origin;    /* [n_tx][3] origin of each transmit wave             */
+    int32_t n_lines;            /* reconstructed scanlines                            */
+    const double *line_origin;  /* [n_lines][3]                                       */
+    const double *line_dir;     /* [n_lines][3] unit direction                        */
+    const int32_t *line_tx;     /* [n_lines] transmit event each line is formed from  */
+    int32_t n_depth;            /* samples per line: r_i = depth0 + i * depth_step    */
+    double depth0, depth_step;
+    int32_t geometry;           /* SUPRA_GEOM_* (used by scan conversion)             */
+    int32_t lines_x, lines_y;   /* line layout; lines_y = 1 for 2D                    */
+} supra_scan;
+
+/* Receive parameters (Sec. 2 item 2; dynamic aperture by F-number). */
+typedef struct supra_rx {
+    double c;                   /* speed of sound                                      */
+    double fs;                  /* sampling rate of the channel records                */
+    double fc;                  /* centre (demodulation) frequency                     */
+    double fnumber;             /* aperture half width = max(z / (2 F), min_half_aperture) */
+    double min_half_aperture;
+    int32_t window;             /* SUPRA_WINDOW_*                                      */
+    int32_t n_samples;          /* samples per channel record                          */
+    double t0;                  /* time of channel sample 0 after transmit             */
+} supra_rx;
+
+/* Post-processing (Sec. 2 items 3-4). */
+typedef struct supra_post {
+    int32_t fir_taps;           /* odd, 1..127: IQ low-pass length                     */
+    double fir_cutoff;          /* Hz (Blackman windowed sinc, unit DC gain)           */
+    double dyn_range_db;        /* D: displayed dynamic range                          */
+    double log_ref;             /* envelope value mapped to 0 dB (gray level 255)      */
+} supra_post;
+
+/* Cartesian output grid of scan conversion: point (ix, iy, iz) lies at
+ * origin + (ix, iy, iz) * spacing; the image is stored [nz][ny][nx] (x
+ * fastest) as uint8.  ny = 1 for 2D. */
+typedef struct supra_grid {
+    int32_t nx, ny, nz;
+    double origin[3];
+    double spacing[3];
+} supra_grid;
+
+typedef struct supra_plan supra_plan;
+
+/* Sizes and algorithmic work of one frame under a plan. */
+typedef struct supra_plan_info {
+    int64_t n_tx, n_el, n_samples, n_lines, n_depth;
+    int64_t channel_bytes;          /* n_tx * n_el * n_samples * 2: the full int16 frame             */
+    int64_t aperture_element_samples; /* sum over (line, depth) of elements inside the aperture     */
+    int64_t aperture_bytes;         /* 2 bytes per in-aperture element-sample                        */
+    int64_t rf_bytes;               /* n_lines * n_depth * 4                                         */
+    int64_t bmode_bytes;            /* n_lines * n_depth (uint8 log-compressed lines)                */
+    int64_t image_bytes;            /* nx * ny * nz, or bmode_bytes without a grid                    */
+    int32_t has_grid;
+    int32_t depth_tile;             /* depth samples per beamforming tile                            */
+} supra_plan_info;
+
+/* Validates every parameter, copies the geometry to the device and builds the
+ * resident tables (element table, per-line constants, per-tile delay bases
+ * and aperture bounds, demodulation taps, log-compression constants,
+ * scan-conversion inverse map).  `grid` may be NULL (no scan conversion: the
+ * B-mode output is then the log-compressed lines [n_lines][n_depth]).
+ * Errors: SUPRA_EINVAL (c, fs, fnumber <= 0; fc >= fs/2; n_* < 1; line_tx
+ * out of range; a non-unit line direction; fir_taps even or > 127;
+ * dyn_range_db <= 0; log_ref <= 0; min_half_aperture <= 0; a scanline layout that does not match
+ * `geometry` when a grid is given), SUPRA_ENOMEM, SUPRA_ECUDA.  Runs on the
+ * current device and is synchronous. */
+SUPRA_API int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const supra_rx *rx,
+                      const supra_post *post, const supra_grid *grid, supra_plan **out);
+
+/* Frees the plan's device tables (synchronous).  NULL is a no-op. */
+SUPRA_API void supra_plan_destroy(supra_plan *plan);
+
+SUPRA_API int supra_plan_get_info(const supra_plan *plan, supra_plan_info *info);
+
+/* Receive delay-and-sum (Sec. 1 "receive beamforming"; Sec. 2 items 1-2;
+ * Table 1 "Beamformer").  For line l and depth sample i the image point is
+ * p = o_l + r_i d_l; element e contributes its record at
+ * s = ((|p - o_t| + |p - x_e|) / c - t0) fs (t = line_tx[l]), linearly
+ * interpolated, zero outside the record; apodized by the window over the
+ * F-number aperture centred on (p_x, p_y) clamped to the array; the sum is
+ * normalised by the sum of weights.
+ *   ch: int16 [n_tx][n_el][n_samples] (device, sample-contiguous)
+ *   rf: float [n_lines][n_depth]      (device)                            */
+SUPRA_API int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *stream);
+
+/* IQ demodulation and envelope (Sec. 1 "envelope detection"; Sec. 2 item 3;
+ * Table 1 "Envelope"): env = 2 |sum_k h_k rf(i + H - k) exp(-j 2 pi fc (i + H - k) dt)|,
+ * h the plan's low-pass, H = (fir_taps - 1) / 2, dt = 2 depth_step / c,
+ * zero padding at both ends of each line.
+ *   rf, env: float [n_lines][n_depth] (device; may not alias)             */
+SUPRA_API int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream);
+
+/* Log compression (Sec. 1 "log-compression"; Sec. 2 item 4; Table 1
+ * "Log comp."): code = floor(255 (20 log10(env / log_ref) + D) / D + 1/2)
+ * clamped to [0, 255]; env <= 0 -> 0.
+ *   env: float [n_lines][n_depth], bm: uint8 [n_lines][n_depth] (device)  */
+SUPRA_API int supra_logcompress(const supra_plan *plan, const float *env, uint8_t *bm, void *stream);
+
+/* Scan conversion (Sec. 1 "scan conversion"; Sec. 2 item 5; Table 1
+ * "Scan conv."): each grid point is mapped back to fractional (line,
+ * depth) coordinates of the plan's layout and bilinearly (2D) or
+ * trilinearly (3D) interpolated from bm, result floor(v + 1/2); points
+ * outside the scanned region (more than 1e-3 index units beyond its edge)
+ * are 0.  Requires a plan with a grid (else SUPRA_EINVAL).
+ *   bm: uint8 [n_lines][n_depth], img: uint8 [nz][ny][nx] (device)        */
+SUPRA_API int supra_scanconvert(const supra_plan *plan, const uint8_t *bm, uint8_t *img, void *stream);
+
+/* Bytes of device workspace the fused chain needs for these n frames (the
+ * log-compressed lines of every frame that is scan converted, 256-byte
+ * aligned each).  0 when no frame has a grid. */
+SUPRA_API size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *plans);
+
+/* Fused chain of one frame: beamforming, envelope and log compression in one
+ * kernel that streams the frame's channel data once, then scan conversion.
+ * Result equals supra_scanconvert(supra_logcompress(supra_envelope(
+ * supra_beamform(ch)))) up to floating-point rounding.
+ *   ch:  int16 [n_tx][n_el][n_samples] (device)
+ *   out: uint8 [nz][ny][nx] with a grid, else uint8 [n_lines][n_depth]
+ *   workspace: device memory of at least supra_bmode_workspace_size(1, &plan)
+ *   bytes, 256-byte aligned (may be NULL when that size is 0).  Calls that
+ *   share a workspace must not overlap on the device.                     */
+SUPRA_API int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *workspace, size_t workspace_bytes,
+                void *stream);
+
+/* Fused chain of n frames in one launch per stage (n >= 1).  Frames may use
+ * different plans (uneven 2D/3D sizes); consecutive frames that share a plan
+ * are beamformed together so their delays and weights are computed once.
+ * plans, ch, out: host arrays of n entries (device data pointers as for
+ * supra_bmode).  workspace: supra_bmode_workspace_size(n, plans) bytes.   */
+SUPRA_API int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t *const *ch, uint8_t *const *out,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* Reads (and, if clear != 0, resets) the device status word of the current
+ * device: 0 = no device-side failure since the last clear, else the
+ * negative SUPRA_E* code of the first failure.  Synchronizes the device. */
+SUPRA_API int supra_device_status(int32_t clear);
+
+/* Static description of a return code. */
+SUPRA_API const char *supra_strerror(int code);
+
+/* Library version string. */
+SUPRA_API const char *supra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUPRA_H */

@@ -1,0 +1,141 @@
+// common.cuh -- device-resident plan record and small PTX wrappers shared by
+// the kernels of libsupra (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "supra.h"
+
+namespace supra {
+
+constexpr int kDepthTile = 128;     // depth samples per beamforming tile (one per thread of a half-CTA)
+constexpr int kThreads = 256;       // threads of the beamforming CTA: 128 depths x 2 element halves
+constexpr int kChunk = 16;          // aperture elements staged per pipeline stage
+constexpr int kMaxTaps = 127;
+constexpr int kMaxGroup = 8;        // frames of one plan beamformed together
+constexpr int kMaxStages = 4;
+
+// Per-line constants (fp32; built from fp64 host geometry).
+struct LineGeo {
+    float ox, oy, oz;   // line origin
+    float dx, dy, dz;   // unit direction
+    float bt, gt;       // transmit path: bt = d.(o_l - o_t), gt = |o_l - o_t|^2
+    int tx;             // transmit event
+    int pad[3];
+};
+
+// Resident plan record (lives in device global memory; kernels read it through a pointer).
+struct DevPlan {
+    // ---- receive geometry
+    int n_el, n_tx, n_lines, n_depth, n_s;
+    int n_tiles;             // ceil(n_depth / kDepthTile)
+    int regular, el_nx, el_ny;   // elements on a row-major nx x ny grid (e = iy * nx + ix)
+    int window;
+    int win_row;             // staged samples per element row (multiple of 8)
+    int bulk_ok;             // n_s % 8 == 0: rows of 16-byte aligned records may be staged with bulk copies
+    float fsc;               // fs / c: samples per metre of path
+    float t0fs;              // t0 * fs: record start in samples
+    float a1;                // two-way delay step per depth sample, in samples
+    float depth0, depth_step;
+    float inv2f, amin;       // 1 / (2 F), minimum half aperture
+    float xmin, xmax, ymin, ymax;
+    const float4 *elem;      // [n_el] (x, y, z, 0)
+    const LineGeo *lines;    // [n_lines]
+    const int *tile_k;       // [n_tiles] integer base of the two-way delay at the tile's first depth
+    const float *tile_f;     // [n_tiles] fractional remainder of that base
+    const short4 *ap_box;    // [n_lines * n_tiles] element box (ix_lo, ix_hi, iy_lo, iy_hi), inclusive
+    // ---- envelope + log compression
+    int taps;                // odd
+    float taps_c[kMaxTaps];  // h_k cos(w (k - H)), demodulation folded into the taps
+    float taps_s[kMaxTaps];  // h_k sin(w (k - H))
+    float log_a, log_b;      // code = log_a * log2(env) + log_b  (includes the +1/2 of rounding)
+    // ---- scan conversion
+    int has_grid, geometry, lines_x, lines_y;
+    int gnx, gny, gnz;
+    float gox, goy, goz, gsx, gsy, gsz;
+    float apx, apy, apz;     // apex (sector / pyramid) or line-origin reference (linear)
+    float u0, du_inv;        // x-axis line coordinate: u = (t - u0) * du_inv (t = x, angle or tan-angle)
+    float w0, dw_inv;        // y-axis line coordinate (pyramid)
+    float v0, dv_inv;        // depth coordinate: v = (r - v0) * dv_inv
+};
+
+// A group of up to kMaxGroup frames beamformed together under one plan.
+struct FrameGroup {
+    const DevPlan *plan;
+    int n;                               // frames in the group
+    int bulk;                            // rows may be staged with bulk async copies (aligned records)
+    int line0;                           // first work item (lines) of this group in the launch
+    const int16_t *ch[kMaxGroup];
+    void *out[kMaxGroup];                // float rf / uint8 bm per frame
+};
+
+constexpr int kMaxGroupsPerLaunch = 96;
+
+struct LaunchGroups {
+    int n_groups;
+    int total_lines;
+    FrameGroup g[kMaxGroupsPerLaunch];
+};
+
+// device status word of this library on each device (first failure code wins);
+// libsupra is one translation unit, so the definition lives here.
+__device__ int g_status = 0;
+
+__device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~budget clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long budget) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > budget) return false;
+    }
+    return true;
+}
+
+// 1D bulk async copy global -> shared (TMA engine), completion counted on bar.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace supra

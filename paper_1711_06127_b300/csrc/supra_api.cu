@@ -1,0 +1,643 @@
+// supra_api.cu -- host side of libsupra: plan creation (the geometry-dependent
+// work SUPRA does "once for a fixed acquisition", Sec. 2), parameter
+// validation, launches of the beamforming / post-processing kernels, and the
+// C ABI declared in include/supra.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "das_kernel.cuh"
+#include "post_kernels.cuh"
+
+using namespace supra;
+
+struct supra_plan {
+    DevPlan host;           // host copy of the device record (pointers are device pointers)
+    DevPlan *dev = nullptr; // device record
+    void *blob = nullptr;   // one device allocation holding every table
+    supra_plan_info info{};
+    int device = 0;
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Blackman windowed-sinc low-pass, unit DC gain (odd length, centred).
+std::vector<double> lowpass_taps(int K, double cutoff_hz, double rate_hz) {
+    std::vector<double> h(K);
+    const double fc = cutoff_hz / rate_hz;
+    double sum = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double mm = k - (K - 1) / 2.0;
+        const double x = 2.0 * fc * mm;
+        const double sinc = (x == 0.0) ? 1.0 : std::sin(kPi * x) / (kPi * x);
+        const double win = K > 1 ? 0.42 - 0.5 * std::cos(2.0 * kPi * k / (K - 1)) + 0.08 * std::cos(4.0 * kPi * k / (K - 1))
+                                 : 1.0;
+        h[k] = 2.0 * fc * sinc * win;
+        sum += h[k];
+    }
+    for (auto &v : h) v /= sum;
+    return h;
+}
+
+struct Regular {
+    bool ok = false;
+    int nx = 0, ny = 0;
+    double x0 = 0, y0 = 0, px = 0, py = 0;
+};
+
+// Detects elements on a row-major grid: e = iy * nx + ix, x = x0 + ix px, y = y0 + iy py.
+Regular detect_regular(int n, const double *p) {
+    Regular r;
+    int nx = 1;
+    while (nx < n && std::fabs(p[3 * nx + 1] - p[1]) <= 1e-12) ++nx;
+    if (n % nx) return r;
+    const int ny = n / nx;
+    const double px = nx > 1 ? p[3] - p[0] : 0.0;
+    const double py = ny > 1 ? p[3 * nx + 1] - p[1] : 0.0;
+    if ((nx > 1 && !(px > 0)) || (ny > 1 && !(py > 0))) return r;
+    const double tol = 1e-9 + 1e-6 * std::max(px, py);
+    for (int e = 0; e < n; ++e) {
+        const int ix = e % nx, iy = e / nx;
+        if (std::fabs(p[3 * e] - (p[0] + ix * px)) > tol || std::fabs(p[3 * e + 1] - (p[1] + iy * py)) > tol) return r;
+    }
+    r.ok = true;
+    r.nx = nx;
+    r.ny = ny;
+    r.x0 = p[0];
+    r.y0 = p[1];
+    r.px = px;
+    r.py = py;
+    return r;
+}
+
+// index range of grid nodes x0 + k p (k in [0, n)) within [lo, hi], widened by `margin` nodes
+void node_range(double lo, double hi, double x0, double p, int n, int margin, int &a, int &b) {
+    if (n == 1 || p <= 0) {
+        a = 0;
+        b = 0;
+        return;
+    }
+    a = (int)std::ceil((lo - x0) / p - 1e-9) - margin;
+    b = (int)std::floor((hi - x0) / p + 1e-9) + margin;
+    a = std::max(a, 0);
+    b = std::min(b, n - 1);
+    if (a > b) {  // nothing inside: keep one node so the box is well formed
+        a = std::min(std::max(a, 0), n - 1);
+        b = a;
+    }
+}
+
+// number of nodes x0 + k p, k in [0, n), with |x - q| <= a
+long long count_nodes(double q, double a, double x0, double p, int n) {
+    if (n == 1 || p <= 0) return std::fabs(x0 - q) <= a ? 1 : 0;
+    long long lo = (long long)std::ceil((q - a - x0) / p);
+    long long hi = (long long)std::floor((q + a - x0) / p);
+    lo = std::max(lo, 0LL);
+    hi = std::min(hi, (long long)n - 1);
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? SUPRA_OK : SUPRA_ECUDA; }
+
+// kernel choice for a frame group size
+int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : 8; }
+
+size_t das_smem_bytes(int G, int mode, int stages, int W, int ring_stride) {
+    size_t head = 64 + kMaxStages * kChunk * sizeof(StageMeta) + (size_t)(G + 1) * kDepthTile * 4 +
+                  (mode == 1 ? ((size_t)G * ring_stride + 2 * kMaxTaps) * 4 : 0);
+    head = (head + 127) & ~size_t(127);
+    return head + (size_t)stages * G * kChunk * W * 2;
+}
+
+template <int G, int MODE>
+int launch_das_t(const LaunchGroups &L, int W, int ring_stride, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int stages = kMaxStages;
+    while (stages > 2 && das_smem_bytes(G, MODE, stages, W, ring_stride) > (size_t)max_optin) --stages;
+    const size_t smem = das_smem_bytes(G, MODE, stages, W, ring_stride);
+    if (smem > (size_t)max_optin) return SUPRA_EINVAL;
+    auto kern = das_kernel<G, MODE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SUPRA_ECUDA;
+    kern<<<L.total_lines, kThreads, smem, st>>>(L, stages, W, ring_stride);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_das(int G, int mode, const LaunchGroups &L, int W, int ring_stride, cudaStream_t st) {
+    if (L.total_lines == 0) return SUPRA_OK;
+    if (mode == 0) {
+        switch (G) {
+            case 1: return launch_das_t<1, 0>(L, W, ring_stride, st);
+            case 2: return launch_das_t<2, 0>(L, W, ring_stride, st);
+            case 4: return launch_das_t<4, 0>(L, W, ring_stride, st);
+            default: return launch_das_t<8, 0>(L, W, ring_stride, st);
+        }
+    }
+    switch (G) {
+        case 1: return launch_das_t<1, 1>(L, W, ring_stride, st);
+        case 2: return launch_das_t<2, 1>(L, W, ring_stride, st);
+        case 4: return launch_das_t<4, 1>(L, W, ring_stride, st);
+        default: return launch_das_t<8, 1>(L, W, ring_stride, st);
+    }
+}
+
+int launch_scan(const ScanLaunch &S, cudaStream_t st) {
+    if (S.n == 0) return SUPRA_OK;
+    // frames are independent along grid.y; about 8 CTAs per SM in total
+    int blocks_x = 1;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks_x = std::max(1, (sms * 8 + S.n - 1) / S.n);
+    dim3 grid(blocks_x, S.n);
+    scanconvert_kernel<<<grid, 256, 0, st>>>(S);
+    return check_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *supra_version(void) { return "supra-b300 0.1 (sm_103a)"; }
+
+const char *supra_strerror(int code) {
+    switch (code) {
+        case SUPRA_OK: return "ok";
+        case SUPRA_EINVAL: return "invalid argument";
+        case SUPRA_ENOMEM: return "out of memory";
+        case SUPRA_ECUDA: return "CUDA runtime error";
+        case SUPRA_ETIMEOUT: return "bounded device wait ran out";
+        case SUPRA_EINTERNAL: return "internal consistency check failed";
+        case SUPRA_EWORKSPACE: return "workspace missing, misaligned or too small";
+        default: return "unknown error";
+    }
+}
+
+int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const supra_rx *rx, const supra_post *post,
+                      const supra_grid *grid, supra_plan **out) {
+    if (!out) return SUPRA_EINVAL;
+    *out = nullptr;
+    if (!probe || !scan || !rx || !post) return SUPRA_EINVAL;
+    const int n_el = probe->n_el, n_tx = scan->n_tx, n_lines = scan->n_lines, n_d = scan->n_depth,
+              n_s = rx->n_samples;
+    if (n_el < 1 || n_tx < 1 || n_lines < 1 || n_d < 1 || n_s < 1) return SUPRA_EINVAL;
+    if (n_el > 65536 || n_d > (1 << 24) || n_s > (1 << 24)) return SUPRA_EINVAL;
+    if (!probe->elem_pos || !scan->tx_origin || !scan->line_origin || !scan->line_dir || !scan->line_tx)
+        return SUPRA_EINVAL;
+    if (!finite_pos(rx->c) || !finite_pos(rx->fs) || !finite_pos(rx->fc) || !(rx->fc < rx->fs / 2) ||
+        !finite_pos(rx->fnumber) || !finite_pos(rx->min_half_aperture) ||
+        !std::isfinite(rx->t0))
+        return SUPRA_EINVAL;
+    if (rx->window < SUPRA_WINDOW_RECT || rx->window > SUPRA_WINDOW_HAMMING) return SUPRA_EINVAL;
+    if (!(scan->depth0 >= 0) || !finite_pos(scan->depth_step) || !std::isfinite(scan->depth0)) return SUPRA_EINVAL;
+    if (post->fir_taps < 1 || post->fir_taps > kMaxTaps || (post->fir_taps % 2) == 0) return SUPRA_EINVAL;
+    if (!finite_pos(post->fir_cutoff) || !finite_pos(post->dyn_range_db) || !finite_pos(post->log_ref))
+        return SUPRA_EINVAL;
+    for (int e = 0; e < 3 * n_el; ++e)
+        if (!std::isfinite(probe->elem_pos[e])) return SUPRA_EINVAL;
+    for (int t = 0; t < 3 * n_tx; ++t)
+        if (!std::isfinite(scan->tx_origin[t])) return SUPRA_EINVAL;
+    for (int l = 0; l < n_lines; ++l) {
+        const double *d = scan->line_dir + 3 * l;
+        const double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!std::isfinite(nn) || std::fabs(nn - 1.0) > 1e-6) return SUPRA_EINVAL;
+        if (scan->line_tx[l] < 0 || scan->line_tx[l] >= n_tx) return SUPRA_EINVAL;
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(scan->line_origin[3 * l + k])) return SUPRA_EINVAL;
+    }
+    const double depth_rate = rx->c / (2.0 * scan->depth_step);   // samples per second of the depth axis
+    if (!(post->fir_cutoff < depth_rate / 2)) return SUPRA_EINVAL;
+
+    // ---- scan conversion layout
+    DevPlan H{};
+    H.has_grid = grid != nullptr;
+    H.geometry = scan->geometry;
+    H.lines_x = scan->lines_x;
+    H.lines_y = scan->lines_y;
+    if (grid) {
+        if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return SUPRA_EINVAL;
+        if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 34)) return SUPRA_EINVAL;
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(grid->origin[k]) || !std::isfinite(grid->spacing[k])) return SUPRA_EINVAL;
+        if (scan->lines_x < 2 || scan->lines_y < 1 || (long long)scan->lines_x * scan->lines_y != n_lines || n_d < 2)
+            return SUPRA_EINVAL;
+        const double *lo = scan->line_origin, *ld = scan->line_dir;
+        const double tol = 1e-6;
+        H.gnx = grid->nx;
+        H.gny = grid->ny;
+        H.gnz = grid->nz;
+        H.gox = (float)grid->origin[0];
+        H.goy = (float)grid->origin[1];
+        H.goz = (float)grid->origin[2];
+        H.gsx = (float)grid->spacing[0];
+        H.gsy = (float)grid->spacing[1];
+        H.gsz = (float)grid->spacing[2];
+        H.v0 = (float)scan->depth0;
+        H.dv_inv = (float)(1.0 / scan->depth_step);
+        if (scan->geometry == SUPRA_GEOM_LINEAR) {
+            if (scan->lines_y != 1) return SUPRA_EINVAL;
+            const double x0 = lo[0], x1 = lo[3 * (n_lines - 1)];
+            const double dx = (x1 - x0) / (n_lines - 1);
+            if (!(dx > 0)) return SUPRA_EINVAL;
+            for (int l = 0; l < n_lines; ++l) {
+                if (std::fabs(lo[3 * l] - (x0 + l * dx)) > tol * (std::fabs(dx) + 1e-6) + 1e-12) return SUPRA_EINVAL;
+                if (std::fabs(lo[3 * l + 1] - lo[1]) > 1e-12 || std::fabs(lo[3 * l + 2] - lo[2]) > 1e-12)
+                    return SUPRA_EINVAL;
+                if (std::fabs(ld[3 * l + 2] - 1.0) > 1e-9) return SUPRA_EINVAL;
+            }
+            H.apx = 0;
+            H.apy = 0;
+            H.apz = (float)lo[2];
+            H.u0 = (float)x0;
+            H.du_inv = (float)(1.0 / dx);
+        } else if (scan->geometry == SUPRA_GEOM_SECTOR) {
+            if (scan->lines_y != 1) return SUPRA_EINVAL;
+            std::vector<double> th(n_lines);
+            for (int l = 0; l < n_lines; ++l) {
+                for (int k = 0; k < 3; ++k)
+                    if (std::fabs(lo[3 * l + k] - lo[k]) > 1e-12) return SUPRA_EINVAL;
+                if (std::fabs(ld[3 * l + 1]) > 1e-9) return SUPRA_EINVAL;
+                th[l] = std::atan2(ld[3 * l], ld[3 * l + 2]);
+            }
+            const double dth = (th[n_lines - 1] - th[0]) / (n_lines - 1);
+            if (!(dth > 0)) return SUPRA_EINVAL;
+            for (int l = 0; l < n_lines; ++l)
+                if (std::fabs(th[l] - (th[0] + l * dth)) > tol * dth) return SUPRA_EINVAL;
+            H.apx = (float)lo[0];
+            H.apy = (float)lo[1];
+            H.apz = (float)lo[2];
+            H.u0 = (float)th[0];
+            H.du_inv = (float)(1.0 / dth);
+        } else if (scan->geometry == SUPRA_GEOM_PYRAMID) {
+            const int nlx = scan->lines_x, nly = scan->lines_y;
+            if (nly < 2) return SUPRA_EINVAL;
+            std::vector<double> tx(nlx), ty(nly);
+            for (int l = 0; l < n_lines; ++l) {
+                for (int k = 0; k < 3; ++k)
+                    if (std::fabs(lo[3 * l + k] - lo[k]) > 1e-12) return SUPRA_EINVAL;
+                if (!(ld[3 * l + 2] > 0)) return SUPRA_EINVAL;
+            }
+            for (int ix = 0; ix < nlx; ++ix) tx[ix] = std::atan(ld[3 * ix] / ld[3 * ix + 2]);
+            for (int iy = 0; iy < nly; ++iy) ty[iy] = std::atan(ld[3 * iy * nlx + 1] / ld[3 * iy * nlx + 2]);
+            const double dtx = (tx[nlx - 1] - tx[0]) / (nlx - 1), dty = (ty[nly - 1] - ty[0]) / (nly - 1);
+            if (!(dtx > 0) || !(dty > 0)) return SUPRA_EINVAL;
+            for (int l = 0; l < n_lines; ++l) {
+                const int ix = l % nlx, iy = l / nlx;
+                const double a = std::atan(ld[3 * l] / ld[3 * l + 2]), b = std::atan(ld[3 * l + 1] / ld[3 * l + 2]);
+                if (std::fabs(a - (tx[0] + ix * dtx)) > tol * dtx || std::fabs(b - (ty[0] + iy * dty)) > tol * dty)
+                    return SUPRA_EINVAL;
+            }
+            H.apx = (float)lo[0];
+            H.apy = (float)lo[1];
+            H.apz = (float)lo[2];
+            H.u0 = (float)tx[0];
+            H.du_inv = (float)(1.0 / dtx);
+            H.w0 = (float)ty[0];
+            H.dw_inv = (float)(1.0 / dty);
+        } else {
+            return SUPRA_EINVAL;
+        }
+    }
+
+    // ---- receive geometry
+    H.n_el = n_el;
+    H.n_tx = n_tx;
+    H.n_lines = n_lines;
+    H.n_depth = n_d;
+    H.n_s = n_s;
+    H.n_tiles = (n_d + kDepthTile - 1) / kDepthTile;
+    H.window = rx->window;
+    H.bulk_ok = (n_s % 8) == 0;
+    const double fsc = rx->fs / rx->c;
+    const double a1 = 2.0 * scan->depth_step * fsc;
+    if (a1 > 16.0) return SUPRA_EINVAL;  // coarser than 16 samples per depth step: no staging window fits
+    H.fsc = (float)fsc;
+    H.a1 = (float)a1;
+    H.t0fs = (float)(rx->t0 * rx->fs);
+    H.depth0 = (float)scan->depth0;
+    H.depth_step = (float)scan->depth_step;
+    H.inv2f = (float)(1.0 / (2.0 * rx->fnumber));
+    H.amin = (float)rx->min_half_aperture;
+    H.win_row = (int)align_up((size_t)std::ceil(a1 * (kDepthTile - 1) + 13.0), 8);
+    double ext[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
+    for (int e = 0; e < n_el; ++e) {
+        ext[0] = std::min(ext[0], probe->elem_pos[3 * e]);
+        ext[1] = std::max(ext[1], probe->elem_pos[3 * e]);
+        ext[2] = std::min(ext[2], probe->elem_pos[3 * e + 1]);
+        ext[3] = std::max(ext[3], probe->elem_pos[3 * e + 1]);
+    }
+    H.xmin = (float)ext[0];
+    H.xmax = (float)ext[1];
+    H.ymin = (float)ext[2];
+    H.ymax = (float)ext[3];
+    const Regular reg = detect_regular(n_el, probe->elem_pos);
+    if (reg.ok && (reg.nx > 32767 || reg.ny > 32767)) return SUPRA_EINVAL;   // element boxes are int16
+    H.regular = reg.ok;
+    H.el_nx = reg.ok ? reg.nx : n_el;
+    H.el_ny = reg.ok ? reg.ny : 1;
+
+    // host tables
+    std::vector<float4> elem(n_el);
+    for (int e = 0; e < n_el; ++e)
+        elem[e] = make_float4((float)probe->elem_pos[3 * e], (float)probe->elem_pos[3 * e + 1],
+                              (float)probe->elem_pos[3 * e + 2], 0.f);
+    std::vector<LineGeo> lines(n_lines);
+    for (int l = 0; l < n_lines; ++l) {
+        const double *o = scan->line_origin + 3 * l, *d = scan->line_dir + 3 * l;
+        const double *ot = scan->tx_origin + 3 * scan->line_tx[l];
+        const double m0 = o[0] - ot[0], m1 = o[1] - ot[1], m2 = o[2] - ot[2];
+        LineGeo g{};
+        g.ox = (float)o[0];
+        g.oy = (float)o[1];
+        g.oz = (float)o[2];
+        g.dx = (float)d[0];
+        g.dy = (float)d[1];
+        g.dz = (float)d[2];
+        g.bt = (float)(d[0] * m0 + d[1] * m1 + d[2] * m2);
+        g.gt = (float)(m0 * m0 + m1 * m1 + m2 * m2);
+        g.tx = scan->line_tx[l];
+        lines[l] = g;
+    }
+    const int NT = H.n_tiles;
+    std::vector<int> tile_k(NT);
+    std::vector<float> tile_f(NT);
+    const double A0 = (2.0 * scan->depth0 / rx->c - rx->t0) * rx->fs;
+    for (int t = 0; t < NT; ++t) {
+        const double v = A0 + a1 * (double)t * kDepthTile;
+        const double k = std::floor(v);
+        tile_k[t] = (int)k;
+        tile_f[t] = (float)(v - k);
+    }
+    // per (line, tile) element box and the count of in-aperture element-samples
+    std::vector<short4> box((size_t)n_lines * NT);
+    long long ap_count = 0;
+    {
+        const double F2 = 2.0 * rx->fnumber;
+        for (int l = 0; l < n_lines; ++l) {
+            const double *o = scan->line_origin + 3 * l, *d = scan->line_dir + 3 * l;
+            for (int t = 0; t < NT; ++t) {
+                int bx0 = 1 << 30, bx1 = -1, by0 = 1 << 30, by1 = -1;
+                for (int i = t * kDepthTile; i < std::min(n_d, (t + 1) * kDepthTile); ++i) {
+                    const double r = scan->depth0 + i * scan->depth_step;
+                    const double p0 = o[0] + r * d[0], p1 = o[1] + r * d[1], p2 = o[2] + r * d[2];
+                    const double qx = std::min(std::max(p0, ext[0]), ext[1]);
+                    const double qy = std::min(std::max(p1, ext[2]), ext[3]);
+                    const double a = std::max(p2 / F2, rx->min_half_aperture);
+                    if (reg.ok) {
+                        int a0, a1i, b0, b1;
+                        node_range(qx - a, qx + a, reg.x0, reg.px, reg.nx, 1, a0, a1i);
+                        node_range(qy - a, qy + a, reg.y0, reg.py, reg.ny, 1, b0, b1);
+                        bx0 = std::min(bx0, a0);
+                        bx1 = std::max(bx1, a1i);
+                        by0 = std::min(by0, b0);
+                        by1 = std::max(by1, b1);
+                        ap_count += count_nodes(qx, a, reg.x0, reg.px, reg.nx) * count_nodes(qy, a, reg.y0, reg.py, reg.ny);
+                    } else {
+                        for (int e = 0; e < n_el; ++e) {
+                            const double *x = probe->elem_pos + 3 * e;
+                            if (std::fabs(x[0] - qx) <= a && std::fabs(x[1] - qy) <= a) ++ap_count;
+                        }
+                    }
+                }
+                if (!reg.ok) {
+                    bx0 = 0;
+                    bx1 = n_el - 1;
+                    by0 = 0;
+                    by1 = 0;
+                }
+                box[(size_t)l * NT + t] = make_short4((short)bx0, (short)bx1, (short)by0, (short)by1);
+            }
+        }
+    }
+    if (!reg.ok && n_el > 32767) return SUPRA_EINVAL;
+
+    // ---- envelope + log compression
+    const int K = post->fir_taps;
+    H.taps = K;
+    {
+        const auto h = lowpass_taps(K, post->fir_cutoff, depth_rate);
+        const double w = 2.0 * kPi * rx->fc / depth_rate;
+        const int Hh = (K - 1) / 2;
+        for (int k = 0; k < K; ++k) {
+            H.taps_c[k] = (float)(h[k] * std::cos(w * (k - Hh)));
+            H.taps_s[k] = (float)(h[k] * std::sin(w * (k - Hh)));
+        }
+        const double D = post->dyn_range_db;
+        H.log_a = (float)(255.0 / D * 20.0 * std::log10(2.0));
+        H.log_b = (float)(255.0 / D * (D - 20.0 * std::log10(post->log_ref)) + 0.5);
+    }
+
+    // ---- device allocation: one blob for all tables
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = align_up(off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_plan = take(sizeof(DevPlan));
+    const size_t o_elem = take(sizeof(float4) * n_el);
+    const size_t o_lines = take(sizeof(LineGeo) * n_lines);
+    const size_t o_tk = take(sizeof(int) * NT);
+    const size_t o_tf = take(sizeof(float) * NT);
+    const size_t o_box = take(sizeof(short4) * box.size());
+    auto *plan = new (std::nothrow) supra_plan();
+    if (!plan) return SUPRA_ENOMEM;
+    cudaGetDevice(&plan->device);
+    if (cudaMalloc(&plan->blob, off) != cudaSuccess) {
+        delete plan;
+        cudaGetLastError();
+        return SUPRA_ENOMEM;
+    }
+    char *b = static_cast<char *>(plan->blob);
+    H.elem = reinterpret_cast<const float4 *>(b + o_elem);
+    H.lines = reinterpret_cast<const LineGeo *>(b + o_lines);
+    H.tile_k = reinterpret_cast<const int *>(b + o_tk);
+    H.tile_f = reinterpret_cast<const float *>(b + o_tf);
+    H.ap_box = reinterpret_cast<const short4 *>(b + o_box);
+    plan->dev = reinterpret_cast<DevPlan *>(b + o_plan);
+    plan->host = H;
+    cudaError_t err = cudaSuccess;
+    err = err ? err : cudaMemcpy(b + o_plan, &H, sizeof(DevPlan), cudaMemcpyHostToDevice);
+    err = err ? err : cudaMemcpy(b + o_elem, elem.data(), sizeof(float4) * n_el, cudaMemcpyHostToDevice);
+    err = err ? err : cudaMemcpy(b + o_lines, lines.data(), sizeof(LineGeo) * n_lines, cudaMemcpyHostToDevice);
+    err = err ? err : cudaMemcpy(b + o_tk, tile_k.data(), sizeof(int) * NT, cudaMemcpyHostToDevice);
+    err = err ? err : cudaMemcpy(b + o_tf, tile_f.data(), sizeof(float) * NT, cudaMemcpyHostToDevice);
+    err = err ? err : cudaMemcpy(b + o_box, box.data(), sizeof(short4) * box.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        cudaFree(plan->blob);
+        delete plan;
+        return SUPRA_ECUDA;
+    }
+    supra_plan_info &I = plan->info;
+    I.n_tx = n_tx;
+    I.n_el = n_el;
+    I.n_samples = n_s;
+    I.n_lines = n_lines;
+    I.n_depth = n_d;
+    I.channel_bytes = 2LL * n_tx * n_el * n_s;
+    I.aperture_element_samples = ap_count;
+    I.aperture_bytes = 2 * ap_count;
+    I.rf_bytes = 4LL * n_lines * n_d;
+    I.bmode_bytes = (long long)n_lines * n_d;
+    I.image_bytes = grid ? (long long)grid->nx * grid->ny * grid->nz : I.bmode_bytes;
+    I.has_grid = grid != nullptr;
+    I.depth_tile = kDepthTile;
+    *out = plan;
+    return SUPRA_OK;
+}
+
+void supra_plan_destroy(supra_plan *plan) {
+    if (!plan) return;
+    if (plan->blob) cudaFree(plan->blob);
+    delete plan;
+}
+
+int supra_plan_get_info(const supra_plan *plan, supra_plan_info *info) {
+    if (!plan || !info) return SUPRA_EINVAL;
+    *info = plan->info;
+    return SUPRA_OK;
+}
+
+int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *stream) {
+    if (!plan || !ch || !rf) return SUPRA_EINVAL;
+    LaunchGroups L{};
+    L.n_groups = 1;
+    L.total_lines = plan->host.n_lines;
+    L.g[0].plan = plan->dev;
+    L.g[0].n = 1;
+    L.g[0].line0 = 0;
+    L.g[0].bulk = plan->host.bulk_ok && (reinterpret_cast<uintptr_t>(ch) & 15) == 0;
+    L.g[0].ch[0] = ch;
+    L.g[0].out[0] = rf;
+    return launch_das(1, 0, L, plan->host.win_row, 0, static_cast<cudaStream_t>(stream));
+}
+
+int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream) {
+    if (!plan || !rf || !env || rf == env) return SUPRA_EINVAL;
+    dim3 grid((plan->host.n_depth + kEnvTile - 1) / kEnvTile, plan->host.n_lines);
+    envelope_kernel<<<grid, kEnvTile, 0, static_cast<cudaStream_t>(stream)>>>(plan->dev, rf, env);
+    return check_cuda(cudaGetLastError());
+}
+
+int supra_logcompress(const supra_plan *plan, const float *env, uint8_t *bm, void *stream) {
+    if (!plan || !env || !bm) return SUPRA_EINVAL;
+    const long long n = (long long)plan->host.n_lines * plan->host.n_depth;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    logcompress_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(plan->dev, env, bm, n);
+    return check_cuda(cudaGetLastError());
+}
+
+int supra_scanconvert(const supra_plan *plan, const uint8_t *bm, uint8_t *img, void *stream) {
+    if (!plan || !bm || !img || !plan->host.has_grid) return SUPRA_EINVAL;
+    ScanLaunch S{};
+    S.n = 1;
+    S.f[0] = ScanFrame{plan->dev, bm, img};
+    return launch_scan(S, static_cast<cudaStream_t>(stream));
+}
+
+size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *plans) {
+    if (n < 1 || !plans) return 0;
+    size_t total = 0;
+    for (int k = 0; k < n; ++k)
+        if (plans[k] && plans[k]->host.has_grid) total += align_up((size_t)plans[k]->info.bmode_bytes, 256);
+    return total;
+}
+
+int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t *const *ch, uint8_t *const *out,
+                        void *workspace, size_t workspace_bytes, void *stream) {
+    if (n < 1 || !plans || !ch || !out) return SUPRA_EINVAL;
+    for (int k = 0; k < n; ++k)
+        if (!plans[k] || !ch[k] || !out[k]) return SUPRA_EINVAL;
+    const size_t need = supra_bmode_workspace_size(n, plans);
+    if (need > 0 && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)))
+        return SUPRA_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // log-compressed lines of scan-converted frames go to the workspace
+    std::vector<uint8_t *> bm(n);
+    {
+        size_t off = 0;
+        for (int k = 0; k < n; ++k) {
+            if (plans[k]->host.has_grid) {
+                bm[k] = static_cast<uint8_t *>(workspace) + off;
+                off += align_up((size_t)plans[k]->info.bmode_bytes, 256);
+            } else {
+                bm[k] = out[k];
+            }
+        }
+    }
+    // group consecutive frames of one plan, at most kMaxGroup per group
+    int k = 0;
+    while (k < n) {
+        LaunchGroups L{};
+        int W = 8, ring = kDepthTile, Gmax = 1;
+        while (k < n && L.n_groups < kMaxGroupsPerLaunch) {
+            FrameGroup &g = L.g[L.n_groups];
+            g.plan = plans[k]->dev;
+            g.line0 = L.total_lines;
+            g.n = 0;
+            const supra_plan *p = plans[k];
+            g.bulk = p->host.bulk_ok;
+            while (k < n && plans[k] == p && g.n < kMaxGroup) {
+                if (reinterpret_cast<uintptr_t>(ch[k]) & 15) g.bulk = 0;
+                g.ch[g.n] = ch[k];
+                g.out[g.n] = bm[k];
+                ++g.n;
+                ++k;
+            }
+            Gmax = std::max(Gmax, g.n);
+            W = std::max(W, p->host.win_row);
+            ring = std::max(ring, kDepthTile + p->host.taps - 1);
+            L.total_lines += p->host.n_lines;
+            ++L.n_groups;
+        }
+        const int rc = launch_das(group_template(Gmax), 1, L, W, ring, st);
+        if (rc) return rc;
+    }
+    // scan conversion of the frames with a grid
+    ScanLaunch S{};
+    for (int f = 0; f < n; ++f) {
+        if (!plans[f]->host.has_grid) continue;
+        S.f[S.n++] = ScanFrame{plans[f]->dev, bm[f], out[f]};
+        if (S.n == kMaxScanFrames) {
+            const int rc = launch_scan(S, st);
+            if (rc) return rc;
+            S.n = 0;
+        }
+    }
+    return launch_scan(S, st);
+}
+
+int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *workspace, size_t workspace_bytes,
+                void *stream) {
+    const supra_plan *p[1] = {plan};
+    const int16_t *c[1] = {ch};
+    uint8_t *o[1] = {out};
+    if (!plan) return SUPRA_EINVAL;
+    return supra_bmode_batched(1, p, c, o, workspace, workspace_bytes, stream);
+}
+
+int supra_device_status(int32_t clear) {
+    int v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SUPRA_ECUDA;
+    if (cudaMemcpyFromSymbol(&v, supra::g_status, sizeof(int)) != cudaSuccess) return SUPRA_ECUDA;
+    if (clear) {
+        const int z = 0;
+        if (cudaMemcpyToSymbol(supra::g_status, &z, sizeof(int)) != cudaSuccess) return SUPRA_ECUDA;
+    }
+    return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+"""GPU parity of every node of the chain against the FP64 oracle, through the
+C ABI (Sec. 1 step list, Sec. 2 items 1-5, Table 1 nodes).  Sizes span several
+depth tiles with ragged tails; edge cases: single element, multi-line
+transmits, record start t0 > 0, coarse depth steps, unaligned records (the
+plain-load staging path), sector and pyramid layouts, windows with a hard
+aperture edge."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1711_06127_b300 as supra
+import phantom
+from _setups import small_linear, tiny
+from gpu_util import ENV_TOL, RF_TOL, assert_gray, max_norm_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _built():
+    from paper_1711_06127_b300 import build
+
+    build.build()
+    supra.load()
+    yield
+    assert supra.device_status() == 0
+
+
+def gpu_rf(p, ch):
+    plan = supra.Plan(**p)
+    rf = plan.beamform(torch.as_tensor(np.asarray(ch)).cuda())
+    torch.cuda.synchronize()
+    return rf.cpu().numpy().astype(np.float64)
+
+
+def setups():
+    out = {
+        "linear16_ragged": small_linear(16, 12, 300),
+        "linear_phantom": small_linear(32, 24, 700),
+        "sector": phantom.sector_setup(24, 0.3e-3, 17, 35.0, 350, fc=3.5e6, fs=20e6),
+        "pyramid": phantom.pyramid_setup(8, 8, 0.3e-3, 5, 4, 25.0, 260, fc=3.5e6, fs=20e6),
+        "multiline": phantom.linear_setup(16, 0.3e-3, 31, 400, fc=5e6, fs=40e6, lines_per_tx=2),
+        "single_element": phantom.linear_setup(1, 0.3e-3, 1, 200, fc=5e6, fs=40e6),
+        "unaligned_ns": small_linear(12, 8, 301),
+    }
+    return out
+
+
+@pytest.mark.parametrize("name", list(setups().keys()))
+def test_beamform_matches_oracle(name):
+    s = setups()[name]
+    p = s.params()
+    if name == "linear_phantom":
+        ch = phantom.synth_channels(s, phantom.default_phantom(s, 11), 11).numpy()
+    else:
+        ch = phantom.random_channels(s, 3).numpy()
+    ref = oracle.das(p, ch)
+    got = gpu_rf(p, ch)
+    assert max_norm_err(got, ref) <= RF_TOL
+
+
+def test_beamform_config1_full_size():
+    s = phantom.config1()
+    p = s.params()
+    ch = phantom.synth_channels(s, phantom.default_phantom(s, 1), 1).numpy()
+    assert max_norm_err(gpu_rf(p, ch), oracle.das(p, ch)) <= RF_TOL
+
+
+def test_beamform_record_start_and_coarse_depth():
+    s = small_linear(16, 10, 400)
+    p = s.params()
+    p.update(t0=37.3 / s.fs, depth0=0.7e-3, depth_step=1.5 * s.c / (2 * s.fs), n_depth=250)
+    ch = phantom.random_channels(s, 5).numpy()
+    assert max_norm_err(gpu_rf(p, ch), oracle.das(p, ch)) <= RF_TOL
+
+
+def test_beamform_unaligned_record_pointer():
+    s = small_linear(16, 10, 256)
+    p = s.params()
+    ch = phantom.random_channels(s, 6)
+    buf = torch.zeros(ch.numel() + 1, dtype=torch.int16, device="cuda")
+    view = buf[1:].view(ch.shape)
+    view.copy_(ch.cuda())
+    plan = supra.Plan(**p)
+    rf = plan.beamform(view).cpu().numpy()
+    assert max_norm_err(rf, oracle.das(p, ch.numpy())) <= RF_TOL
+
+
+@pytest.mark.parametrize("window", ["rect", "hamming"])
+def test_beamform_hard_edge_windows(window):
+    # A hard aperture edge makes the sum jump when an element crosses it; samples
+    # whose aperture has an element within 1e-9 m of the edge are decided by
+    # rounding and are left out (fp32 and fp64 may place it on either side).
+    s = small_linear(16, 9, 260, window=window)
+    p = s.params()
+    ch = phantom.random_channels(s, 8).numpy()
+    ref = oracle.das(p, ch)
+    got = gpu_rf(p, ch)
+    keep = np.ones_like(ref, bool)
+    for l in range(s.n_lines):
+        for i in range(s.n_depth):
+            _, _, margin = oracle.aperture(p, l, i)
+            keep[l, i] = np.min(np.abs(margin)) > 1e-9
+    assert keep.mean() > 0.9
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)[keep]) / scale <= RF_TOL
+
+
+def test_envelope_matches_oracle():
+    s = small_linear(16, 12, 700)
+    p = s.params()
+    rf = np.random.default_rng(0).normal(size=(s.n_lines, s.n_depth)).astype(np.float32)
+    ref = oracle.envelope(p, rf.astype(np.float64))
+    plan = supra.Plan(**p)
+    got = plan.envelope(torch.as_tensor(rf).cuda()).cpu().numpy()
+    assert max_norm_err(got, ref) <= ENV_TOL
+
+
+def test_logcompress_matches_oracle():
+    s = small_linear(16, 12, 700)
+    p = s.params()
+    env = np.exp(np.random.default_rng(1).uniform(-2, 11, (s.n_lines, s.n_depth))).astype(np.float32)
+    env[0, :5] = 0.0
+    ref = oracle.logcompress(env.astype(np.float64), p["log_ref"], p["dyn_range_db"])
+    plan = supra.Plan(**p)
+    got = plan.logcompress(torch.as_tensor(env).cuda()).cpu().numpy()
+    d = np.abs(got.astype(int) - ref.astype(int))
+    assert d.max() <= 1 and np.mean(d == 0) >= 0.999
+
+
+@pytest.mark.parametrize("kind", ["linear", "sector", "pyramid"])
+def test_scanconvert_matches_oracle(kind):
+    if kind == "linear":
+        s = phantom.linear_setup(32, 0.3e-3, 64, 500, grid_n=(123, 201))
+    elif kind == "sector":
+        s = phantom.sector_setup(32, 0.3e-3, 48, 40.0, 400, grid_n=(150, 130))
+    else:
+        s = phantom.pyramid_setup(8, 8, 0.3e-3, 12, 10, 30.0, 300, grid_n=(41, 37, 53))
+    p = s.params()
+    bm = np.random.default_rng(2).integers(0, 256, (s.n_lines, s.n_depth)).astype(np.uint8)
+    ref = oracle.scanconvert(p, bm)
+    ref = ref[:, 0, :] if p["grid"]["n"][1] == 1 else ref
+    plan = supra.Plan(**p)
+    got = plan.scanconvert(torch.as_tensor(bm).cuda()).cpu().numpy()
+    assert got.shape == ref.shape
+    assert_gray(got, ref, what=kind)
+    assert np.abs(got.astype(int) - ref.astype(int)).max() <= 1
+
+
+def test_scanconvert_identity_grid_is_exact():
+    s = phantom.linear_setup(16, 0.3e-3, 16, 300)
+    p = s.params()
+    xs = s.line_origin[:, 0]
+    p["grid"] = {"n": (16, 1, 300), "origin": (xs[0], 0.0, 0.0), "spacing": (xs[1] - xs[0], 1.0, s.depth_step)}
+    bm = np.random.default_rng(4).integers(0, 256, (16, 300)).astype(np.uint8)
+    plan = supra.Plan(**p)
+    got = plan.scanconvert(torch.as_tensor(bm).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(got, bm.T)
+
+
+def _chain_case(name):
+    if name == "linear_lines":
+        s = small_linear(32, 24, 700)
+    elif name == "linear_image":
+        s = phantom.linear_setup(48, 0.3e-3, 64, 900, fc=7e6, fs=40e6, grid_n=(140, 190))
+    elif name == "sector_image":
+        s = phantom.sector_setup(32, 0.3e-3, 40, 35.0, 600, fc=3.5e6, fs=20e6, grid_n=(160, 150))
+    else:
+        s = phantom.pyramid_setup(8, 8, 0.3e-3, 10, 9, 30.0, 400, fc=3.5e6, fs=20e6, grid_n=(40, 36, 50))
+    p = s.params()
+    ch = phantom.synth_channels(s, phantom.make_phantom(s, 21, 1500, n_points=3), 21).numpy()
+    ref = oracle.bmode(p, ch)
+    return s, p, ch, ref
+
+
+@pytest.mark.parametrize("name", ["linear_lines", "linear_image", "sector_image", "pyramid_volume"])
+def test_fused_bmode_matches_oracle(name):
+    s, p, ch, ref = _chain_case(name)
+    plan = supra.Plan(**p)
+    got = plan.bmode(torch.as_tensor(ch).cuda()).cpu().numpy()
+    assert got.shape == ref.shape
+    assert_gray(got, ref, what=name)
+
+
+def test_fused_equals_unfused_chain():
+    s = phantom.linear_setup(48, 0.3e-3, 64, 900, fc=7e6, fs=40e6, grid_n=(140, 190))
+    p = s.params()
+    ch = torch.as_tensor(phantom.synth_channels(s, phantom.default_phantom(s, 5), 5)).cuda()
+    plan = supra.Plan(**p)
+    img_unfused = plan.scanconvert(plan.logcompress(plan.envelope(plan.beamform(ch))))
+    img_fused = plan.bmode(ch)
+    assert_gray(img_fused.cpu().numpy(), img_unfused.cpu().numpy(), frac=0.9999, what="fused vs unfused")
+
+
+def test_batched_uneven_frames_equal_single_frames():
+    a = phantom.linear_setup(32, 0.3e-3, 40, 600, fc=7e6, fs=40e6, grid_n=(100, 120))
+    b = phantom.sector_setup(24, 0.3e-3, 30, 35.0, 500, fc=3.5e6, fs=20e6)   # no grid: lines out
+    pa, pb = supra.Plan(**a.params()), supra.Plan(**b.params())
+    plans = [pa, pa, pa, pb, pa, pb, pb, pa, pa, pa, pa, pa, pa, pa, pa, pa]
+    chs = []
+    for k, pl in enumerate(plans):
+        s = a if pl is pa else b
+        chs.append(torch.as_tensor(phantom.random_channels(s, 100 + k)).cuda())
+    outs = supra.bmode_batched(plans, chs)
+    for pl, c, o in zip(plans, chs, outs):
+        single = pl.bmode(c)
+        d = (single.int() - o.int()).abs().max().item()
+        assert d <= 1
+        assert (single == o).float().mean().item() >= 0.9999
+
+
+def test_config2_batch_of_64_matches_oracle_on_first_and_last_frame():
+    s = phantom.config2()
+    p = s.params()
+    plan = supra.Plan(**p)
+    seeds = list(range(1000, 1064))
+    chs = []
+    for sd in seeds:
+        chs.append(phantom.synth_channels(s, phantom.default_phantom(s, sd), sd, device="cuda"))
+    outs = supra.bmode_batched([plan] * 64, chs)
+    torch.cuda.synchronize()
+    for k in (0, 63):
+        ch = chs[k].cpu().numpy()
+        ref = oracle.bmode(p, ch)
+        assert_gray(outs[k].cpu().numpy(), ref, what=f"frame {k}")
+    # and the RF of one frame at full size
+    rf = plan.beamform(chs[7]).cpu().numpy()
+    assert max_norm_err(rf, oracle.das(p, chs[7].cpu().numpy())) <= RF_TOL
