@@ -2,18 +2,16 @@
 // the kernels of libsupra (sm_103a).
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "supra.h"
 
 namespace supra {
 
-constexpr int kDepthTile = 128;     // depth samples per beamforming tile (one per thread of a half-CTA)
-constexpr int kThreads = 256;       // threads of the beamforming CTA: 128 depths x 2 element halves
-constexpr int kChunk = 16;          // aperture elements staged per pipeline stage
+constexpr int kDepthTile = 256;     // depth samples per beamforming tile (one per consumer thread)
 constexpr int kMaxTaps = 127;
-constexpr int kMaxGroup = 8;        // frames of one plan beamformed together
-constexpr int kMaxStages = 4;
+constexpr int kMaxGroup = 16;       // frames of one plan beamformed together
 
 // Per-line constants (fp32; built from fp64 host geometry).
 struct LineGeo {
@@ -44,6 +42,7 @@ struct DevPlan {
     const int *tile_k;       // [n_tiles] integer base of the two-way delay at the tile's first depth
     const float *tile_f;     // [n_tiles] fractional remainder of that base
     const short4 *ap_box;    // [n_lines * n_tiles] element box (ix_lo, ix_hi, iy_lo, iy_hi), inclusive
+    const int *line_order;   // [n_lines] lines by decreasing beamforming work
     // ---- envelope + log compression
     int taps;                // odd
     float taps_c[kMaxTaps];  // h_k cos(w (k - H)), demodulation folded into the taps
@@ -61,21 +60,25 @@ struct DevPlan {
 
 // A group of up to kMaxGroup frames beamformed together under one plan.
 struct FrameGroup {
+    CUtensorMap tmap;                    // 4D map (sample pairs, element, transmit, frame) when tma != 0
     const DevPlan *plan;
     int n;                               // frames in the group
-    int bulk;                            // rows may be staged with bulk async copies (aligned records)
+    int bulk;                            // rows may be staged with 1D bulk async copies (aligned records)
+    int tma;                             // frames uniformly strided: stage all frames of a row with one tensor copy
     int line0;                           // first work item (lines) of this group in the launch
     const int16_t *ch[kMaxGroup];
     void *out[kMaxGroup];                // float rf / uint8 bm per frame
 };
 
-constexpr int kMaxGroupsPerLaunch = 96;
+constexpr int kMaxGroupsPerLaunch = 48;
 
 struct LaunchGroups {
     int n_groups;
     int total_lines;
+    int uniform;                         // every group uses the same plan
     FrameGroup g[kMaxGroupsPerLaunch];
 };
+static_assert(sizeof(LaunchGroups) <= 32000, "kernel parameter space is 32 KB");
 
 // device status word of this library on each device (first failure code wins);
 // libsupra is one translation unit, so the definition lives here.

@@ -1,19 +1,33 @@
 // das_kernel.cuh -- receive delay-and-sum beamforming (Sec. 1 "receive
 // beamforming", Sec. 2 items 1-2, Table 1 "Beamformer") with the envelope and
-// log-compression nodes (Sec. 2 items 3-4) fused behind it.
+// log-compression nodes (Sec. 2 items 3-4, Table 1 "Envelope", "Log comp.")
+// fused behind it.
 //
 // One CTA owns one scanline of a group of G frames that share a plan and
-// streams the line's depth axis in tiles of kDepthTile samples.  For every
-// tile the aperture's elements are visited in chunks of kChunk: a producer
-// (lanes 0..15 of warp 0, one element each) computes the element's sample
-// window for the tile and stages that window of all G frames' records into
-// shared memory with bulk async copies (TMA engine, cp.async.bulk) that
-// complete on the stage's mbarrier; a ring of `stages` buffers keeps
-// several chunks in flight while the CTA computes on the oldest.  Each thread
-// owns one depth sample and one half of the chunk's elements and computes the
-// delay, the linear interpolation weights and the apodization weight once,
-// then applies them to all G frames -- frames of one plan share their delays,
-// which is what makes a batch cheaper per frame than a single frame.
+// streams the line's depth axis in tiles of kTD = 256 samples, one consumer
+// thread per depth sample.  The CTA is warp-specialized:
+//   * warp 8 (producer) walks the tiles and, for each chunk of E = 32 / G
+//     aperture elements, computes every element's sample window for the tile
+//     and stages that window of all G frames' records into shared memory with
+//     the TMA engine, completing on the stage's "full" mbarrier.  When the
+//     group's frames lie at a uniform stride in memory, one tiled tensor copy
+//     (box: 136 sample pairs x 1 element x 1 transmit x G frames) moves an
+//     element's window for all frames at once and the tensor map's
+//     out-of-bounds fill supplies the zero padding outside the record;
+//     otherwise each of the 32 lanes issues one 1D bulk copy (cp.async.bulk)
+//     per (element, frame) row.
+//   * warps 0..7 (consumers) wait on "full", compute the delay, the linear
+//     interpolation weights and the apodization weight of each element once,
+//     apply them to all G frames, and release the buffer on its "empty"
+//     mbarrier.  A ring of kStages buffers keeps the HBM stream going while the
+//     consumers work; consumers and producer never meet at a CTA barrier.
+// Frames of one plan share their delays, which is what makes a batch cheaper
+// per frame than a single frame.
+//
+// The int16 samples are turned into fp32 without the conversion pipe: the
+// 16-bit pattern, its sign bit flipped, is placed in the mantissa of 2^23
+// (one LOP3), and 2^23 + 2^15 is subtracted (exact).  Pairs of frames share
+// packed f32x2 adds and FMAs.
 //
 // Delay precision.  The two-way delay in samples reaches a few thousand,
 // where the fp32 ulp is ~2.4e-4 samples.  The kernel therefore splits it as
@@ -21,17 +35,67 @@
 // with K_tile/f_tile the fp64-built base of the tile's first depth, and
 // dt = |p - o_t| - r, de = |p - x_e| - r evaluated without cancellation as
 // (|o - q|^2 + 2 r d.(o - q)) / (|p - q| + r).
+//
+// After the last chunk of a tile (MODE 1) the RF of the tile goes to a
+// per-frame ring that keeps the previous tile's last 2H samples, the complex
+// demodulating FIR runs register-blocked over it, and the log-compressed
+// codes are written out.
 #pragma once
 #include "common.cuh"
 
 namespace supra {
 
-struct StageMeta {
-    float beta, gamma, ex, ey;   // element constants for the CTA's line: d.(o - x_e), |o - x_e|^2, x_e, y_e
+constexpr int kTD = 256;             // depth samples per tile = consumer threads
+constexpr int kConsumers = 256;
+constexpr int kCtaThreads = 288;     // + one producer warp
+constexpr int kRows = 32;            // rows staged per stage = producer lanes
+constexpr int kStages = 4;
+constexpr float kMagic = 8421376.0f; // 2^23 + 2^15
+
+struct ElemMeta {
+    float beta, gamma, ex, ey;   // d.(o_l - x_e), |o_l - x_e|^2, x_e, y_e
     int ws;                      // absolute sample index of the row's first staged sample
     int valid;
     int pad[2];
 };
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pack2(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ u64 pack2u(uint32_t lo, uint32_t hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(u64 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// 4D tiled tensor copy global -> shared, completion counted on bar.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// int16 bit pattern (zero-extended) -> float bits of 2^23 + 2^15 + x
+__device__ __forceinline__ uint32_t biased(uint32_t u16) { return (u16 ^ 0x8000u) | 0x4B000000u; }
 
 __device__ __forceinline__ float window_weight(int window, float u) {
     if (window == SUPRA_WINDOW_HANN) return 0.5f + 0.5f * __cosf(3.14159265358979f * u);
@@ -49,287 +113,499 @@ __device__ __forceinline__ float path_excess(float r, float beta, float gamma) {
     return den > 1e-20f ? __fdividef(num, den) : 0.0f;
 }
 
-__device__ __forceinline__ int tile_chunks(const DevPlan *P, int line, int tile) {
+__device__ __forceinline__ int box_count(const DevPlan *P, int line, int tile) {
     short4 b = P->ap_box[line * P->n_tiles + tile];
-    int n = (b.y - b.x + 1) * (b.w - b.z + 1);
-    return (n + kChunk - 1) / kChunk;
+    return (b.y - b.x + 1) * (b.w - b.z + 1);
 }
 
-// Producer: stage chunk `chunk` of tile `tile` into ring buffer `buf`.
-// Called by lanes 0..kChunk-1 of warp 0; each lane stages one element row for all frames.
-template <int G>
-__device__ __forceinline__ void issue_stage(const DevPlan *P, const FrameGroup &fg, int nf, int line,
-                                            const LineGeo &lg, int tile, int chunk, int16_t *ring,
-                                            StageMeta *meta, uint64_t *bar, int W) {
-    const int lane = threadIdx.x;
-    const short4 b = P->ap_box[line * P->n_tiles + tile];
-    const int nbx = b.y - b.x + 1, nby = b.w - b.z + 1;
-    const int j = chunk * kChunk + lane;
-    StageMeta &mt = meta[lane];
-    int16_t *rows = ring + lane * W;   // frame g row: rows + g * kChunk * W
-    if (j >= nbx * nby) {
-        mt.valid = 0;
-        mbar_arrive_expect_tx(bar, 0);
+// named barrier among the 256 consumer threads (the producer warp never joins)
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ int consumer_sync_or(int p) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.s32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, 1, 256, pi;\n\tselp.s32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(p)
+        : "memory");
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Wait for a phase, giving up after ~budget cycles or when another thread has
+// flagged an abort.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+    return true;
+}
+
+// ring position p of the FIR buffer -> word offset (one pad word every 8: conflict-free blocked reads)
+__device__ __forceinline__ int ring_addr(int p) { return p + (p >> 3); }
+
+// Shared-memory layout, identical on host and device.
+struct SmemLayout {
+    int bars, meta, taps, ring, stage, total, ring_stride;
+    __host__ __device__ SmemLayout(int G, int mode, int W, int H) {
+        bars = 0;                                             // full[kStages], empty[kStages]
+        meta = 128;                                           // [kStages][kRows] ElemMeta
+        taps = meta + kStages * kRows * (int)sizeof(ElemMeta); // [128] float4 (c, c, s, s)
+        ring = taps + (mode == 1 ? 128 * 16 : 0);
+        ring_stride = ((kTD + 2 * H + ((kTD + 2 * H) >> 3)) + 3) & ~3;
+        stage = ring + (mode == 1 ? G * ring_stride * 4 : 0);
+        stage = (stage + 127) & ~127;
+        total = stage + kStages * kRows * W * 2;
+    }
+};
+
+// Item -> (group, line).  Launches of one plan interleave groups so that the
+// heaviest lines (plan-sorted) go first over all groups.
+__device__ __forceinline__ void locate_item(const LaunchGroups &L, int item, int &gi, int &line) {
+    if (L.uniform) {
+        gi = item % L.n_groups;
+        line = L.g[gi].plan->line_order[item / L.n_groups];
         return;
     }
-    const int e = (b.z + j / nbx) * P->el_nx + b.x + j % nbx;
-    const float4 xe = __ldg(&P->elem[e]);
+    gi = 0;
+    while (gi + 1 < L.n_groups && L.g[gi + 1].line0 <= item) ++gi;
+    line = L.g[gi].plan->line_order[item - L.g[gi].line0];
+}
+
+// -------------------------------------------------------------------------------------------------
+// Plan constants the producer needs, held in registers (the mbarrier/fence asm
+// statements clobber memory, which would otherwise force reloads every stage).
+struct ProdConst {
+    const short4 *ap_box;
+    const float4 *elem;
+    const int *tile_k;
+    const float *tile_f;
+    int n_tiles, el_nx, n_depth, n_s, n_el;
+    float depth0, depth_step, fsc, a1, t0fs;
+    __device__ ProdConst(const DevPlan *P)
+        : ap_box(P->ap_box), elem(P->elem), tile_k(P->tile_k), tile_f(P->tile_f), n_tiles(P->n_tiles),
+          el_nx(P->el_nx), n_depth(P->n_depth), n_s(P->n_s), n_el(P->n_el), depth0(P->depth0),
+          depth_step(P->depth_step), fsc(P->fsc), a1(P->a1), t0fs(P->t0fs) {}
+};
+
+// Sample window [ws, ws + W) (ws a multiple of 8) of element slot j of the tile's box.
+// Returns false when j is past the box.
+__device__ __forceinline__ bool element_window(const ProdConst &C, const LineGeo &lg, short4 b, int tile, int j,
+                                               int W, int &e, ElemMeta &m) {
+    const int nbx = b.y - b.x + 1, nby = b.w - b.z + 1;
+    if (j >= nbx * nby) return false;
+    e = (b.z + j / nbx) * C.el_nx + b.x + j % nbx;
+    const float4 xe = __ldg(&C.elem[e]);
     const float mx = lg.ox - xe.x, my = lg.oy - xe.y, mz = lg.oz - xe.z;
     const float beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
     const float gamma = mx * mx + my * my + mz * mz;
-
-    const int i0 = tile * kDepthTile;
-    const int i1 = min(i0 + kDepthTile - 1, P->n_depth - 1);
-    const float r0 = P->depth0 + (float)i0 * P->depth_step;
-    const float r1 = P->depth0 + (float)i1 * P->depth_step;
-    const int kt = P->tile_k[tile];
-    const float ft = P->tile_f[tile];
-    float s0 = ft + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * P->fsc;
-    float s1 = ft + P->a1 * (float)(i1 - i0) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * P->fsc;
+    const int i0 = tile * kTD;
+    const int i1 = min(i0 + kTD - 1, C.n_depth - 1);
+    const float r0 = C.depth0 + (float)i0 * C.depth_step;
+    const float r1 = C.depth0 + (float)i1 * C.depth_step;
+    const int kt = __ldg(&C.tile_k[tile]);
+    const float ft = __ldg(&C.tile_f[tile]);
+    const float s0 = ft + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * C.fsc;
+    const float s1 =
+        ft + C.a1 * (float)(i1 - i0) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * C.fsc;
     float lo = fminf(s0, s1), hi = fmaxf(s0, s1);
     // The two-way path is convex in r: its maximum is at an end, its minimum may be
     // inside the tile; bound that minimum by the sum of the two paths' minima.
     if ((-beta > r0 && -beta < r1) || (-lg.bt > r0 && -lg.bt < r1)) {
-        float re = fminf(fmaxf(-beta, r0), r1), rt = fminf(fmaxf(-lg.bt, r0), r1);
-        float de = sqrtf(fmaxf(fmaf(re, re + 2.0f * beta, gamma), 0.0f));
-        float dtp = sqrtf(fmaxf(fmaf(rt, rt + 2.0f * lg.bt, lg.gt), 0.0f));
-        float s_abs = (de + dtp) * P->fsc - P->t0fs;
-        lo = fminf(lo, s_abs - (float)kt);
+        const float re = fminf(fmaxf(-beta, r0), r1), rt = fminf(fmaxf(-lg.bt, r0), r1);
+        const float de = sqrtf(fmaxf(fmaf(re, re + 2.0f * beta, gamma), 0.0f));
+        const float dtp = sqrtf(fmaxf(fmaf(rt, rt + 2.0f * lg.bt, lg.gt), 0.0f));
+        lo = fminf(lo, (de + dtp) * C.fsc - C.t0fs - (float)kt);
     }
     const int lo_i = kt + (int)floorf(lo) - 1;
-    const int ws = (lo_i >> 3) << 3;                     // floor to a multiple of 8 samples (16 bytes)
+    const int ws = (lo_i >> 3) << 3;   // 16-byte aligned window start
     if (kt + (int)floorf(hi) + 2 > ws + W - 1) set_status(SUPRA_EINTERNAL);
-    const int n_s = P->n_s;
-    const int c0 = max(ws, 0), c1 = min(ws + W, n_s);
-    const long long rec = ((long long)lg.tx * P->n_el + e) * (long long)n_s;
-    // zero padding outside the record (generic stores, released by this lane's arrive)
-    if (c0 > ws || c1 < ws + W) {
-        for (int g = 0; g < nf; ++g) {
-            int16_t *dst = rows + g * kChunk * W;
-            const int a_end = min(c0, ws + W) - ws;
-            for (int k = 0; k < a_end; ++k) dst[k] = 0;
-            for (int k = max(c1, c0) - ws; k < W; ++k) dst[k] = 0;
+    m.beta = beta;
+    m.gamma = gamma;
+    m.ex = xe.x;
+    m.ey = xe.y;
+    m.ws = ws;
+    m.valid = 1;
+    m.pad[0] = m.pad[1] = 0;
+    return true;
+}
+
+// Producer, one stage.  Shared layout of a stage: rows [element slot][frame][W].
+// Every lane arrives once on `full` (count kRows).
+template <int G>
+__device__ __forceinline__ void produce_stage(const ProdConst &C, const FrameGroup &fg, int nf, const LineGeo &lg,
+                                              int line, int tile, int chunk, int16_t *sbuf, ElemMeta *meta,
+                                              uint64_t *full, int W) {
+    constexpr int E = kRows / G;
+    const int lane = threadIdx.x & 31;
+    const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
+    if (fg.tma) {
+        // lane ej < E: one tensor copy of the element's window for all G frames
+        if (lane < E) {
+            int e;
+            ElemMeta m;
+            if (element_window(C, lg, b, tile, chunk * E + lane, W, e, m)) {
+                meta[lane] = m;
+                mbar_arrive_expect_tx(full, (uint32_t)(G * W * 2));
+                tma_load_4d(sbuf + lane * G * W, &fg.tmap, m.ws >> 1, e, lg.tx, 0, full);
+                return;
+            }
+            meta[lane].valid = 0;
         }
+        mbar_arrive_expect_tx(full, 0);
+        return;
     }
-    mt.beta = beta;
-    mt.gamma = gamma;
-    mt.ex = xe.x;
-    mt.ey = xe.y;
-    mt.ws = ws;
-    mt.valid = 1;
+    // fallback: lane l stages row l = (element slot l / G, frame l % G) with one 1D bulk copy
+    const int ej = lane / G, f = lane % G;
+    int16_t *row = sbuf + lane * W;
+    int e;
+    ElemMeta m;
+    if (!element_window(C, lg, b, tile, chunk * E + ej, W, e, m)) {
+        if (f == 0) meta[ej].valid = 0;
+        mbar_arrive_expect_tx(full, 0);
+        return;
+    }
+    if (f == 0) meta[ej] = m;
+    if (f >= nf) {
+        mbar_arrive_expect_tx(full, 0);
+        return;
+    }
+    const int ws = m.ws;
+    const int n_s = C.n_s;
+    const int c0 = max(ws, 0), c1 = min(ws + W, n_s);
+    const long long rec = ((long long)lg.tx * C.n_el + e) * (long long)n_s;
+    if (c0 > ws || c1 < ws + W) {   // zero padding outside the record
+        const int a_end = min(c0, ws + W) - ws;
+        for (int k = 0; k < a_end; ++k) row[k] = 0;
+        for (int k = max(c1, c0) - ws; k < W; ++k) row[k] = 0;
+    }
     if (fg.bulk) {
         const uint32_t bytes = c1 > c0 ? (uint32_t)(c1 - c0) * 2u : 0u;
-        mbar_arrive_expect_tx(bar, bytes * (uint32_t)nf);
+        mbar_arrive_expect_tx(full, bytes);
         if (bytes) {
             fence_proxy_async_smem();
-            for (int g = 0; g < nf; ++g)
-                bulk_g2s(rows + g * kChunk * W + (c0 - ws), fg.ch[g] + rec + c0, bytes, bar);
+            bulk_g2s(row + (c0 - ws), fg.ch[f] + rec + c0, bytes, full);
         }
     } else {
-        for (int g = 0; g < nf; ++g) {
-            int16_t *dst = rows + g * kChunk * W;
-            const int16_t *src = fg.ch[g] + rec;
-            for (int k = c0; k < c1; ++k) dst[k - ws] = src[k];
-        }
-        mbar_arrive_expect_tx(bar, 0);
+        const int16_t *src = fg.ch[f] + rec;
+        for (int k = c0; k < c1; ++k) row[k - ws] = src[k];
+        mbar_arrive_expect_tx(full, 0);
     }
 }
 
+// -------------------------------------------------------------------------------------------------
+// Consumer: all E element slots of one stage for this thread's depth sample.
+struct Geo {
+    float w0, w1;
+    int idx;
+    bool go;   // some lane of the warp is inside this element's aperture
+};
+
+__device__ __forceinline__ Geo element_geo(const ElemMeta &md, int W, float r, float qx, float qy, float inv_a,
+                                           float base, int kt, bool use_y, int window, float fsc) {
+    Geo g;
+    const float ux = (md.ex - qx) * inv_a;
+    bool in = fabsf(ux) <= 1.0f;
+    float w = window_weight(window, ux);
+    if (use_y) {
+        const float uy = (md.ey - qy) * inv_a;
+        in = in && fabsf(uy) <= 1.0f;
+        w *= window_weight(window, uy);
+    }
+    g.go = __any_sync(0xffffffffu, in) && md.valid;
+    w = in ? w : 0.0f;
+    const float s = base + path_excess(r, md.beta, md.gamma) * fsc;
+    const float fl = floorf(s);
+    g.w1 = w * (s - fl);
+    g.w0 = w - g.w1;
+    g.idx = min(max(kt + (int)fl - md.ws, 0), W - 2);
+    return g;
+}
+
+// Frame loop of one element: rows [frame][W] starting at `rows`.
+template <int G, int WT>
+__device__ __forceinline__ void element_frames(const int16_t *rows, int Wrt, const Geo &g,
+                                               u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1) {
+    const int W = WT ? WT : Wrt;
+    const uint16_t *row = reinterpret_cast<const uint16_t *>(rows) + g.idx;
+    if constexpr (G == 1) {
+        const float x0 = __uint_as_float(biased(row[0])) - kMagic;
+        const float x1 = __uint_as_float(biased(row[1])) - kMagic;
+        acc1 = fmaf(g.w0, x0, fmaf(g.w1, x1, acc1));
+    } else {
+        const u64 W0 = pack2(g.w0, g.w0), W1 = pack2(g.w1, g.w1), NB = pack2(-kMagic, -kMagic);
+#pragma unroll
+        for (int q = 0; q < G / 2; ++q) {
+            const uint16_t *ra = row + (2 * q) * W;
+            const uint16_t *rb = row + (2 * q + 1) * W;
+            const u64 f0 = add2(pack2u(biased(ra[0]), biased(rb[0])), NB);
+            const u64 f1 = add2(pack2u(biased(ra[1]), biased(rb[1])), NB);
+            acc2[q] = fma2(W1, f1, fma2(W0, f0, acc2[q]));
+        }
+    }
+}
+
+template <int G, int WT>
+__device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int Wrt,
+                                              float r, float qx, float qy, float inv_a, float base, int kt,
+                                              bool use_y, int window, float fsc, u64 (&acc2)[G / 2 > 0 ? G / 2 : 1],
+                                              float &acc1, float &wsum) {
+    constexpr int E = kRows / G;
+    const int W = WT ? WT : Wrt;
+    if constexpr (E <= 4) {
+        // geometry of every slot first (independent chains), then the frame loops
+        Geo g[E];
+#pragma unroll
+        for (int ej = 0; ej < E; ++ej)
+            g[ej] = element_geo(meta[ej], W, r, qx, qy, inv_a, base, kt, use_y, window, fsc);
+#pragma unroll
+        for (int ej = 0; ej < E; ++ej) {
+            if (!g[ej].go) continue;
+            element_frames<G, WT>(sbuf + ej * G * W, W, g[ej], acc2, acc1);
+            wsum += g[ej].w0 + g[ej].w1;
+        }
+    } else {
+#pragma unroll 2
+        for (int ej = 0; ej < E; ++ej) {
+            const ElemMeta md = meta[ej];
+            if (!md.valid) break;
+            const Geo g = element_geo(md, W, r, qx, qy, inv_a, base, kt, use_y, window, fsc);
+            if (!g.go) continue;
+            element_frames<G, WT>(sbuf + ej * G * W, W, g, acc2, acc1);
+            wsum += g.w0 + g.w1;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------------------
+// Envelope + log compression of one tile: outputs o = i0 - H + t for t in [0, kTD).
+// Thread -> (frame pair q, block b of BO consecutive outputs); G == 1: one output per thread.
+template <int G>
+__device__ __forceinline__ void fir_log_tile(const DevPlan *P, const FrameGroup &fg, int nf, int line, int i0,
+                                             const float *ring, int RS, const float4 *taps4, int K, int H) {
+    const int tid = threadIdx.x;
+    const int nd = P->n_depth;
+    const float la = P->log_a, lb = P->log_b;
+    if constexpr (G == 1) {
+        const int o = i0 - H + tid;
+        if (o < 0 || o >= nd || nf < 1) return;
+        float re = 0.f, im = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const float v = ring[ring_addr(tid + 2 * H - k)];
+            const float4 t = taps4[k];
+            re = fmaf(t.x, v, re);
+            im = fmaf(t.z, v, im);
+        }
+        const float env = 2.0f * sqrtf(fmaf(re, re, im * im));
+        float code = 0.f;
+        if (env > 0.f) code = fminf(fmaxf(floorf(fmaf(la, __log2f(env), lb)), 0.f), 255.f);
+        static_cast<uint8_t *>(fg.out[0])[(long long)line * nd + o] = (uint8_t)code;
+    } else {
+        constexpr int NP = G / 2;                  // frame pairs
+        constexpr int TPP = kConsumers / NP;       // threads per pair
+        constexpr int BO = kTD / TPP;              // outputs per thread
+        const int q = tid / TPP, bq = tid % TPP;
+        const int fa = 2 * q, fb = 2 * q + 1;
+        const float *ra = ring + fa * RS, *rb = ring + fb * RS;
+        u64 re[BO], im[BO];
+#pragma unroll
+        for (int j = 0; j < BO; ++j) re[j] = im[j] = 0ull;
+        // window: positions P0 - k + j for j < BO, P0 = bq*BO + 2H; taps zero-padded to a multiple of BO
+        const int P0 = bq * BO + 2 * H;
+        u64 win[2 * BO];
+        for (int k0 = 0; k0 < K; k0 += BO) {
+            // positions P0 - k0 - BO + 1 .. P0 - k0 + BO - 1  ->  win[1 .. 2BO-1]
+#pragma unroll
+            for (int t = 1; t < 2 * BO; ++t) {
+                const int p = P0 - k0 - BO + t;
+                const int a = ring_addr(max(p, 0));
+                win[t] = pack2(ra[a], rb[a]);
+            }
+#pragma unroll
+            for (int kk = 0; kk < BO; ++kk) {
+                const float4 t4 = taps4[k0 + kk];
+                const u64 C = pack2(t4.x, t4.y), S = pack2(t4.z, t4.w);
+#pragma unroll
+                for (int j = 0; j < BO; ++j) {
+                    const u64 v = win[BO - kk + j];   // position P0 - (k0 + kk) + j
+                    re[j] = fma2(C, v, re[j]);
+                    im[j] = fma2(S, v, im[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < BO; ++j) {
+            const int o = i0 - H + bq * BO + j;
+            if (o < 0 || o >= nd) continue;
+            float rea, reb, ima, imb;
+            unpack2(re[j], rea, reb);
+            unpack2(im[j], ima, imb);
+            const float ea = 2.0f * sqrtf(fmaf(rea, rea, ima * ima));
+            const float eb = 2.0f * sqrtf(fmaf(reb, reb, imb * imb));
+            float ca = 0.f, cb = 0.f;
+            if (ea > 0.f) ca = fminf(fmaxf(floorf(fmaf(la, __log2f(ea), lb)), 0.f), 255.f);
+            if (eb > 0.f) cb = fminf(fmaxf(floorf(fmaf(la, __log2f(eb), lb)), 0.f), 255.f);
+            if (fa < nf) static_cast<uint8_t *>(fg.out[fa])[(long long)line * nd + o] = (uint8_t)ca;
+            if (fb < nf) static_cast<uint8_t *>(fg.out[fb])[(long long)line * nd + o] = (uint8_t)cb;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------------------
 // MODE 0: write RF (float [n_lines][n_depth] per frame).
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
-template <int G, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
-    das_kernel(const __grid_constant__ LaunchGroups L, int stages, int W, int ring_stride) {
+// WT: compile-time staged row length (0 = runtime W; G == 1 only).
+template <int G, int MODE, int WT>
+__global__ void __launch_bounds__(kCtaThreads, 2)
+    das_kernel(const __grid_constant__ LaunchGroups L, int Wrt, int Hmax) {
+    constexpr int E = kRows / G;
     extern __shared__ __align__(128) unsigned char smem[];
-    // ---- which (group, line)
-    const int item = blockIdx.x;
-    int gi = 0;
-    while (gi + 1 < L.n_groups && L.g[gi + 1].line0 <= item) ++gi;
+    const int W = WT ? WT : Wrt;
+    int gi, line;
+    locate_item(L, blockIdx.x, gi, line);
     const FrameGroup &fg = L.g[gi];
     const DevPlan *P = fg.plan;
-    const int line = item - fg.line0;
     const int nf = min(fg.n, G);
-    const LineGeo lg = P->lines[line];
     const int NT = P->n_tiles;
     const int nd = P->n_depth;
-
-    // ---- shared memory carve-up
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                     // [kMaxStages]
-    StageMeta *metas = reinterpret_cast<StageMeta *>(smem + 64);             // [kMaxStages][kChunk]
-    float *red = reinterpret_cast<float *>(smem + 64 + kMaxStages * kChunk * sizeof(StageMeta));  // [G + 1][128]
-    float *ring_rf = red + (G + 1) * kDepthTile;                             // MODE 1: [G][ring_stride]
-    float *taps = ring_rf + (MODE == 1 ? G * ring_stride : 0);               // MODE 1: [2][kMaxTaps]
-    size_t head = 64 + kMaxStages * kChunk * sizeof(StageMeta) + (G + 1) * kDepthTile * 4 +
-                  (MODE == 1 ? (G * ring_stride + 2 * kMaxTaps) * 4 : 0);
-    head = (head + 127) & ~size_t(127);
-    int16_t *stage_buf = reinterpret_cast<int16_t *>(smem + head);
-    const int stage_elems = G * kChunk * W;                                  // int16 per stage
-
+    const int K = P->taps, H = (K - 1) >> 1;
+    const SmemLayout lay(G, MODE, W, Hmax);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
+    uint64_t *empty = full + kStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kStages);
+    ElemMeta *metas = reinterpret_cast<ElemMeta *>(smem + lay.meta);
+    float4 *taps4 = reinterpret_cast<float4 *>(smem + lay.taps);
+    float *ring = reinterpret_cast<float *>(smem + lay.ring);
+    int16_t *stages = reinterpret_cast<int16_t *>(smem + lay.stage);
+    const int stage_elems = kRows * W;
     const int tid = threadIdx.x;
-    const int m = tid & (kDepthTile - 1);
-    const int h = tid >> 7;
-    const int H = (P->taps - 1) >> 1;
+    const int warp = tid >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], kChunk);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], kRows);
+            mbar_init(&empty[s], kConsumers / 32);
+        }
+        *abort_flag = 0;
         fence_mbar_init();
     }
     if (MODE == 1) {
-        for (int k = tid; k < P->taps; k += kThreads) {
-            taps[k] = P->taps_c[k];
-            taps[kMaxTaps + k] = P->taps_s[k];
+        for (int k = tid; k < 128; k += kCtaThreads) {
+            const float c = k < K ? P->taps_c[k] : 0.f, s = k < K ? P->taps_s[k] : 0.f;
+            taps4[k] = make_float4(c, c, s, s);
         }
-        for (int k = tid; k < G * ring_stride; k += kThreads) ring_rf[k] = 0.0f;
+        for (int k = tid; k < G * lay.ring_stride; k += kCtaThreads) ring[k] = 0.f;
     }
+    const LineGeo lg = P->lines[line];
     __syncthreads();
 
-    // total stages of this CTA
-    int total = 0;
-    for (int t = 0; t < NT; ++t) total += tile_chunks(P, line, t);
-
-    // producer cursor (kept by every thread; used by warp 0)
-    int p_tile = 0, p_chunk = 0, issued = 0;
-    auto advance = [&]() {
-        ++p_chunk;
-        while (p_tile < NT && p_chunk >= tile_chunks(P, line, p_tile)) {
-            p_chunk = 0;
-            ++p_tile;
+    if (warp == kConsumers / 32) {
+        // ------------------------------------------------------------------ producer warp
+        const ProdConst C(P);
+        int n = 0;
+        bool ok = true;
+        for (int tile = 0; tile < NT && ok; ++tile) {
+            const int nch = (box_count(P, line, tile) + E - 1) / E;
+            for (int c = 0; c < nch; ++c, ++n) {
+                const int s = n % kStages;
+                if (n >= kStages &&
+                    !__all_sync(0xffffffffu, wait_phase(&empty[s], (uint32_t)(((n / kStages) - 1) & 1), abort_flag))) {
+                    ok = false;
+                    break;
+                }
+                produce_stage<G>(C, fg, nf, lg, line, tile, c, stages + s * stage_elems, metas + s * kRows,
+                                 &full[s], W);
+            }
         }
-    };
-    while (p_tile < NT && tile_chunks(P, line, p_tile) == 0) ++p_tile;
-    for (int s = 0; s < stages && issued < total; ++s) {
-        if (tid < kChunk)
-            issue_stage<G>(P, fg, nf, line, lg, p_tile, p_chunk, stage_buf + s * stage_elems, metas + s * kChunk,
-                           &bars[s], W);
-        advance();
-        ++issued;
+        if (!ok) {
+            *abort_flag = 1;
+            set_status(SUPRA_ETIMEOUT);
+            // let copies in flight land before the CTA's shared memory goes away
+            for (int k = max(0, n - kStages); k < n; ++k)
+                mbar_wait_bounded(&full[k % kStages], (uint32_t)((k / kStages) & 1), 1LL << 27);
+        }
+        return;
     }
 
-    int n = 0;            // stages consumed
-    bool failed = false;
-    for (int tile = 0; tile <= NT && !failed; ++tile) {
-        const int i0 = tile * kDepthTile;
+    // ---------------------------------------------------------------------- consumer warps
+    const int m = tid;
+    const bool use_y = P->el_ny > 1 || P->ymax > P->ymin;
+    const int window = P->window;
+    const float fsc = P->fsc;
+    int n = 0;
+    bool aborted = false;
+    for (int tile = 0; tile < NT + (MODE == 1 ? 1 : 0); ++tile) {
+        const int i0 = tile * kTD;
         const int i = i0 + m;
-        const bool act = (tile < NT) && (i < nd);
-        float acc[G];
+        u64 acc2[G / 2 > 0 ? G / 2 : 1];
 #pragma unroll
-        for (int g = 0; g < G; ++g) acc[g] = 0.0f;
-        float wsum = 0.0f;
+        for (int q = 0; q < (G / 2 > 0 ? G / 2 : 1); ++q) acc2[q] = 0ull;
+        float acc1 = 0.f, wsum = 0.f;
         if (tile < NT) {
-            // per-thread constants of depth sample i
             const float r = P->depth0 + (float)i * P->depth_step;
             const float px = fmaf(r, lg.dx, lg.ox), py = fmaf(r, lg.dy, lg.oy), pz = fmaf(r, lg.dz, lg.oz);
             const float qx = fminf(fmaxf(px, P->xmin), P->xmax);
             const float qy = fminf(fmaxf(py, P->ymin), P->ymax);
-            const float a = fmaxf(pz * P->inv2f, P->amin);
-            const float inv_a = 1.0f / a;
-            const float base = P->tile_f[tile] + P->a1 * (float)m + path_excess(r, lg.bt, lg.gt) * P->fsc;
+            const float inv_a = 1.0f / fmaxf(pz * P->inv2f, P->amin);
+            const float base = P->tile_f[tile] + P->a1 * (float)m + path_excess(r, lg.bt, lg.gt) * fsc;
             const int kt = P->tile_k[tile];
-            const int nch = tile_chunks(P, line, tile);
-            const int window = P->window;
-            const float fsc = P->fsc;
+            const int nch = (box_count(P, line, tile) + E - 1) / E;
             for (int c = 0; c < nch; ++c, ++n) {
-                const int sb = n % stages;
-                bool ok = mbar_wait_bounded(&bars[sb], (uint32_t)((n / stages) & 1), 1LL << 31);
-                if (ok && act) {
-                    const StageMeta *mt = metas + sb * kChunk;
-                    const int16_t *buf = stage_buf + sb * stage_elems;
-#pragma unroll 2
-                    for (int jj = 0; jj < kChunk / 2; ++jj) {
-                        const int slot = h * (kChunk / 2) + jj;
-                        const StageMeta md = mt[slot];
-                        if (!md.valid) break;
-                        const float ux = (md.ex - qx) * inv_a, uy = (md.ey - qy) * inv_a;
-                        if (fabsf(ux) > 1.0f || fabsf(uy) > 1.0f) continue;
-                        const float w = window_weight(window, ux) * window_weight(window, uy);
-                        const float s = base + path_excess(r, md.beta, md.gamma) * fsc;
-                        const float fl = floorf(s);
-                        const float phi = s - fl;
-                        int idx = kt + (int)fl - md.ws;
-                        idx = min(max(idx, 0), W - 2);
-                        const int16_t *row = buf + slot * W + idx;
-#pragma unroll
-                        for (int g = 0; g < G; ++g) {
-                            const float x0 = (float)row[g * kChunk * W];
-                            const float x1 = (float)row[g * kChunk * W + 1];
-                            acc[g] = fmaf(w, fmaf(phi, x1 - x0, x0), acc[g]);
-                        }
-                        wsum += w;
-                    }
+                const int s = n % kStages;
+                // warp-uniform decision: consume_stage uses warp votes
+                if (!aborted &&
+                    !__all_sync(0xffffffffu, wait_phase(&full[s], (uint32_t)((n / kStages) & 1), abort_flag))) {
+                    aborted = true;
+                    *abort_flag = 1;
+                    set_status(SUPRA_ETIMEOUT);
                 }
-                failed = __syncthreads_or(!ok);
-                if (failed) break;
-                // refill the buffer just consumed with stage n + stages
-                if (issued < total) {
-                    if (tid < kChunk)
-                        issue_stage<G>(P, fg, nf, line, lg, p_tile, p_chunk, stage_buf + sb * stage_elems,
-                                       metas + sb * kChunk, &bars[sb], W);
-                    advance();
-                    ++issued;
-                }
+                if (!aborted)
+                    consume_stage<G, WT>(stages + s * stage_elems, metas + s * kRows, W, r, qx, qy, inv_a, base,
+                                         kt, use_y, window, fsc, acc2, acc1, wsum);
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&empty[s]);
             }
-            if (failed) break;
-            // combine the two element halves
-            if (h == 1) {
-#pragma unroll
-                for (int g = 0; g < G; ++g) red[g * kDepthTile + m] = acc[g];
-                red[G * kDepthTile + m] = wsum;
-            }
-            __syncthreads();
-            if (h == 0) {
-                wsum += red[G * kDepthTile + m];
-                const float inv = wsum > 0.0f ? 1.0f / wsum : 0.0f;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const float v = act ? (acc[g] + red[g * kDepthTile + m]) * inv : 0.0f;
-                    if (MODE == 0) {
-                        if (act && g < nf)
-                            static_cast<float *>(fg.out[g])[(long long)line * nd + i] = v;
-                    } else {
-                        ring_rf[g * ring_stride + 2 * H + m] = v;
-                    }
-                }
-            }
-        } else if (MODE == 1) {
-            // the tile past the end: zero padding feeds the last H outputs
-            for (int k = tid; k < G * kDepthTile; k += kThreads)
-                ring_rf[(k / kDepthTile) * ring_stride + 2 * H + (k % kDepthTile)] = 0.0f;
         }
-        if (MODE == 1) {
-            __syncthreads();
-            // envelope of depth o = i0 - H + m: 2 |sum_k g_k rf(o + H - k)|, g_k = h_k e^{j w (k - H)}
-            const int o = i0 - H + m;
-            if (o >= 0 && o < nd) {
-                for (int g = h; g < nf; g += 2) {
-                    const float *x = ring_rf + g * ring_stride + 2 * H + m;
-                    float re = 0.0f, im = 0.0f;
-                    for (int k = 0; k < 2 * H + 1; ++k) {
-                        const float v = x[-k];
-                        re = fmaf(taps[k], v, re);
-                        im = fmaf(taps[kMaxTaps + k], v, im);
-                    }
-                    const float env = 2.0f * sqrtf(fmaf(re, re, im * im));
-                    float code = 0.0f;
-                    if (env > 0.0f) code = fminf(fmaxf(floorf(fmaf(P->log_a, __log2f(env), P->log_b)), 0.0f), 255.0f);
-                    static_cast<uint8_t *>(fg.out[g])[(long long)line * nd + o] = (uint8_t)code;
-                }
+        if (consumer_sync_or(aborted ? 1 : 0)) return;
+        const bool act = (tile < NT) && (i < nd);
+        const float inv = wsum > 0.f ? 1.0f / wsum : 0.f;
+        float v[G];
+        if constexpr (G == 1) {
+            v[0] = act ? acc1 * inv : 0.f;
+        } else {
+#pragma unroll
+            for (int q = 0; q < G / 2; ++q) {
+                float a, b;
+                unpack2(acc2[q], a, b);
+                v[2 * q] = act ? a * inv : 0.f;
+                v[2 * q + 1] = act ? b * inv : 0.f;
             }
-            __syncthreads();
-            // keep the last 2H RF samples for the next tile's halo
-            for (int k = tid; k < G * 2 * H; k += kThreads) {
+        }
+        if (MODE == 0) {
+            if (act) {
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (g < nf) static_cast<float *>(fg.out[g])[(long long)line * nd + i] = v[g];
+            }
+        } else {
+            const int a = ring_addr(2 * H + m);
+#pragma unroll
+            for (int g = 0; g < G; ++g) ring[g * lay.ring_stride + a] = v[g];
+            consumer_sync();
+            fir_log_tile<G>(P, fg, nf, line, i0, ring, lay.ring_stride, taps4, K, H);
+            consumer_sync();
+            // keep the last 2H RF samples as the next tile's leading halo
+            for (int k = m; k < G * 2 * H; k += kConsumers) {
                 const int g = k / (2 * H), j = k % (2 * H);
-                ring_rf[g * ring_stride + j] = ring_rf[g * ring_stride + kDepthTile + j];
+                ring[g * lay.ring_stride + ring_addr(j)] = ring[g * lay.ring_stride + ring_addr(kTD + j)];
             }
-            __syncthreads();
+            consumer_sync();
         }
-    }
-    if (failed) {
-        set_status(SUPRA_ETIMEOUT);
-        // let copies still in flight land before the CTA's shared memory goes away
-        if (tid == 0)
-            for (int k = n; k < issued; ++k)
-                mbar_wait_bounded(&bars[k % stages], (uint32_t)((k / stages) & 1), 1LL << 27);
-        __syncthreads();
     }
 }
 

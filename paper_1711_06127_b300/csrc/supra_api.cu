@@ -109,48 +109,81 @@ long long count_nodes(double q, double a, double x0, double p, int n) {
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? SUPRA_OK : SUPRA_ECUDA; }
 
-// kernel choice for a frame group size
-int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : 8; }
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-size_t das_smem_bytes(int G, int mode, int stages, int W, int ring_stride) {
-    size_t head = 64 + kMaxStages * kChunk * sizeof(StageMeta) + (size_t)(G + 1) * kDepthTile * 4 +
-                  (mode == 1 ? ((size_t)G * ring_stride + 2 * kMaxTaps) * 4 : 0);
-    head = (head + 127) & ~size_t(127);
-    return head + (size_t)stages * G * kChunk * W * 2;
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
 }
 
-template <int G, int MODE>
-int launch_das_t(const LaunchGroups &L, int W, int ring_stride, cudaStream_t st) {
+// 4D map over a group's records viewed as int32 sample pairs: (n_s / 2, n_el, n_tx, frames),
+// box (W / 2, 1, 1, G); reads outside the records fill zeros.
+bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, int frames, const DevPlan &H, int W,
+                    int G) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || frame_stride <= 0 || (frame_stride & 15)) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)H.n_s / 2, (cuuint64_t)H.n_el, (cuuint64_t)H.n_tx, (cuuint64_t)frames};
+    const cuuint64_t strides[3] = {(cuuint64_t)H.n_s * 2, (cuuint64_t)H.n_s * 2 * H.n_el, (cuuint64_t)frame_stride};
+    const cuuint32_t box[4] = {(cuuint32_t)W / 2, 1, 1, (cuuint32_t)G};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// kernel choice for a frame group size
+int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
+
+// Staged row length for a plan: compile-time 272 (depth step <= c/(2 fs)) or 528
+// (<= c/fs) samples, enough for a 256-sample depth tile plus alignment slack.
+int row_len_for(double a1) { return a1 <= 1.0 + 1e-9 ? 272 : 528; }
+
+template <int G, int MODE, int WT>
+int launch_das_t(const LaunchGroups &L, int W, int Hmax, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int stages = kMaxStages;
-    while (stages > 2 && das_smem_bytes(G, MODE, stages, W, ring_stride) > (size_t)max_optin) --stages;
-    const size_t smem = das_smem_bytes(G, MODE, stages, W, ring_stride);
-    if (smem > (size_t)max_optin) return SUPRA_EINVAL;
-    auto kern = das_kernel<G, MODE>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const SmemLayout lay(G, MODE, WT ? WT : W, Hmax);
+    if (lay.total > max_optin) return SUPRA_EINVAL;
+    auto kern = das_kernel<G, MODE, WT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess)
         return SUPRA_ECUDA;
-    kern<<<L.total_lines, kThreads, smem, st>>>(L, stages, W, ring_stride);
+    kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L, W, Hmax);
     return check_cuda(cudaGetLastError());
 }
 
-int launch_das(int G, int mode, const LaunchGroups &L, int W, int ring_stride, cudaStream_t st) {
+template <int G, int MODE>
+int launch_das_w(const LaunchGroups &L, int W, int Hmax, cudaStream_t st) {
+    if (W == 272) return launch_das_t<G, MODE, 272>(L, W, Hmax, st);
+    if (W == 528) return launch_das_t<G, MODE, 528>(L, W, Hmax, st);
+    return SUPRA_EINVAL;
+}
+
+int launch_das(int G, int mode, const LaunchGroups &L, int W, int Hmax, cudaStream_t st) {
     if (L.total_lines == 0) return SUPRA_OK;
-    if (mode == 0) {
-        switch (G) {
-            case 1: return launch_das_t<1, 0>(L, W, ring_stride, st);
-            case 2: return launch_das_t<2, 0>(L, W, ring_stride, st);
-            case 4: return launch_das_t<4, 0>(L, W, ring_stride, st);
-            default: return launch_das_t<8, 0>(L, W, ring_stride, st);
-        }
-    }
+    if (G == 1) return mode == 0 ? launch_das_t<1, 0, 0>(L, W, Hmax, st) : launch_das_t<1, 1, 0>(L, W, Hmax, st);
+    if (mode == 0) return SUPRA_EINVAL;
     switch (G) {
-        case 1: return launch_das_t<1, 1>(L, W, ring_stride, st);
-        case 2: return launch_das_t<2, 1>(L, W, ring_stride, st);
-        case 4: return launch_das_t<4, 1>(L, W, ring_stride, st);
-        default: return launch_das_t<8, 1>(L, W, ring_stride, st);
+        case 2: return launch_das_w<2, 1>(L, W, Hmax, st);
+        case 4: return launch_das_w<4, 1>(L, W, Hmax, st);
+        case 8: return launch_das_w<8, 1>(L, W, Hmax, st);
+        default: return launch_das_w<16, 1>(L, W, Hmax, st);
     }
 }
 
@@ -323,7 +356,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.bulk_ok = (n_s % 8) == 0;
     const double fsc = rx->fs / rx->c;
     const double a1 = 2.0 * scan->depth_step * fsc;
-    if (a1 > 16.0) return SUPRA_EINVAL;  // coarser than 16 samples per depth step: no staging window fits
+    if (a1 > 2.0 + 1e-9) return SUPRA_EINVAL;  // depth steps coarser than c / fs: no staging row fits
     H.fsc = (float)fsc;
     H.a1 = (float)a1;
     H.t0fs = (float)(rx->t0 * rx->fs);
@@ -331,7 +364,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.depth_step = (float)scan->depth_step;
     H.inv2f = (float)(1.0 / (2.0 * rx->fnumber));
     H.amin = (float)rx->min_half_aperture;
-    H.win_row = (int)align_up((size_t)std::ceil(a1 * (kDepthTile - 1) + 13.0), 8);
+    H.win_row = row_len_for(a1);
     double ext[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
     for (int e = 0; e < n_el; ++e) {
         ext[0] = std::min(ext[0], probe->elem_pos[3 * e]);
@@ -423,6 +456,18 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
         }
     }
     if (!reg.ok && n_el > 32767) return SUPRA_EINVAL;
+    // lines by decreasing beamforming work, so the heaviest CTAs start first
+    std::vector<int> line_order(n_lines);
+    {
+        std::vector<long long> cost(n_lines, 0);
+        for (int l = 0; l < n_lines; ++l)
+            for (int t = 0; t < NT; ++t) {
+                const short4 bb = box[(size_t)l * NT + t];
+                cost[l] += (long long)(bb.y - bb.x + 1) * (bb.w - bb.z + 1);
+            }
+        for (int l = 0; l < n_lines; ++l) line_order[l] = l;
+        std::stable_sort(line_order.begin(), line_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    }
 
     // ---- envelope + log compression
     const int K = post->fir_taps;
@@ -453,6 +498,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     const size_t o_tk = take(sizeof(int) * NT);
     const size_t o_tf = take(sizeof(float) * NT);
     const size_t o_box = take(sizeof(short4) * box.size());
+    const size_t o_ord = take(sizeof(int) * n_lines);
     auto *plan = new (std::nothrow) supra_plan();
     if (!plan) return SUPRA_ENOMEM;
     cudaGetDevice(&plan->device);
@@ -467,6 +513,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.tile_k = reinterpret_cast<const int *>(b + o_tk);
     H.tile_f = reinterpret_cast<const float *>(b + o_tf);
     H.ap_box = reinterpret_cast<const short4 *>(b + o_box);
+    H.line_order = reinterpret_cast<const int *>(b + o_ord);
     plan->dev = reinterpret_cast<DevPlan *>(b + o_plan);
     plan->host = H;
     cudaError_t err = cudaSuccess;
@@ -476,6 +523,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     err = err ? err : cudaMemcpy(b + o_tk, tile_k.data(), sizeof(int) * NT, cudaMemcpyHostToDevice);
     err = err ? err : cudaMemcpy(b + o_tf, tile_f.data(), sizeof(float) * NT, cudaMemcpyHostToDevice);
     err = err ? err : cudaMemcpy(b + o_box, box.data(), sizeof(short4) * box.size(), cudaMemcpyHostToDevice);
+    err = err ? err : cudaMemcpy(b + o_ord, line_order.data(), sizeof(int) * n_lines, cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
         cudaFree(plan->blob);
         delete plan;
@@ -522,6 +570,7 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].bulk = plan->host.bulk_ok && (reinterpret_cast<uintptr_t>(ch) & 15) == 0;
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
+    L.uniform = 1;
     return launch_das(1, 0, L, plan->host.win_row, 0, static_cast<cudaStream_t>(stream));
 }
 
@@ -578,33 +627,69 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
             }
         }
     }
-    // group consecutive frames of one plan, at most kMaxGroup per group
-    int k = 0;
-    while (k < n) {
-        LaunchGroups L{};
-        int W = 8, ring = kDepthTile, Gmax = 1;
-        while (k < n && L.n_groups < kMaxGroupsPerLaunch) {
-            FrameGroup &g = L.g[L.n_groups];
-            g.plan = plans[k]->dev;
-            g.line0 = L.total_lines;
-            g.n = 0;
-            const supra_plan *p = plans[k];
-            g.bulk = p->host.bulk_ok;
-            while (k < n && plans[k] == p && g.n < kMaxGroup) {
-                if (reinterpret_cast<uintptr_t>(ch[k]) & 15) g.bulk = 0;
-                g.ch[g.n] = ch[k];
-                g.out[g.n] = bm[k];
-                ++g.n;
-                ++k;
-            }
-            Gmax = std::max(Gmax, g.n);
-            W = std::max(W, p->host.win_row);
-            ring = std::max(ring, kDepthTile + p->host.taps - 1);
-            L.total_lines += p->host.n_lines;
-            ++L.n_groups;
+    // Frames of one plan that are adjacent form groups of up to kMaxGroup; one launch
+    // per group size class and row length, up to kMaxGroupsPerLaunch groups each.
+    struct Grp {
+        const supra_plan *p;
+        int first, n;
+    };
+    std::vector<Grp> groups;
+    for (int k = 0; k < n;) {
+        Grp g{plans[k], k, 0};
+        while (k < n && plans[k] == g.p && g.n < kMaxGroup) {
+            ++g.n;
+            ++k;
         }
-        const int rc = launch_das(group_template(Gmax), 1, L, W, ring, st);
-        if (rc) return rc;
+        groups.push_back(g);
+    }
+    for (int Gc : {16, 8, 4, 2, 1}) {
+        for (int Wc : {272, 528}) {
+            LaunchGroups L{};
+            L.uniform = 1;
+            int Hmax = 0;
+            auto flush = [&]() -> int {
+                if (L.n_groups == 0) return SUPRA_OK;
+                const int rc = launch_das(Gc, 1, L, Wc, Hmax, st);
+                L = LaunchGroups{};
+                L.uniform = 1;
+                Hmax = 0;
+                return rc;
+            };
+            for (const Grp &gr : groups) {
+                if (group_template(gr.n) != Gc || gr.p->host.win_row != Wc) continue;
+                FrameGroup &g = L.g[L.n_groups];
+                g.plan = gr.p->dev;
+                g.line0 = L.total_lines;
+                g.n = gr.n;
+                g.bulk = gr.p->host.bulk_ok;
+                for (int f = 0; f < gr.n; ++f) {
+                    if (reinterpret_cast<uintptr_t>(ch[gr.first + f]) & 15) g.bulk = 0;
+                    g.ch[f] = ch[gr.first + f];
+                    g.out[f] = bm[gr.first + f];
+                }
+                g.tma = 0;
+                if (Gc >= 4 && g.bulk) {
+                    // one tensor copy per element for all frames when they sit at a uniform stride
+                    const char *b0 = reinterpret_cast<const char *>(ch[gr.first]);
+                    const long long stride =
+                        gr.n > 1 ? reinterpret_cast<const char *>(ch[gr.first + 1]) - b0 : (long long)gr.p->info.channel_bytes;
+                    bool uni = stride > 0;
+                    for (int f = 2; f < gr.n && uni; ++f)
+                        uni = reinterpret_cast<const char *>(ch[gr.first + f]) - b0 == f * stride;
+                    if (uni) g.tma = make_frame_map(&g.tmap, b0, stride, gr.n, gr.p->host, Wc, Gc) ? 1 : 0;
+                }
+                if (L.n_groups > 0 && L.g[0].plan != g.plan) L.uniform = 0;
+                Hmax = std::max(Hmax, (gr.p->host.taps - 1) / 2);
+                L.total_lines += gr.p->host.n_lines;
+                ++L.n_groups;
+                if (L.n_groups == kMaxGroupsPerLaunch) {
+                    const int rc = flush();
+                    if (rc) return rc;
+                }
+            }
+            const int rc = flush();
+            if (rc) return rc;
+        }
     }
     // scan conversion of the frames with a grid
     ScanLaunch S{};

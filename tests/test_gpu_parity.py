@@ -227,3 +227,27 @@ def test_config2_batch_of_64_matches_oracle_on_first_and_last_frame():
     # and the RF of one frame at full size
     rf = plan.beamform(chs[7]).cpu().numpy()
     assert max_norm_err(rf, oracle.das(p, chs[7].cpu().numpy())) <= RF_TOL
+
+
+def test_contiguous_batch_uses_tensor_copies_and_matches():
+    # frames at a uniform stride are staged with one tensor copy per element for all
+    # frames of a group; results equal the per-frame path and the oracle
+    s = phantom.linear_setup(48, 0.3e-3, 40, 700, fc=7e6, fs=40e6, grid_n=(96, 128))
+    p = s.params()
+    plan = supra.Plan(**p)
+    n = 21                                              # groups of 16 + 5 (a partial group)
+    batch = torch.empty((n, *plan.ch_shape), dtype=torch.int16, device="cuda")
+    for k in range(n):
+        batch[k].copy_(phantom.random_channels(s, 300 + k))
+    outs = supra.bmode_batched([plan] * n, list(batch))
+    for k in (0, 7, 15, 16, 20):
+        single = plan.bmode(batch[k].clone())
+        assert (single.int() - outs[k].int()).abs().max().item() <= 1
+        assert (single == outs[k]).float().mean().item() >= 0.9999
+    ref = oracle.bmode(p, batch[20].cpu().numpy())
+    assert_gray(outs[20].cpu().numpy(), ref, what="frame 20")
+    # lines without a grid, contiguous 8-frame group
+    plan_l = supra.Plan(**dict(p, grid=None))
+    outs_l = supra.bmode_batched([plan_l] * 8, list(batch[:8]))
+    ref_l = oracle.bmode(dict(p, grid=None), batch[3].cpu().numpy())
+    assert_gray(outs_l[3].cpu().numpy(), ref_l, what="lines frame 3")
