@@ -104,7 +104,7 @@ typedef struct supra_rx {
 
 /* Post-processing (Sec. 2 items 3-4). */
 typedef struct supra_post {
-    int32_t fir_taps;           /* odd, 1..127: IQ low-pass length                     */
+    int32_t fir_taps;           /* odd, 1..63: IQ low-pass length                      */
     double fir_cutoff;          /* Hz (Blackman windowed sinc, unit DC gain)           */
     double dyn_range_db;        /* D: displayed dynamic range                          */
     double log_ref;             /* envelope value mapped to 0 dB (gray level 255)      */
@@ -140,7 +140,7 @@ typedef struct supra_plan_info {
  * scan-conversion inverse map).  `grid` may be NULL (no scan conversion: the
  * B-mode output is then the log-compressed lines [n_lines][n_depth]).
  * Errors: SUPRA_EINVAL (c, fs, fnumber <= 0; fc >= fs/2; n_* < 1; line_tx
- * out of range; a non-unit line direction; fir_taps even or > 127;
+ * out of range; a non-unit line direction; fir_taps even or > 63;
  * dyn_range_db <= 0; log_ref <= 0; min_half_aperture <= 0; a scanline layout that does not match
  * `geometry` when a grid is given), SUPRA_ENOMEM, SUPRA_ECUDA.  Runs on the
  * current device and is synchronous. */

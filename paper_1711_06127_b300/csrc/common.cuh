@@ -10,7 +10,8 @@
 namespace supra {
 
 constexpr int kDepthTile = 256;     // depth samples per beamforming tile (one per consumer thread)
-constexpr int kMaxTaps = 127;
+constexpr int kMaxTaps = 63;       // IQ low-pass taps; shorter filters are zero-padded to 63, centred
+constexpr int kTapSlots = 64;      // 63 centred taps + one zero slot
 constexpr int kMaxGroup = 16;       // frames of one plan beamformed together
 
 // Per-line constants (fp32; built from fp64 host geometry).
@@ -44,10 +45,13 @@ struct DevPlan {
     const short4 *ap_box;    // [n_lines * n_tiles] element box (ix_lo, ix_hi, iy_lo, iy_hi), inclusive
     const int *line_order;   // [n_lines] lines by decreasing beamforming work
     // ---- envelope + log compression
-    int taps;                // odd
-    float taps_c[kMaxTaps];  // h_k cos(w (k - H)), demodulation folded into the taps
-    float taps_s[kMaxTaps];  // h_k sin(w (k - H))
+    int taps;                // odd, <= kMaxTaps (the plan's filter length)
+    // Centred form: slot k' = k + 31 - H holds tap k of the plan's filter, the rest are 0,
+    // so every filter is applied as a 63-tap one: iq(i) = sum_k' g_k' rf(i + 31 - k').
+    float taps_c[kTapSlots]; // h cos(w (k' - 31)): demodulation folded into the taps
+    float taps_s[kTapSlots]; // h sin(w (k' - 31))
     float log_a, log_b;      // code = log_a * log2(env) + log_b  (includes the +1/2 of rounding)
+    float log_a2, log_b2;    // the same from |iq|^2: code = log_a2 * log2(|iq|^2) + log_b2
     // ---- scan conversion
     int has_grid, geometry, lines_x, lines_y;
     int gnx, gny, gnz;

@@ -84,6 +84,12 @@ __device__ __forceinline__ u64 add2(u64 a, u64 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // 4D tiled tensor copy global -> shared, completion counted on bar.
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
                                             uint64_t *bar) {
@@ -136,28 +142,49 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // Wait for a phase, giving up after ~budget cycles or when another thread has
 // flagged an abort.
+// try_wait that lets the thread sleep (up to ~20 us) until the phase completes,
+// so waiting warps do not take issue slots from working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > (1LL << 31)) return false;
     }
     return true;
 }
 
-// ring position p of the FIR buffer -> word offset (one pad word every 8: conflict-free blocked reads)
+// Per-frame RF ring of the envelope stage: position u holds the RF of depth
+// i0 - 64 + u (u in [0, kRingLen)): the previous tile's last 64 samples, then the
+// current tile.  Tile outputs are depths o = i0 - 32 + t, t in [0, kTD), and use
+// positions u = 63 + t - k' (k' = 0..63 over the centred taps).  One pad word every
+// 8 positions keeps blocked reads conflict-free.
+constexpr int kHalo = 64;
+constexpr int kLag = 32;
+constexpr int kRingLen = kTD + kHalo;
 __device__ __forceinline__ int ring_addr(int p) { return p + (p >> 3); }
 
 // Shared-memory layout, identical on host and device.
 struct SmemLayout {
     int bars, meta, taps, ring, stage, total, ring_stride;
-    __host__ __device__ SmemLayout(int G, int mode, int W, int H) {
-        bars = 0;                                             // full[kStages], empty[kStages]
+    __host__ __device__ SmemLayout(int G, int mode, int W) {
+        bars = 0;                                             // full[kStages], empty[kStages], abort flag
         meta = 128;                                           // [kStages][kRows] ElemMeta
-        taps = meta + kStages * kRows * (int)sizeof(ElemMeta); // [128] float4 (c, c, s, s)
-        ring = taps + (mode == 1 ? 128 * 16 : 0);
-        ring_stride = ((kTD + 2 * H + ((kTD + 2 * H) >> 3)) + 3) & ~3;
+        taps = meta + kStages * kRows * (int)sizeof(ElemMeta); // [kTapSlots] float4 (c, c, s, s)
+        ring = taps + (mode == 1 ? kTapSlots * 16 : 0);
+        ring_stride = ((kRingLen - 1) + ((kRingLen - 1) >> 3) + 1 + 3) & ~3;
         stage = ring + (mode == 1 ? G * ring_stride * 4 : 0);
         stage = (stage + 127) & ~127;
         total = stage + kStages * kRows * W * 2;
@@ -383,75 +410,130 @@ __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, 
 }
 
 // -------------------------------------------------------------------------------------------------
-// Envelope + log compression of one tile: outputs o = i0 - H + t for t in [0, kTD).
-// Thread -> (frame pair q, block b of BO consecutive outputs); G == 1: one output per thread.
-template <int G>
-__device__ __forceinline__ void fir_log_tile(const DevPlan *P, const FrameGroup &fg, int nf, int line, int i0,
-                                             const float *ring, int RS, const float4 *taps4, int K, int H) {
+// Envelope + log compression of one tile (outputs o = i0 - 32 + t, t in [0, kTD)):
+// iq = sum_k' g_k' rf(o + 31 - k'), code = floor(a2 log2|iq|^2 + b2) clamped to [0, 255]
+// (|iq|^2 = 0 gives -inf and code 0, as env = 0 does).
+__device__ __forceinline__ uint32_t code_of(float q, float a2, float b2) {
+    return (uint32_t)fminf(fmaxf(floorf(fmaf(a2, __log2f(q), b2)), 0.f), 255.f);
+}
+
+__device__ __forceinline__ void store_codes8(uint8_t *row, int o, int nd, const uint32_t (&c)[8]) {
+    if (o >= 0 && o + 8 <= nd && (reinterpret_cast<uintptr_t>(row + o) & 7) == 0) {
+        uint2 v;
+        v.x = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
+        v.y = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
+        *reinterpret_cast<uint2 *>(row + o) = v;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (o + j >= 0 && o + j < nd) row[o + j] = (uint8_t)c[j];
+    }
+}
+
+// G == 16: thread -> frame pair q = tid / 32, outputs t = 8 bq + j (bq = tid % 32, j < 8).
+// Taps go in 8 blocks of 8; the sliding window of 15 ring values is kept in
+// registers and shifted by 8 positions per block (8 new loads per block), and
+// every shared address is the thread's base plus a compile-time offset:
+// for block b and d = j - kk, u = 8 (bq - b) + 63 + d, so
+// ring_addr(u) = 9 bq - 9 b + 63 + d + ((63 + d) >> 3).
+__device__ __forceinline__ void fir_log_tile16(const float *ring, int RS, const float4 *taps4, uint8_t *outA,
+                                               uint8_t *outB, long long row_off, int i0, int nd, float a2, float b2,
+                                               bool wa, bool wb) {
     const int tid = threadIdx.x;
-    const int nd = P->n_depth;
-    const float la = P->log_a, lb = P->log_b;
+    const int q = tid >> 5, bq = tid & 31;
+    const float *ra = ring + (2 * q) * RS + 9 * bq;
+    const float *rb = ring + (2 * q + 1) * RS + 9 * bq;
+    u64 re[8], im[8], win[15];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) re[j] = im[j] = 0ull;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        // window slot d + 7 (d = -7..7); slots d = 1..7 carry over from the previous block
+#pragma unroll
+        for (int d = 7; d >= -7; --d) {
+            if (b > 0 && d >= 1) {
+                win[d + 7] = win[d - 1];   // value of d - 8 in the previous block
+            } else {
+                const int off = -9 * b + 63 + d + ((63 + d) >> 3);
+                win[d + 7] = pack2(ra[off], rb[off]);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const float4 t4 = taps4[8 * b + kk];
+            const u64 C = pack2(t4.x, t4.y), S = pack2(t4.z, t4.w);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const u64 v = win[j - kk + 7];
+                re[j] = fma2(C, v, re[j]);
+                im[j] = fma2(S, v, im[j]);
+            }
+        }
+    }
+    uint32_t ca[8], cb[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const u64 qq = fma2(re[j], re[j], mul2(im[j], im[j]));
+        float qa, qb;
+        unpack2(qq, qa, qb);
+        ca[j] = code_of(qa, a2, b2);
+        cb[j] = code_of(qb, a2, b2);
+    }
+    const int o = i0 - kLag + 8 * bq;
+    if (wa) store_codes8(outA + row_off, o, nd, ca);
+    if (wb) store_codes8(outB + row_off, o, nd, cb);
+}
+
+// Other group sizes: frame pairs with BO = G / 2 outputs per thread (G >= 2), or one
+// output per thread (G == 1); addresses computed at run time.
+template <int G>
+__device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int nf, int line, int i0, int nd,
+                                                     const float *ring, int RS, const float4 *taps4, float a2,
+                                                     float b2) {
+    const int tid = threadIdx.x;
+    const long long row_off = (long long)line * nd;
     if constexpr (G == 1) {
-        const int o = i0 - H + tid;
+        const int o = i0 - kLag + tid;
         if (o < 0 || o >= nd || nf < 1) return;
         float re = 0.f, im = 0.f;
-        for (int k = 0; k < K; ++k) {
-            const float v = ring[ring_addr(tid + 2 * H - k)];
+#pragma unroll 8
+        for (int k = 0; k < kTapSlots; ++k) {
+            const float v = ring[ring_addr(63 + tid - k)];
             const float4 t = taps4[k];
             re = fmaf(t.x, v, re);
             im = fmaf(t.z, v, im);
         }
-        const float env = 2.0f * sqrtf(fmaf(re, re, im * im));
-        float code = 0.f;
-        if (env > 0.f) code = fminf(fmaxf(floorf(fmaf(la, __log2f(env), lb)), 0.f), 255.f);
-        static_cast<uint8_t *>(fg.out[0])[(long long)line * nd + o] = (uint8_t)code;
+        static_cast<uint8_t *>(fg.out[0])[row_off + o] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
     } else {
-        constexpr int NP = G / 2;                  // frame pairs
-        constexpr int TPP = kConsumers / NP;       // threads per pair
-        constexpr int BO = kTD / TPP;              // outputs per thread
+        constexpr int NP = G / 2;
+        constexpr int TPP = kConsumers / NP;
+        constexpr int BO = kTD / TPP;
         const int q = tid / TPP, bq = tid % TPP;
         const int fa = 2 * q, fb = 2 * q + 1;
         const float *ra = ring + fa * RS, *rb = ring + fb * RS;
         u64 re[BO], im[BO];
 #pragma unroll
         for (int j = 0; j < BO; ++j) re[j] = im[j] = 0ull;
-        // window: positions P0 - k + j for j < BO, P0 = bq*BO + 2H; taps zero-padded to a multiple of BO
-        const int P0 = bq * BO + 2 * H;
-        u64 win[2 * BO];
-        for (int k0 = 0; k0 < K; k0 += BO) {
-            // positions P0 - k0 - BO + 1 .. P0 - k0 + BO - 1  ->  win[1 .. 2BO-1]
+        for (int k = 0; k < kTapSlots; ++k) {
+            const float4 t4 = taps4[k];
+            const u64 C = pack2(t4.x, t4.y), S = pack2(t4.z, t4.w);
 #pragma unroll
-            for (int t = 1; t < 2 * BO; ++t) {
-                const int p = P0 - k0 - BO + t;
-                const int a = ring_addr(max(p, 0));
-                win[t] = pack2(ra[a], rb[a]);
-            }
-#pragma unroll
-            for (int kk = 0; kk < BO; ++kk) {
-                const float4 t4 = taps4[k0 + kk];
-                const u64 C = pack2(t4.x, t4.y), S = pack2(t4.z, t4.w);
-#pragma unroll
-                for (int j = 0; j < BO; ++j) {
-                    const u64 v = win[BO - kk + j];   // position P0 - (k0 + kk) + j
-                    re[j] = fma2(C, v, re[j]);
-                    im[j] = fma2(S, v, im[j]);
-                }
+            for (int j = 0; j < BO; ++j) {
+                const int a = ring_addr(63 + bq * BO + j - k);
+                const u64 v = pack2(ra[a], rb[a]);
+                re[j] = fma2(C, v, re[j]);
+                im[j] = fma2(S, v, im[j]);
             }
         }
 #pragma unroll
         for (int j = 0; j < BO; ++j) {
-            const int o = i0 - H + bq * BO + j;
+            const int o = i0 - kLag + bq * BO + j;
             if (o < 0 || o >= nd) continue;
-            float rea, reb, ima, imb;
-            unpack2(re[j], rea, reb);
-            unpack2(im[j], ima, imb);
-            const float ea = 2.0f * sqrtf(fmaf(rea, rea, ima * ima));
-            const float eb = 2.0f * sqrtf(fmaf(reb, reb, imb * imb));
-            float ca = 0.f, cb = 0.f;
-            if (ea > 0.f) ca = fminf(fmaxf(floorf(fmaf(la, __log2f(ea), lb)), 0.f), 255.f);
-            if (eb > 0.f) cb = fminf(fmaxf(floorf(fmaf(la, __log2f(eb), lb)), 0.f), 255.f);
-            if (fa < nf) static_cast<uint8_t *>(fg.out[fa])[(long long)line * nd + o] = (uint8_t)ca;
-            if (fb < nf) static_cast<uint8_t *>(fg.out[fb])[(long long)line * nd + o] = (uint8_t)cb;
+            const u64 qq = fma2(re[j], re[j], mul2(im[j], im[j]));
+            float qa, qb;
+            unpack2(qq, qa, qb);
+            if (fa < nf) static_cast<uint8_t *>(fg.out[fa])[row_off + o] = (uint8_t)code_of(qa, a2, b2);
+            if (fb < nf) static_cast<uint8_t *>(fg.out[fb])[row_off + o] = (uint8_t)code_of(qb, a2, b2);
         }
     }
 }
@@ -462,7 +544,7 @@ __device__ __forceinline__ void fir_log_tile(const DevPlan *P, const FrameGroup 
 // WT: compile-time staged row length (0 = runtime W; G == 1 only).
 template <int G, int MODE, int WT>
 __global__ void __launch_bounds__(kCtaThreads, 2)
-    das_kernel(const __grid_constant__ LaunchGroups L, int Wrt, int Hmax) {
+    das_kernel(const __grid_constant__ LaunchGroups L, int Wrt) {
     constexpr int E = kRows / G;
     extern __shared__ __align__(128) unsigned char smem[];
     const int W = WT ? WT : Wrt;
@@ -473,8 +555,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
     const int nf = min(fg.n, G);
     const int NT = P->n_tiles;
     const int nd = P->n_depth;
-    const int K = P->taps, H = (K - 1) >> 1;
-    const SmemLayout lay(G, MODE, W, Hmax);
+    const SmemLayout lay(G, MODE, W);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
     uint64_t *empty = full + kStages;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kStages);
@@ -495,8 +576,8 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
         fence_mbar_init();
     }
     if (MODE == 1) {
-        for (int k = tid; k < 128; k += kCtaThreads) {
-            const float c = k < K ? P->taps_c[k] : 0.f, s = k < K ? P->taps_s[k] : 0.f;
+        for (int k = tid; k < kTapSlots; k += kCtaThreads) {
+            const float c = P->taps_c[k], s = P->taps_s[k];
             taps4[k] = make_float4(c, c, s, s);
         }
         for (int k = tid; k < G * lay.ring_stride; k += kCtaThreads) ring[k] = 0.f;
@@ -593,15 +674,23 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
                     if (g < nf) static_cast<float *>(fg.out[g])[(long long)line * nd + i] = v[g];
             }
         } else {
-            const int a = ring_addr(2 * H + m);
+            const int a = ring_addr(kHalo + m);
 #pragma unroll
             for (int g = 0; g < G; ++g) ring[g * lay.ring_stride + a] = v[g];
             consumer_sync();
-            fir_log_tile<G>(P, fg, nf, line, i0, ring, lay.ring_stride, taps4, K, H);
+            const float a2 = P->log_a2, b2 = P->log_b2;
+            if constexpr (G == 16) {
+                const int q = m >> 5;
+                fir_log_tile16(ring, lay.ring_stride, taps4, static_cast<uint8_t *>(fg.out[2 * q]),
+                               static_cast<uint8_t *>(fg.out[2 * q + 1]), (long long)line * nd, i0, nd, a2, b2,
+                               2 * q < nf, 2 * q + 1 < nf);
+            } else {
+                fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, a2, b2);
+            }
             consumer_sync();
-            // keep the last 2H RF samples as the next tile's leading halo
-            for (int k = m; k < G * 2 * H; k += kConsumers) {
-                const int g = k / (2 * H), j = k % (2 * H);
+            // keep the last kHalo RF samples as the next tile's leading halo
+            for (int k = m; k < G * kHalo; k += kConsumers) {
+                const int g = k / kHalo, j = k % kHalo;
                 ring[g * lay.ring_stride + ring_addr(j)] = ring[g * lay.ring_stride + ring_addr(kTD + j)];
             }
             consumer_sync();

@@ -9,32 +9,32 @@ namespace supra {
 constexpr int kEnvTile = 256;
 constexpr float kInsideEps = 1e-3f;   // grid points this close (in index units) to the scanned region's edge are inside
 
-// IQ demodulation + low-pass + |.|: env(i) = 2 |sum_k g_k rf(i + H - k)| with the
-// demodulation phase folded into the taps (g_k = h_k e^{j w (k - H)}; the
-// remaining factor e^{-j w i} has unit modulus).
+// IQ demodulation + low-pass + |.|: env(i) = 2 |sum_k' g_k' rf(i + 31 - k')| over the
+// plan's centred 63-slot taps, with the demodulation phase folded into the taps
+// (g_k' = h e^{j w (k' - 31)}; the remaining factor e^{-j w i} has unit modulus).
 __global__ void __launch_bounds__(kEnvTile) envelope_kernel(const DevPlan *__restrict__ P, const float *__restrict__ rf,
                                                             float *__restrict__ env) {
-    __shared__ float x[kEnvTile + 2 * kMaxTaps];
-    __shared__ float tc[kMaxTaps], ts[kMaxTaps];
+    __shared__ float x[kEnvTile + kTapSlots];
+    __shared__ float tc[kTapSlots], ts[kTapSlots];
     const int line = blockIdx.y;
     const int nd = P->n_depth;
-    const int K = P->taps, H = (K - 1) >> 1;
     const int i0 = blockIdx.x * kEnvTile;
     const float *src = rf + (long long)line * nd;
-    for (int k = threadIdx.x; k < K; k += kEnvTile) {
+    for (int k = threadIdx.x; k < kTapSlots; k += kEnvTile) {
         tc[k] = P->taps_c[k];
         ts[k] = P->taps_s[k];
     }
-    for (int k = threadIdx.x; k < kEnvTile + 2 * H; k += kEnvTile) {
-        const int i = i0 - H + k;
+    for (int k = threadIdx.x; k < kEnvTile + kTapSlots - 1; k += kEnvTile) {
+        const int i = i0 - kTapSlots / 2 + k;   // x[k] = rf(i0 - 32 + k)
         x[k] = (i >= 0 && i < nd) ? src[i] : 0.0f;
     }
     __syncthreads();
     const int i = i0 + threadIdx.x;
     if (i >= nd) return;
     float re = 0.0f, im = 0.0f;
-    const float *xp = x + threadIdx.x + 2 * H;   // rf(i + H)
-    for (int k = 0; k < K; ++k) {
+    const float *xp = x + threadIdx.x + kTapSlots - 1;   // rf(i + 31)
+#pragma unroll 8
+    for (int k = 0; k < kTapSlots; ++k) {
         re = fmaf(tc[k], xp[-k], re);
         im = fmaf(ts[k], xp[-k], im);
     }

@@ -142,7 +142,7 @@ bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, 
     const cuuint32_t box[4] = {(cuuint32_t)W / 2, 1, 1, (cuuint32_t)G};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -154,36 +154,36 @@ int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8
 int row_len_for(double a1) { return a1 <= 1.0 + 1e-9 ? 272 : 528; }
 
 template <int G, int MODE, int WT>
-int launch_das_t(const LaunchGroups &L, int W, int Hmax, cudaStream_t st) {
+int launch_das_t(const LaunchGroups &L, int W, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const SmemLayout lay(G, MODE, WT ? WT : W, Hmax);
+    const SmemLayout lay(G, MODE, WT ? WT : W);
     if (lay.total > max_optin) return SUPRA_EINVAL;
     auto kern = das_kernel<G, MODE, WT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess)
         return SUPRA_ECUDA;
-    kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L, W, Hmax);
+    kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L, W);
     return check_cuda(cudaGetLastError());
 }
 
 template <int G, int MODE>
-int launch_das_w(const LaunchGroups &L, int W, int Hmax, cudaStream_t st) {
-    if (W == 272) return launch_das_t<G, MODE, 272>(L, W, Hmax, st);
-    if (W == 528) return launch_das_t<G, MODE, 528>(L, W, Hmax, st);
+int launch_das_w(const LaunchGroups &L, int W, cudaStream_t st) {
+    if (W == 272) return launch_das_t<G, MODE, 272>(L, W, st);
+    if (W == 528) return launch_das_t<G, MODE, 528>(L, W, st);
     return SUPRA_EINVAL;
 }
 
-int launch_das(int G, int mode, const LaunchGroups &L, int W, int Hmax, cudaStream_t st) {
+int launch_das(int G, int mode, const LaunchGroups &L, int W, cudaStream_t st) {
     if (L.total_lines == 0) return SUPRA_OK;
-    if (G == 1) return mode == 0 ? launch_das_t<1, 0, 0>(L, W, Hmax, st) : launch_das_t<1, 1, 0>(L, W, Hmax, st);
+    if (G == 1) return mode == 0 ? launch_das_t<1, 0, 0>(L, W, st) : launch_das_t<1, 1, 0>(L, W, st);
     if (mode == 0) return SUPRA_EINVAL;
     switch (G) {
-        case 2: return launch_das_w<2, 1>(L, W, Hmax, st);
-        case 4: return launch_das_w<4, 1>(L, W, Hmax, st);
-        case 8: return launch_das_w<8, 1>(L, W, Hmax, st);
-        default: return launch_das_w<16, 1>(L, W, Hmax, st);
+        case 2: return launch_das_w<2, 1>(L, W, st);
+        case 4: return launch_das_w<4, 1>(L, W, st);
+        case 8: return launch_das_w<8, 1>(L, W, st);
+        default: return launch_das_w<16, 1>(L, W, st);
     }
 }
 
@@ -476,13 +476,20 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
         const auto h = lowpass_taps(K, post->fir_cutoff, depth_rate);
         const double w = 2.0 * kPi * rx->fc / depth_rate;
         const int Hh = (K - 1) / 2;
+        for (int k = 0; k < kTapSlots; ++k) H.taps_c[k] = H.taps_s[k] = 0.0f;
         for (int k = 0; k < K; ++k) {
-            H.taps_c[k] = (float)(h[k] * std::cos(w * (k - Hh)));
-            H.taps_s[k] = (float)(h[k] * std::sin(w * (k - Hh)));
+            const int kp = k + (kMaxTaps - 1) / 2 - Hh;   // centred slot
+            H.taps_c[kp] = (float)(h[k] * std::cos(w * (k - Hh)));
+            H.taps_s[kp] = (float)(h[k] * std::sin(w * (k - Hh)));
         }
         const double D = post->dyn_range_db;
-        H.log_a = (float)(255.0 / D * 20.0 * std::log10(2.0));
-        H.log_b = (float)(255.0 / D * (D - 20.0 * std::log10(post->log_ref)) + 0.5);
+        const double la = 255.0 / D * 20.0 * std::log10(2.0);
+        const double lb = 255.0 / D * (D - 20.0 * std::log10(post->log_ref)) + 0.5;
+        H.log_a = (float)la;
+        H.log_b = (float)lb;
+        // env = 2 sqrt(q): log2(env) = 1 + log2(q) / 2
+        H.log_a2 = (float)(la / 2.0);
+        H.log_b2 = (float)(la + lb);
     }
 
     // ---- device allocation: one blob for all tables
@@ -571,7 +578,7 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
     L.uniform = 1;
-    return launch_das(1, 0, L, plan->host.win_row, 0, static_cast<cudaStream_t>(stream));
+    return launch_das(1, 0, L, plan->host.win_row, static_cast<cudaStream_t>(stream));
 }
 
 int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream) {
@@ -646,13 +653,11 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
         for (int Wc : {272, 528}) {
             LaunchGroups L{};
             L.uniform = 1;
-            int Hmax = 0;
             auto flush = [&]() -> int {
                 if (L.n_groups == 0) return SUPRA_OK;
-                const int rc = launch_das(Gc, 1, L, Wc, Hmax, st);
+                const int rc = launch_das(Gc, 1, L, Wc, st);
                 L = LaunchGroups{};
                 L.uniform = 1;
-                Hmax = 0;
                 return rc;
             };
             for (const Grp &gr : groups) {
@@ -679,7 +684,6 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
                     if (uni) g.tma = make_frame_map(&g.tmap, b0, stride, gr.n, gr.p->host, Wc, Gc) ? 1 : 0;
                 }
                 if (L.n_groups > 0 && L.g[0].plan != g.plan) L.uniform = 0;
-                Hmax = std::max(Hmax, (gr.p->host.taps - 1) / 2);
                 L.total_lines += gr.p->host.n_lines;
                 ++L.n_groups;
                 if (L.n_groups == kMaxGroupsPerLaunch) {

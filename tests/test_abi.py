@@ -50,7 +50,7 @@ def _params(**over):
 
 @pytest.mark.parametrize("over", [
     dict(c=0.0), dict(c=-1.0), dict(fs=0.0), dict(fc=30e6), dict(fnumber=0.0), dict(min_half_aperture=0.0),
-    dict(fir_taps=62), dict(fir_taps=129), dict(fir_taps=0), dict(dyn_range_db=0.0), dict(log_ref=-1.0),
+    dict(fir_taps=62), dict(fir_taps=65), dict(fir_taps=129), dict(fir_taps=0), dict(dyn_range_db=0.0), dict(log_ref=-1.0),
     dict(n_depth=0), dict(n_samples=0), dict(window=7), dict(depth_step=0.0), dict(depth0=-1e-3),
     dict(line_tx=np.full(64, 64, np.int32)), dict(line_tx=np.full(64, -1, np.int32)),
     dict(line_dir=np.tile([0.0, 0.0, 2.0], (64, 1))), dict(fir_cutoff=25e6), dict(c=float("nan")),
