@@ -30,6 +30,7 @@ struct DevPlan {
     int n_tiles;             // ceil(n_depth / kDepthTile)
     int regular, el_nx, el_ny;   // elements on a row-major nx x ny grid (e = iy * nx + ix)
     int window;
+    float win_a, win_b;      // apodization window A + B cos(pi u)
     int win_row;             // staged samples per element row (multiple of 8)
     int bulk_ok;             // n_s % 8 == 0: rows of 16-byte aligned records may be staged with bulk copies
     float fsc;               // fs / c: samples per metre of path
@@ -64,7 +65,7 @@ struct DevPlan {
 
 // A group of up to kMaxGroup frames beamformed together under one plan.
 struct FrameGroup {
-    CUtensorMap tmap;                    // 4D map (sample pairs, element, transmit, frame) when tma != 0
+    CUtensorMap tmap[4];                 // 4D maps (sample pairs, element, transmit, frame), one per staged width
     const DevPlan *plan;
     int n;                               // frames in the group
     int bulk;                            // rows may be staged with 1D bulk async copies (aligned records)
@@ -74,7 +75,7 @@ struct FrameGroup {
     void *out[kMaxGroup];                // float rf / uint8 bm per frame
 };
 
-constexpr int kMaxGroupsPerLaunch = 48;
+constexpr int kMaxGroupsPerLaunch = 32;
 
 struct LaunchGroups {
     int n_groups;

@@ -6,16 +6,18 @@
 // One CTA owns one scanline of a group of G frames that share a plan and
 // streams the line's depth axis in tiles of kTD = 256 samples, one consumer
 // thread per depth sample.  The CTA is warp-specialized:
-//   * warp 8 (producer) walks the tiles and, for each chunk of E = 32 / G
-//     aperture elements, computes every element's sample window for the tile
-//     and stages that window of all G frames' records into shared memory with
-//     the TMA engine, completing on the stage's "full" mbarrier.  When the
-//     group's frames lie at a uniform stride in memory, one tiled tensor copy
-//     (box: 136 sample pairs x 1 element x 1 transmit x G frames) moves an
-//     element's window for all frames at once and the tensor map's
-//     out-of-bounds fill supplies the zero padding outside the record;
-//     otherwise each of the 32 lanes issues one 1D bulk copy (cp.async.bulk)
-//     per (element, frame) row.
+//   * warp 8 (producer) walks the tiles.  Its 32 lanes take 32 elements of the
+//     tile's aperture box at a time, bound the depths of the tile at which each
+//     element can be inside the F-number aperture, drop elements that never
+//     are, and pack the others E = 32 / G to a stage.  For each element it
+//     stages the record window those depths read -- one of four widths (80,
+//     144, 208 or 272 samples) -- for all G frames with the TMA engine,
+//     completing on the stage's "full" mbarrier.  When the group's frames lie
+//     at a uniform stride in memory, one tiled tensor copy (box: width/2 sample
+//     pairs x 1 element x 1 transmit x G frames) moves the window for all frames
+//     at once and the tensor map's out-of-bounds fill supplies the zero padding
+//     outside the record; otherwise the element's lane issues one 1D bulk copy
+//     (cp.async.bulk) per frame.
 //   * warps 0..7 (consumers) wait on "full", compute the delay, the linear
 //     interpolation weights and the apodization weight of each element once,
 //     apply them to all G frames, and release the buffer on its "empty"
@@ -53,11 +55,18 @@ constexpr int kStages = 4;
 constexpr float kMagic = 8421376.0f; // 2^23 + 2^15
 
 struct ElemMeta {
-    float beta, gamma, ex, ey;   // d.(o_l - x_e), |o_l - x_e|^2, x_e, y_e
+    float beta2, gamma, ex, ey;  // 2 d.(o_l - x_e), |o_l - x_e|^2, x_e, y_e
     int ws;                      // absolute sample index of the row's first staged sample
-    int valid;
-    int pad[2];
+    int ia, ib;                  // depths (absolute indices) this staged window serves
+    int flags;                   // bit 0 valid, bits 1-2 width class, bit 3 (slot 0): last stage of the tile
 };
+__device__ __forceinline__ int meta_valid(const ElemMeta &m) { return m.flags & 1; }
+__device__ __forceinline__ int meta_widx(const ElemMeta &m) { return (m.flags >> 1) & 3; }
+__device__ __forceinline__ int meta_last(const ElemMeta &m) { return (m.flags >> 3) & 1; }
+
+// Staged window widths (samples; multiples of 16) and their frame-row strides in shared memory.
+constexpr int kNumWidths = 4;
+__host__ __device__ constexpr int width_of(int widx) { return 80 + 64 * widx; }   // 80, 144, 208, 272
 
 typedef unsigned long long u64;
 
@@ -103,25 +112,17 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
 // int16 bit pattern (zero-extended) -> float bits of 2^23 + 2^15 + x
 __device__ __forceinline__ uint32_t biased(uint32_t u16) { return (u16 ^ 0x8000u) | 0x4B000000u; }
 
-__device__ __forceinline__ float window_weight(int window, float u) {
-    if (window == SUPRA_WINDOW_HANN) return 0.5f + 0.5f * __cosf(3.14159265358979f * u);
-    if (window == SUPRA_WINDOW_HAMMING) return 0.54f + 0.46f * __cosf(3.14159265358979f * u);
-    return 1.0f;
+// Apodization window A + B cos(pi u): Hann (1/2, 1/2), Hamming (0.54, 0.46), rect (1, 0).
+__device__ __forceinline__ float window_weight(float A, float B, float u) {
+    return fmaf(B, __cosf(3.14159265358979f * u), A);
 }
 
 // |o + r d - q| - r without cancellation: (gamma + 2 r beta) / (|p - q| + r),
-// beta = d.(o - q), gamma = |o - q|^2.
+// beta = d.(o - q), gamma = |o - q|^2.  (0 when p = q = o.)
 __device__ __forceinline__ float path_excess(float r, float beta, float gamma) {
-    float r2 = fmaxf(fmaf(r, r + 2.0f * beta, gamma), 0.0f);
-    float dist = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-    float den = dist + r;
-    float num = fmaf(2.0f * r, beta, gamma);
-    return den > 1e-20f ? __fdividef(num, den) : 0.0f;
-}
-
-__device__ __forceinline__ int box_count(const DevPlan *P, int line, int tile) {
-    short4 b = P->ap_box[line * P->n_tiles + tile];
-    return (b.y - b.x + 1) * (b.w - b.z + 1);
+    const float r2 = fmaxf(fmaf(r, r + 2.0f * beta, gamma), 1e-30f);
+    const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);
+    return __fdividef(fmaf(2.0f * r, beta, gamma), den);
 }
 
 // named barrier among the 256 consumer threads (the producer warp never joins)
@@ -213,36 +214,75 @@ struct ProdConst {
     const int *tile_k;
     const float *tile_f;
     int n_tiles, el_nx, n_depth, n_s, n_el;
-    float depth0, depth_step, fsc, a1, t0fs;
+    float depth0, depth_step, fsc, a1, t0fs, inv2f, amin, xmin, xmax, ymin, ymax;
     __device__ ProdConst(const DevPlan *P)
         : ap_box(P->ap_box), elem(P->elem), tile_k(P->tile_k), tile_f(P->tile_f), n_tiles(P->n_tiles),
           el_nx(P->el_nx), n_depth(P->n_depth), n_s(P->n_s), n_el(P->n_el), depth0(P->depth0),
-          depth_step(P->depth_step), fsc(P->fsc), a1(P->a1), t0fs(P->t0fs) {}
+          depth_step(P->depth_step), fsc(P->fsc), a1(P->a1), t0fs(P->t0fs), inv2f(P->inv2f), amin(P->amin),
+          xmin(P->xmin), xmax(P->xmax), ymin(P->ymin), ymax(P->ymax) {}
 };
 
-// Sample window [ws, ws + W) (ws a multiple of 8) of element slot j of the tile's box.
-// Returns false when j is past the box.
-__device__ __forceinline__ bool element_window(const ProdConst &C, const LineGeo &lg, short4 b, int tile, int j,
-                                               int W, int &e, ElemMeta &m) {
+// Depths of the tile at which element slot j of the box can be inside the
+// aperture: the test max(|x_e - q_x|, |y_e - q_y|) <= a is evaluated every 32
+// depths; the left side minus a changes by at most lip per metre of r (q is a
+// clamp of a point moving along d, a grows at d_z / (2F)), so a depth within
+// 16 samples of a test point can pass only if that point is within
+// lip * 16 * depth_step of passing.  Returns false if no depth can.
+// With `halves`, item j is half j % 2 of box element j / 2 (depth steps coarser
+// than c / (2 fs) make a whole tile's window too wide for one slot).
+__device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo &lg, float lip, short4 b, int tile,
+                                              bool halves, int j, int &e, float4 &xe, int &ia, int &ib) {
     const int nbx = b.y - b.x + 1, nby = b.w - b.z + 1;
-    if (j >= nbx * nby) return false;
-    e = (b.z + j / nbx) * C.el_nx + b.x + j % nbx;
-    const float4 xe = __ldg(&C.elem[e]);
+    const int je = halves ? j >> 1 : j;
+    if (je >= nbx * nby) return false;
+    e = (b.z + je / nbx) * C.el_nx + b.x + je % nbx;
+    xe = __ldg(&C.elem[e]);
+    int i0 = tile * kTD;
+    int i1 = min(i0 + kTD - 1, C.n_depth - 1);
+    if (halves) {
+        if (j & 1) i0 += kTD / 2;
+        else i1 = min(i1, i0 + kTD / 2 - 1);
+        if (i0 > i1) return false;
+    }
+    const float margin = lip * 16.0f * C.depth_step * 1.001f + 1e-9f;
+    int first = -1, last = -1;
+#pragma unroll
+    for (int k = 0; k <= kTD / 32; ++k) {
+        const int i = min(i0 + 32 * k, i1);
+        if (k > 0 && i0 + 32 * (k - 1) >= i1) break;
+        const float r = C.depth0 + (float)i * C.depth_step;
+        const float px = fmaf(r, lg.dx, lg.ox), py = fmaf(r, lg.dy, lg.oy), pz = fmaf(r, lg.dz, lg.oz);
+        const float qx = fminf(fmaxf(px, C.xmin), C.xmax), qy = fminf(fmaxf(py, C.ymin), C.ymax);
+        const float a = fmaxf(pz * C.inv2f, C.amin);
+        const float g = fmaxf(fabsf(xe.x - qx), fabsf(xe.y - qy)) - a;
+        if (g <= margin) {
+            if (first < 0) first = k;
+            last = k;
+        }
+    }
+    if (first < 0) return false;
+    ia = max(i0, i0 + 32 * first - 16);
+    ib = min(i1, i0 + 32 * last + 16);
+    return true;
+}
+
+// Record window of depths [ia, ib] for element e: start ws (a multiple of 8) and
+// the width class that covers every sample those depths interpolate.
+__device__ __forceinline__ void element_window(const ProdConst &C, const LineGeo &lg, int tile, int ia, int ib,
+                                               float4 xe, ElemMeta &m) {
     const float mx = lg.ox - xe.x, my = lg.oy - xe.y, mz = lg.oz - xe.z;
     const float beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
     const float gamma = mx * mx + my * my + mz * mz;
-    const int i0 = tile * kTD;
-    const int i1 = min(i0 + kTD - 1, C.n_depth - 1);
-    const float r0 = C.depth0 + (float)i0 * C.depth_step;
-    const float r1 = C.depth0 + (float)i1 * C.depth_step;
+    const int i0 = tile * kTD;   // the tile's delay base is at its first depth
+    const float r0 = C.depth0 + (float)ia * C.depth_step;
+    const float r1 = C.depth0 + (float)ib * C.depth_step;
     const int kt = __ldg(&C.tile_k[tile]);
     const float ft = __ldg(&C.tile_f[tile]);
-    const float s0 = ft + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * C.fsc;
-    const float s1 =
-        ft + C.a1 * (float)(i1 - i0) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * C.fsc;
+    const float s0 = ft + C.a1 * (float)(ia - i0) + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * C.fsc;
+    const float s1 = ft + C.a1 * (float)(ib - i0) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * C.fsc;
     float lo = fminf(s0, s1), hi = fmaxf(s0, s1);
     // The two-way path is convex in r: its maximum is at an end, its minimum may be
-    // inside the tile; bound that minimum by the sum of the two paths' minima.
+    // inside; bound that minimum by the sum of the two paths' minima.
     if ((-beta > r0 && -beta < r1) || (-lg.bt > r0 && -lg.bt < r1)) {
         const float re = fminf(fmaxf(-beta, r0), r1), rt = fminf(fmaxf(-lg.bt, r0), r1);
         const float de = sqrtf(fmaxf(fmaf(re, re + 2.0f * beta, gamma), 0.0f));
@@ -250,115 +290,94 @@ __device__ __forceinline__ bool element_window(const ProdConst &C, const LineGeo
         lo = fminf(lo, (de + dtp) * C.fsc - C.t0fs - (float)kt);
     }
     const int lo_i = kt + (int)floorf(lo) - 1;
-    const int ws = (lo_i >> 3) << 3;   // 16-byte aligned window start
-    if (kt + (int)floorf(hi) + 2 > ws + W - 1) set_status(SUPRA_EINTERNAL);
-    m.beta = beta;
+    const int ws = (lo_i >> 3) << 3;                              // 16-byte aligned window start
+    const int need = kt + (int)floorf(hi) + 2 - ws;               // samples up to x1 of the last depth
+    int widx = need <= width_of(0) ? 0 : (need - width_of(0) + 63) / 64;   // smallest width >= need
+    if (widx >= kNumWidths) {
+        set_status(SUPRA_EINTERNAL);
+        widx = kNumWidths - 1;
+    }
+    m.beta2 = beta + beta;
     m.gamma = gamma;
     m.ex = xe.x;
     m.ey = xe.y;
     m.ws = ws;
-    m.valid = 1;
-    m.pad[0] = m.pad[1] = 0;
-    return true;
+    m.ia = ia;
+    m.ib = ib;
+    m.flags = 1 | (widx << 1);
 }
 
-// Producer, one stage.  Shared layout of a stage: rows [element slot][frame][W].
-// Every lane arrives once on `full` (count kRows).
+// Stages the element's window of all frames into slot `slot` of a stage (frame
+// rows of width_of(widx) samples, packed).  Returns the bytes that will land.
 template <int G>
-__device__ __forceinline__ void produce_stage(const ProdConst &C, const FrameGroup &fg, int nf, const LineGeo &lg,
-                                              int line, int tile, int chunk, int16_t *sbuf, ElemMeta *meta,
-                                              uint64_t *full, int W) {
-    constexpr int E = kRows / G;
-    const int lane = threadIdx.x & 31;
-    const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
+__device__ __forceinline__ uint32_t stage_element(const ProdConst &C, const FrameGroup &fg, int nf, const LineGeo &lg,
+                                                  int e, const ElemMeta &m, int16_t *slot_base, uint64_t *full) {
+    const int wsamp = width_of(meta_widx(m));
     if (fg.tma) {
-        // lane ej < E: one tensor copy of the element's window for all G frames
-        if (lane < E) {
-            int e;
-            ElemMeta m;
-            if (element_window(C, lg, b, tile, chunk * E + lane, W, e, m)) {
-                meta[lane] = m;
-                mbar_arrive_expect_tx(full, (uint32_t)(G * W * 2));
-                tma_load_4d(sbuf + lane * G * W, &fg.tmap, m.ws >> 1, e, lg.tx, 0, full);
-                return;
-            }
-            meta[lane].valid = 0;
-        }
-        mbar_arrive_expect_tx(full, 0);
-        return;
+        tma_load_4d(slot_base, &fg.tmap[meta_widx(m)], m.ws >> 1, e, lg.tx, 0, full);
+        return (uint32_t)(G * wsamp * 2);
     }
-    // fallback: lane l stages row l = (element slot l / G, frame l % G) with one 1D bulk copy
-    const int ej = lane / G, f = lane % G;
-    int16_t *row = sbuf + lane * W;
-    int e;
-    ElemMeta m;
-    if (!element_window(C, lg, b, tile, chunk * E + ej, W, e, m)) {
-        if (f == 0) meta[ej].valid = 0;
-        mbar_arrive_expect_tx(full, 0);
-        return;
-    }
-    if (f == 0) meta[ej] = m;
-    if (f >= nf) {
-        mbar_arrive_expect_tx(full, 0);
-        return;
-    }
-    const int ws = m.ws;
-    const int n_s = C.n_s;
-    const int c0 = max(ws, 0), c1 = min(ws + W, n_s);
+    const int ws = m.ws, n_s = C.n_s;
+    const int c0 = max(ws, 0), c1 = min(ws + wsamp, n_s);
     const long long rec = ((long long)lg.tx * C.n_el + e) * (long long)n_s;
-    if (c0 > ws || c1 < ws + W) {   // zero padding outside the record
-        const int a_end = min(c0, ws + W) - ws;
-        for (int k = 0; k < a_end; ++k) row[k] = 0;
-        for (int k = max(c1, c0) - ws; k < W; ++k) row[k] = 0;
-    }
-    if (fg.bulk) {
-        const uint32_t bytes = c1 > c0 ? (uint32_t)(c1 - c0) * 2u : 0u;
-        mbar_arrive_expect_tx(full, bytes);
-        if (bytes) {
-            fence_proxy_async_smem();
-            bulk_g2s(row + (c0 - ws), fg.ch[f] + rec + c0, bytes, full);
+    uint32_t total = 0;
+    for (int f = 0; f < nf; ++f) {
+        int16_t *row = slot_base + f * wsamp;
+        if (c0 > ws || c1 < ws + wsamp) {   // zero padding outside the record
+            const int a_end = min(c0, ws + wsamp) - ws;
+            for (int k = 0; k < a_end; ++k) row[k] = 0;
+            for (int k = max(c1, c0) - ws; k < wsamp; ++k) row[k] = 0;
         }
-    } else {
-        const int16_t *src = fg.ch[f] + rec;
-        for (int k = c0; k < c1; ++k) row[k - ws] = src[k];
-        mbar_arrive_expect_tx(full, 0);
+        if (fg.bulk) {
+            if (c1 > c0) {
+                fence_proxy_async_smem();
+                bulk_g2s(row + (c0 - ws), fg.ch[f] + rec + c0, (uint32_t)(c1 - c0) * 2u, full);
+                total += (uint32_t)(c1 - c0) * 2u;
+            }
+        } else {
+            const int16_t *src = fg.ch[f] + rec;
+            for (int k = c0; k < c1; ++k) row[k - ws] = src[k];
+        }
     }
+    return total;
 }
 
 // -------------------------------------------------------------------------------------------------
-// Consumer: all E element slots of one stage for this thread's depth sample.
+// Consumer: the element slots of one stage for this thread's depth sample.
 struct Geo {
-    float w0, w1;
+    float w0, w1, w;
     int idx;
     bool go;   // some lane of the warp is inside this element's aperture
 };
 
-__device__ __forceinline__ Geo element_geo(const ElemMeta &md, int W, float r, float qx, float qy, float inv_a,
-                                           float base, int kt, bool use_y, int window, float fsc) {
+__device__ __forceinline__ Geo element_geo(const ElemMeta &md, int i, float r, float qx, float qy, float inv_a,
+                                           float base, int kt, bool use_y, float wa, float wb, float fsc) {
     Geo g;
     const float ux = (md.ex - qx) * inv_a;
-    bool in = fabsf(ux) <= 1.0f;
-    float w = window_weight(window, ux);
+    bool in = fabsf(ux) <= 1.0f && i >= md.ia && i <= md.ib;
+    float w = window_weight(wa, wb, ux);
     if (use_y) {
         const float uy = (md.ey - qy) * inv_a;
         in = in && fabsf(uy) <= 1.0f;
-        w *= window_weight(window, uy);
+        w *= window_weight(wa, wb, uy);
     }
-    g.go = __any_sync(0xffffffffu, in) && md.valid;
+    g.go = __any_sync(0xffffffffu, in) && meta_valid(md);
     w = in ? w : 0.0f;
-    const float s = base + path_excess(r, md.beta, md.gamma) * fsc;
+    const float r2 = fmaxf(fmaf(r, r + md.beta2, md.gamma), 1e-30f);   // |p - x_e|^2
+    const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);            // |p - x_e| + r
+    const float s = fmaf(__fdividef(fmaf(r, md.beta2, md.gamma), den), fsc, base);
     const float fl = floorf(s);
+    g.w = w;
     g.w1 = w * (s - fl);
     g.w0 = w - g.w1;
-    g.idx = min(max(kt + (int)fl - md.ws, 0), W - 2);
+    g.idx = min(max(kt + (int)fl - md.ws, 0), width_of(kNumWidths - 1) - 2);
     return g;
 }
 
-// Frame loop of one element: rows [frame][W] starting at `rows`.
-template <int G, int WT>
-__device__ __forceinline__ void element_frames(const int16_t *rows, int Wrt, const Geo &g,
-                                               u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1) {
-    const int W = WT ? WT : Wrt;
+// Frame loop of one element: frame f's row starts at rows + f * FS.
+template <int G, int FS>
+__device__ __forceinline__ void element_frames(const int16_t *rows, const Geo &g, u64 (&acc2)[G / 2 > 0 ? G / 2 : 1],
+                                               float &acc1) {
     const uint16_t *row = reinterpret_cast<const uint16_t *>(rows) + g.idx;
     if constexpr (G == 1) {
         const float x0 = __uint_as_float(biased(row[0])) - kMagic;
@@ -368,8 +387,8 @@ __device__ __forceinline__ void element_frames(const int16_t *rows, int Wrt, con
         const u64 W0 = pack2(g.w0, g.w0), W1 = pack2(g.w1, g.w1), NB = pack2(-kMagic, -kMagic);
 #pragma unroll
         for (int q = 0; q < G / 2; ++q) {
-            const uint16_t *ra = row + (2 * q) * W;
-            const uint16_t *rb = row + (2 * q + 1) * W;
+            const uint16_t *ra = row + (2 * q) * FS;
+            const uint16_t *rb = row + (2 * q + 1) * FS;
             const u64 f0 = add2(pack2u(biased(ra[0]), biased(rb[0])), NB);
             const u64 f1 = add2(pack2u(biased(ra[1]), biased(rb[1])), NB);
             acc2[q] = fma2(W1, f1, fma2(W0, f0, acc2[q]));
@@ -377,34 +396,54 @@ __device__ __forceinline__ void element_frames(const int16_t *rows, int Wrt, con
     }
 }
 
-template <int G, int WT>
-__device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int Wrt,
-                                              float r, float qx, float qy, float inv_a, float base, int kt,
-                                              bool use_y, int window, float fsc, u64 (&acc2)[G / 2 > 0 ? G / 2 : 1],
-                                              float &acc1, float &wsum) {
+template <int G>
+__device__ __forceinline__ void element_frames_w(const int16_t *rows, int widx, const Geo &g,
+                                                 u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1) {
+    if constexpr (G == 1) {
+        element_frames<1, 0>(rows, g, acc2, acc1);
+    } else {
+        switch (widx) {
+            case 0: element_frames<G, width_of(0)>(rows, g, acc2, acc1); break;
+            case 1: element_frames<G, width_of(1)>(rows, g, acc2, acc1); break;
+            case 2: element_frames<G, width_of(2)>(rows, g, acc2, acc1); break;
+            default: element_frames<G, width_of(3)>(rows, g, acc2, acc1); break;
+        }
+    }
+}
+
+constexpr int kSlotSamples = width_of(kNumWidths - 1);   // samples per frame row reserved in a slot
+
+template <int G>
+__device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int i, float r,
+                                              float qx, float qy, float inv_a, float base, int kt,
+                                              bool use_y, float wa, float wb, float fsc,
+                                              u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1, float &wsum) {
     constexpr int E = kRows / G;
-    const int W = WT ? WT : Wrt;
     if constexpr (E <= 4) {
         // geometry of every slot first (independent chains), then the frame loops
         Geo g[E];
+        int widx[E];
 #pragma unroll
-        for (int ej = 0; ej < E; ++ej)
-            g[ej] = element_geo(meta[ej], W, r, qx, qy, inv_a, base, kt, use_y, window, fsc);
+        for (int ej = 0; ej < E; ++ej) {
+            const ElemMeta md = meta[ej];
+            widx[ej] = meta_widx(md);
+            g[ej] = element_geo(md, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc);
+        }
 #pragma unroll
         for (int ej = 0; ej < E; ++ej) {
             if (!g[ej].go) continue;
-            element_frames<G, WT>(sbuf + ej * G * W, W, g[ej], acc2, acc1);
-            wsum += g[ej].w0 + g[ej].w1;
+            element_frames_w<G>(sbuf + ej * G * kSlotSamples, widx[ej], g[ej], acc2, acc1);
+            wsum += g[ej].w;
         }
     } else {
 #pragma unroll 2
         for (int ej = 0; ej < E; ++ej) {
             const ElemMeta md = meta[ej];
-            if (!md.valid) break;
-            const Geo g = element_geo(md, W, r, qx, qy, inv_a, base, kt, use_y, window, fsc);
+            if (!meta_valid(md)) break;   // valid slots are a prefix
+            const Geo g = element_geo(md, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc);
             if (!g.go) continue;
-            element_frames<G, WT>(sbuf + ej * G * W, W, g, acc2, acc1);
-            wsum += g.w0 + g.w1;
+            element_frames_w<G>(sbuf + ej * G * kSlotSamples, meta_widx(md), g, acc2, acc1);
+            wsum += g.w;
         }
     }
 }
@@ -541,13 +580,10 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // -------------------------------------------------------------------------------------------------
 // MODE 0: write RF (float [n_lines][n_depth] per frame).
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
-// WT: compile-time staged row length (0 = runtime W; G == 1 only).
-template <int G, int MODE, int WT>
-__global__ void __launch_bounds__(kCtaThreads, 2)
-    das_kernel(const __grid_constant__ LaunchGroups L, int Wrt) {
+template <int G, int MODE>
+__global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_constant__ LaunchGroups L) {
     constexpr int E = kRows / G;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int W = WT ? WT : Wrt;
     int gi, line;
     locate_item(L, blockIdx.x, gi, line);
     const FrameGroup &fg = L.g[gi];
@@ -555,7 +591,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
     const int nf = min(fg.n, G);
     const int NT = P->n_tiles;
     const int nd = P->n_depth;
-    const SmemLayout lay(G, MODE, W);
+    const SmemLayout lay(G, MODE, kSlotSamples);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
     uint64_t *empty = full + kStages;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kStages);
@@ -563,13 +599,13 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
     float4 *taps4 = reinterpret_cast<float4 *>(smem + lay.taps);
     float *ring = reinterpret_cast<float *>(smem + lay.ring);
     int16_t *stages = reinterpret_cast<int16_t *>(smem + lay.stage);
-    const int stage_elems = kRows * W;
+    constexpr int stage_elems = kRows * kSlotSamples;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], kRows);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumers / 32);
         }
         *abort_flag = 0;
@@ -588,19 +624,81 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
     if (warp == kConsumers / 32) {
         // ------------------------------------------------------------------ producer warp
         const ProdConst C(P);
-        int n = 0;
+        const int lane = tid & 31;
+        const float lip = fmaxf(fabsf(lg.dx), fabsf(lg.dy)) + fabsf(lg.dz) * C.inv2f;
+        const bool halves = C.a1 > 1.0f + 1e-6f;
+        int n = 0;              // stages issued
+        int slot = 0;           // filled slots of stage n
+        uint32_t bytes = 0;     // bytes of stage n this lane has put in flight
         bool ok = true;
+        auto acquire = [&]() -> bool {   // stage n's buffer is free once consumers released stage n - kStages
+            if (n < kStages) return true;
+            const int sb = n % kStages;
+            return __all_sync(0xffffffffu, wait_phase(&empty[sb], (uint32_t)(((n / kStages) - 1) & 1), abort_flag));
+        };
+        auto finalize = [&](bool last) {
+            const int sb = n % kStages;
+            ElemMeta *meta = metas + sb * kRows;
+            if (lane >= slot && lane < E) meta[lane].flags = 0;
+            __syncwarp();
+            if (lane == 0 && last) meta[0].flags |= 8;
+            const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+            __syncwarp();
+            if (lane == 0) mbar_arrive_expect_tx(&full[sb], total);
+            bytes = 0;
+            slot = 0;
+            ++n;
+        };
         for (int tile = 0; tile < NT && ok; ++tile) {
-            const int nch = (box_count(P, line, tile) + E - 1) / E;
-            for (int c = 0; c < nch; ++c, ++n) {
-                const int s = n % kStages;
-                if (n >= kStages &&
-                    !__all_sync(0xffffffffu, wait_phase(&empty[s], (uint32_t)(((n / kStages) - 1) & 1), abort_flag))) {
-                    ok = false;
-                    break;
+            const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
+            const int nbox = (b.y - b.x + 1) * (b.w - b.z + 1) * (halves ? 2 : 1);
+            // pass 1: how many elements can be active in this tile
+            int nact = 0;
+            for (int jb = 0; jb < nbox; jb += 32) {
+                int e, ia, ib;
+                float4 xe;
+                const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                nact += __popc(__ballot_sync(0xffffffffu, a));
+            }
+            const int nst = max(1, (nact + E - 1) / E);
+            int emitted = 0;
+            // pass 2: stage them, E per stage
+            for (int jb = 0; jb < nbox && ok; jb += 32) {
+                int e, ia, ib;
+                float4 xe;
+                const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                ElemMeta m;
+                if (a) element_window(C, lg, tile, ia, ib, xe, m);
+                uint32_t mask = __ballot_sync(0xffffffffu, a);
+                while (mask) {
+                    if (slot == 0 && !acquire()) {
+                        ok = false;
+                        break;
+                    }
+                    const int take = min(E - slot, __popc(mask));
+                    const int rank = __popc(mask & ((1u << lane) - 1u));
+                    const bool mine = ((mask >> lane) & 1u) && rank < take;
+                    if (mine) {
+                        const int sb = n % kStages;
+                        ElemMeta *meta = metas + sb * kRows;
+                        meta[slot + rank] = m;
+                        bytes += stage_element<G>(C, fg, nf, lg, e, m,
+                                                  stages + sb * stage_elems + (slot + rank) * G * kSlotSamples,
+                                                  &full[sb]);
+                    }
+                    // drop the `take` lowest lanes of the mask
+                    for (int t = 0; t < take; ++t) mask &= mask - 1u;
+                    slot += take;
+                    if (slot == E) finalize(++emitted == nst);
                 }
-                produce_stage<G>(C, fg, nf, lg, line, tile, c, stages + s * stage_elems, metas + s * kRows,
-                                 &full[s], W);
+            }
+            if (ok && (slot > 0 || emitted == 0)) {
+                if (slot == 0 && !acquire()) {
+                    ok = false;
+                } else {
+                    ++emitted;
+                    finalize(true);
+                }
             }
         }
         if (!ok) {
@@ -616,9 +714,10 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
     // ---------------------------------------------------------------------- consumer warps
     const int m = tid;
     const bool use_y = P->el_ny > 1 || P->ymax > P->ymin;
-    const int window = P->window;
+    const float wa = P->win_a, wb = P->win_b;
     const float fsc = P->fsc;
-    int n = 0;
+    int sb = 0;                 // stage buffer of the next stage
+    uint32_t parity = 0;        // its full-barrier phase parity
     bool aborted = false;
     for (int tile = 0; tile < NT + (MODE == 1 ? 1 : 0); ++tile) {
         const int i0 = tile * kTD;
@@ -635,21 +734,28 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
             const float inv_a = 1.0f / fmaxf(pz * P->inv2f, P->amin);
             const float base = P->tile_f[tile] + P->a1 * (float)m + path_excess(r, lg.bt, lg.gt) * fsc;
             const int kt = P->tile_k[tile];
-            const int nch = (box_count(P, line, tile) + E - 1) / E;
-            for (int c = 0; c < nch; ++c, ++n) {
-                const int s = n % kStages;
-                // warp-uniform decision: consume_stage uses warp votes
-                if (!aborted &&
-                    !__all_sync(0xffffffffu, wait_phase(&full[s], (uint32_t)((n / kStages) & 1), abort_flag))) {
-                    aborted = true;
-                    *abort_flag = 1;
-                    set_status(SUPRA_ETIMEOUT);
+            for (;;) {
+                bool ok = !aborted && mbar_try_wait_sleep(&full[sb], parity);
+                if (!aborted && !__all_sync(0xffffffffu, ok)) {
+                    ok = __all_sync(0xffffffffu, ok || wait_phase(&full[sb], parity, abort_flag));
+                    if (!ok) {
+                        aborted = true;
+                        *abort_flag = 1;
+                        set_status(SUPRA_ETIMEOUT);
+                    }
                 }
-                if (!aborted)
-                    consume_stage<G, WT>(stages + s * stage_elems, metas + s * kRows, W, r, qx, qy, inv_a, base,
-                                         kt, use_y, window, fsc, acc2, acc1, wsum);
+                if (aborted) break;
+                const ElemMeta *meta = metas + sb * kRows;
+                const int last = meta_last(meta[0]);
+                consume_stage<G>(stages + sb * stage_elems, meta, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc,
+                                 acc2, acc1, wsum);
                 __syncwarp();
-                if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+                if ((tid & 31) == 0) mbar_arrive(&empty[sb]);
+                if (++sb == kStages) {
+                    sb = 0;
+                    parity ^= 1u;
+                }
+                if (last) break;
             }
         }
         if (consumer_sync_or(aborted ? 1 : 0)) return;

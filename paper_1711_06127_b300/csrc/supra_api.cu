@@ -133,13 +133,13 @@ EncodeTiledFn encode_tiled() {
 
 // 4D map over a group's records viewed as int32 sample pairs: (n_s / 2, n_el, n_tx, frames),
 // box (W / 2, 1, 1, G); reads outside the records fill zeros.
-bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, int frames, const DevPlan &H, int W,
-                    int G) {
+bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, int frames, const DevPlan &H,
+                    int width, int G) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || frame_stride <= 0 || (frame_stride & 15)) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)H.n_s / 2, (cuuint64_t)H.n_el, (cuuint64_t)H.n_tx, (cuuint64_t)frames};
     const cuuint64_t strides[3] = {(cuuint64_t)H.n_s * 2, (cuuint64_t)H.n_s * 2 * H.n_el, (cuuint64_t)frame_stride};
-    const cuuint32_t box[4] = {(cuuint32_t)W / 2, 1, 1, (cuuint32_t)G};
+    const cuuint32_t box[4] = {(cuuint32_t)width / 2, 1, 1, (cuuint32_t)G};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, const_cast<void *>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -149,41 +149,30 @@ bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, 
 // kernel choice for a frame group size
 int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
 
-// Staged row length for a plan: compile-time 272 (depth step <= c/(2 fs)) or 528
-// (<= c/fs) samples, enough for a 256-sample depth tile plus alignment slack.
-int row_len_for(double a1) { return a1 <= 1.0 + 1e-9 ? 272 : 528; }
-
-template <int G, int MODE, int WT>
-int launch_das_t(const LaunchGroups &L, int W, cudaStream_t st) {
+template <int G, int MODE>
+int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const SmemLayout lay(G, MODE, WT ? WT : W);
+    const SmemLayout lay(G, MODE, kSlotSamples);
     if (lay.total > max_optin) return SUPRA_EINVAL;
-    auto kern = das_kernel<G, MODE, WT>;
+    auto kern = das_kernel<G, MODE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess)
         return SUPRA_ECUDA;
-    kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L, W);
+    kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L);
     return check_cuda(cudaGetLastError());
 }
 
-template <int G, int MODE>
-int launch_das_w(const LaunchGroups &L, int W, cudaStream_t st) {
-    if (W == 272) return launch_das_t<G, MODE, 272>(L, W, st);
-    if (W == 528) return launch_das_t<G, MODE, 528>(L, W, st);
-    return SUPRA_EINVAL;
-}
-
-int launch_das(int G, int mode, const LaunchGroups &L, int W, cudaStream_t st) {
+int launch_das(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
     if (L.total_lines == 0) return SUPRA_OK;
-    if (G == 1) return mode == 0 ? launch_das_t<1, 0, 0>(L, W, st) : launch_das_t<1, 1, 0>(L, W, st);
+    if (G == 1) return mode == 0 ? launch_das_t<1, 0>(L, st) : launch_das_t<1, 1>(L, st);
     if (mode == 0) return SUPRA_EINVAL;
     switch (G) {
-        case 2: return launch_das_w<2, 1>(L, W, st);
-        case 4: return launch_das_w<4, 1>(L, W, st);
-        case 8: return launch_das_w<8, 1>(L, W, st);
-        default: return launch_das_w<16, 1>(L, W, st);
+        case 2: return launch_das_t<2, 1>(L, st);
+        case 4: return launch_das_t<4, 1>(L, st);
+        case 8: return launch_das_t<8, 1>(L, st);
+        default: return launch_das_t<16, 1>(L, st);
     }
 }
 
@@ -353,6 +342,8 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.n_s = n_s;
     H.n_tiles = (n_d + kDepthTile - 1) / kDepthTile;
     H.window = rx->window;
+    H.win_a = rx->window == SUPRA_WINDOW_HANN ? 0.5f : rx->window == SUPRA_WINDOW_HAMMING ? 0.54f : 1.0f;
+    H.win_b = rx->window == SUPRA_WINDOW_HANN ? 0.5f : rx->window == SUPRA_WINDOW_HAMMING ? 0.46f : 0.0f;
     H.bulk_ok = (n_s % 8) == 0;
     const double fsc = rx->fs / rx->c;
     const double a1 = 2.0 * scan->depth_step * fsc;
@@ -364,7 +355,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.depth_step = (float)scan->depth_step;
     H.inv2f = (float)(1.0 / (2.0 * rx->fnumber));
     H.amin = (float)rx->min_half_aperture;
-    H.win_row = row_len_for(a1);
+    H.win_row = kSlotSamples;
     double ext[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
     for (int e = 0; e < n_el; ++e) {
         ext[0] = std::min(ext[0], probe->elem_pos[3 * e]);
@@ -578,7 +569,7 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
     L.uniform = 1;
-    return launch_das(1, 0, L, plan->host.win_row, static_cast<cudaStream_t>(stream));
+    return launch_das(1, 0, L, static_cast<cudaStream_t>(stream));
 }
 
 int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream) {
@@ -650,18 +641,18 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
         groups.push_back(g);
     }
     for (int Gc : {16, 8, 4, 2, 1}) {
-        for (int Wc : {272, 528}) {
+        {
             LaunchGroups L{};
             L.uniform = 1;
             auto flush = [&]() -> int {
                 if (L.n_groups == 0) return SUPRA_OK;
-                const int rc = launch_das(Gc, 1, L, Wc, st);
+                const int rc = launch_das(Gc, 1, L, st);
                 L = LaunchGroups{};
                 L.uniform = 1;
                 return rc;
             };
             for (const Grp &gr : groups) {
-                if (group_template(gr.n) != Gc || gr.p->host.win_row != Wc) continue;
+                if (group_template(gr.n) != Gc) continue;
                 FrameGroup &g = L.g[L.n_groups];
                 g.plan = gr.p->dev;
                 g.line0 = L.total_lines;
@@ -681,7 +672,11 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
                     bool uni = stride > 0;
                     for (int f = 2; f < gr.n && uni; ++f)
                         uni = reinterpret_cast<const char *>(ch[gr.first + f]) - b0 == f * stride;
-                    if (uni) g.tma = make_frame_map(&g.tmap, b0, stride, gr.n, gr.p->host, Wc, Gc) ? 1 : 0;
+                    if (uni) {
+                        g.tma = 1;
+                        for (int w = 0; w < kNumWidths && g.tma; ++w)
+                            g.tma = make_frame_map(&g.tmap[w], b0, stride, gr.n, gr.p->host, width_of(w), Gc) ? 1 : 0;
+                    }
                 }
                 if (L.n_groups > 0 && L.g[0].plan != g.plan) L.uniform = 0;
                 L.total_lines += gr.p->host.n_lines;
