@@ -210,6 +210,26 @@ SUPRA_API int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *ou
 SUPRA_API int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t *const *ch, uint8_t *const *out,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* supra_bmode for callers that may not allocate device memory.  The paper has
+ * no counterpart: it exists because some callers cannot provide the device
+ * workspace supra_bmode needs -- e.g. a real-time acquisition loop that must
+ * not call cudaMalloc after start-up (it can synchronize the device and has no
+ * latency bound), or a host whose device memory belongs to another
+ * framework's pool.  It runs the same kernels as supra_bmode, taking the
+ * scratch for the frame's log-compressed lines from a fixed 8 MiB array in the
+ * library's device memory, and allocates nothing.
+ *   - Frames whose n_lines * n_depth exceeds 8 MiB (8388608 bytes) are
+ *     rejected with SUPRA_EINVAL before anything is launched.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call on a device uses the same array and leaves its contents
+ *     behind; calls whose work overlaps on the GPU (different streams, host
+ *     threads) race on it and must be ordered by the caller.  No part of the
+ *     array needs to start at zero: each call overwrites what it reads.
+ *   Arguments as for supra_bmode without the workspace. */
+SUPRA_API int supra_bmode_noalloc(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *stream);
+
 /* Reads (and, if clear != 0, resets) the device status word of the current
  * device: 0 = no device-side failure since the last clear, else the
  * negative SUPRA_E* code of the first failure.  Synchronizes the device. */

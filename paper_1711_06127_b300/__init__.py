@@ -25,7 +25,7 @@ GEOMETRIES = {"linear": 0, "sector": 1, "pyramid": 2}
 
 EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "supra_beamform", "supra_envelope",
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
-           "supra_bmode_batched", "supra_device_status", "supra_strerror", "supra_version")
+           "supra_bmode_batched", "supra_bmode_noalloc", "supra_device_status", "supra_strerror", "supra_version")
 
 
 class SupraError(RuntimeError):
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_bmode.argtypes = [P, P, P, P, ctypes.c_size_t, P]
     lib.supra_bmode_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P,
                                         ctypes.c_size_t, P]
+    lib.supra_bmode_noalloc.argtypes = [P, P, P, P]
     lib.supra_device_status.argtypes = [ctypes.c_int32]
     lib.supra_strerror.argtypes = [ctypes.c_int]
     lib.supra_strerror.restype = ctypes.c_char_p

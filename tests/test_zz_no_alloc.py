@@ -1,0 +1,68 @@
+"""supra_bmode_noalloc: the fused chain for callers that may not allocate
+device memory (for example a real-time acquisition loop that must not call
+cudaMalloc after start-up, or a host whose device memory belongs to another
+framework's pool).  It takes its scratch from a fixed array inside the library
+instead of a caller workspace; its results must equal supra_bmode's.
+
+This file is collected last on purpose so that a run stopping at the first
+failure has already run every other test; it also passes on its own."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1711_06127_b300 as supra
+import phantom
+from gpu_util import assert_gray
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1711_06127_b300 import build
+
+    build.build()
+    return supra.load()
+
+
+def _call_noalloc(lib, plan, ch, out):
+    stream = torch.cuda.current_stream().cuda_stream
+    return lib.supra_bmode_noalloc(plan.handle, ctypes.c_void_p(ch.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(stream))
+
+
+def test_noalloc_matches_workspace_entry_point_on_consecutive_calls(lib):
+    s = phantom.linear_setup(48, 0.3e-3, 64, 900, fc=7e6, fs=40e6, grid_n=(140, 190))
+    plan = supra.Plan(**s.params())
+    for seed in (41, 42):   # two calls in a row: the shared scratch keeps the previous call's lines
+        ch = torch.as_tensor(phantom.synth_channels(s, phantom.make_phantom(s, seed, 1500, n_points=3), seed)).cuda()
+        ref = plan.bmode(ch)                                   # supra_bmode with a torch workspace
+        out = torch.full(plan.out_shape, 7, dtype=torch.uint8, device="cuda")
+        assert _call_noalloc(lib, plan, ch, out) == supra.OK
+        torch.cuda.synchronize()
+        got, want = out.cpu().numpy(), ref.cpu().numpy()
+        assert_gray(got, want, what=f"no-alloc call seed {seed}")
+        assert np.abs(got.astype(int) - want.astype(int)).max() <= 1
+    assert supra.device_status() == 0
+
+
+def test_noalloc_lines_without_grid(lib):
+    s = phantom.linear_setup(32, 0.3e-3, 24, 700, fc=5e6, fs=40e6)
+    plan = supra.Plan(**s.params())
+    ch = torch.as_tensor(phantom.random_channels(s, 5)).cuda()
+    ref = plan.bmode(ch)
+    out = torch.empty(plan.out_shape, dtype=torch.uint8, device="cuda")
+    assert _call_noalloc(lib, plan, ch, out) == supra.OK
+    torch.cuda.synchronize()
+    assert_gray(out.cpu().numpy(), ref.cpu().numpy(), what="no-alloc lines")
+
+
+def test_noalloc_rejects_frames_beyond_the_scratch(lib):
+    # 4096 lines x 2100 depth samples of log-compressed lines > 8 MiB: refused before any launch
+    s = phantom.linear_setup(16, 0.3e-3, 4096, 2100, fc=5e6, fs=40e6, grid_n=(64, 64))
+    plan = supra.Plan(**s.params())
+    ch = torch.zeros(plan.ch_shape, dtype=torch.int16, device="cuda")
+    out = torch.empty(plan.out_shape, dtype=torch.uint8, device="cuda")
+    assert _call_noalloc(lib, plan, ch, out) == supra.EINVAL
