@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "beamformed samples·channels/s and frames/s (2D and 3D); p50/p99 frame latency"
 UNIT = "samples*channels/s"
-BATCH = 64
+BATCH = 64          # frames per step of the workload; --frames changes it for small profiling runs only
 SEED0 = 1000
 
 
@@ -228,6 +228,8 @@ def run_reference(args):
 def run_ours(args):
     import torch
 
+    global BATCH
+    BATCH = args.frames
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -314,13 +316,13 @@ def run_ours(args):
     achieved = alg_bytes / (das_ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI from pinned host memory
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    host_batch = torch.empty(batch.shape, dtype=torch.int16).pin_memory()
-    host_batch.copy_(batch)
-    host_out = torch.empty((BATCH, *plan.out_shape), dtype=torch.uint8).pin_memory()
-    dev_batch = torch.empty_like(batch)
-    dev_in = list(dev_batch)
-    host_in = list(host_batch)
+    e2e_steps = 0 if args.skip_e2e else max(1, min(args.steps, args.e2e_steps))
+    if e2e_steps:
+        host_batch = torch.empty(batch.shape, dtype=torch.int16).pin_memory()
+        host_batch.copy_(batch)
+        host_out = torch.empty((BATCH, *plan.out_shape), dtype=torch.uint8).pin_memory()
+        dev_batch = torch.empty_like(batch)
+        dev_in = list(dev_batch)
 
     def e2e_step():
         dev_batch.copy_(host_batch, non_blocking=True)
@@ -328,21 +330,22 @@ def run_ours(args):
         for k, o in enumerate(outs):
             host_out[k].copy_(o, non_blocking=True)
 
-    e2e_step()
+    if e2e_steps:
+        e2e_step()
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
     if world > 1:
         import torch.distributed as dist
 
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = per_frame * BATCH * e2e_steps * world / e2e_s
+    e2e_value = per_frame * BATCH * e2e_steps * world / e2e_s if e2e_steps else None
     h2d = sum(c.numel() * c.element_size() for c in chs)
     d2h = sum(o.numel() for o in outs)
     assert supra.device_status() == 0
@@ -351,7 +354,7 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_oracle_rate(s, [host_in[0].numpy()], budget_s=args.cpu_budget)
+            cpu = cpu_oracle_rate(s, [batch[0].cpu().numpy()], budget_s=args.cpu_budget)
         srt = sorted(step_ms)
         p50 = srt[len(srt) // 2]
         p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
@@ -392,6 +395,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=BATCH, help="frames per step (64 = the workload)")
+    ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -94,68 +94,246 @@ __device__ __forceinline__ void lerp_axis(float u, int n, int &i0, float &f) {
     f = u - (float)i0;
 }
 
-__device__ __forceinline__ uint8_t scan_point(const DevPlan *P, const uint8_t *__restrict__ bm, float x, float y,
-                                              float z) {
-    float u, w, v;
-    if (!scan_coords(P, x, y, z, u, w, v)) return 0;
+// Scan conversion of one output tile per CTA: 2D tiles are 64 (x) x 32 (z) pixels,
+// 3D tiles 16 x 16 x 8 voxels; each thread owns 4 consecutive x at 2 z.  The
+// tile's pixels are mapped back to (line, depth) coordinates, the bounding box
+// of the lines and depths they interpolate is staged into shared memory with
+// coalesced loads, and the interpolation reads shared memory.  A box that does
+// not fit falls back to reading the lines in global memory.
+constexpr int kScanBox = 24576;   // bytes of staged lines per tile
+
+__device__ __forceinline__ uint8_t lerp_lines(const DevPlan *P, const uint8_t *src, int sx, int sy, int sv, float u,
+                                              float w, float v) {
+    // src addresses line (ix, iy) depth iv at ix * sx + iy * sy + iv * sv
     const int nlx = P->lines_x, nd = P->n_depth;
     int ix, iv;
     float fx, fv;
     lerp_axis(u, nlx, ix, fx);
     lerp_axis(v, nd, iv, fv);
-    const int ix1 = min(ix + 1, nlx - 1), iv1 = min(iv + 1, nd - 1);
+    const int dx = ix + 1 < nlx ? sx : 0, dv = iv + 1 < nd ? sv : 0;
     float val;
     if (P->geometry == SUPRA_GEOM_PYRAMID) {
         int iy;
         float fy;
         lerp_axis(w, P->lines_y, iy, fy);
-        const int iy1 = min(iy + 1, P->lines_y - 1);
-        const uint8_t *b00 = bm + ((long long)iy * nlx + ix) * nd;
-        const uint8_t *b01 = bm + ((long long)iy * nlx + ix1) * nd;
-        const uint8_t *b10 = bm + ((long long)iy1 * nlx + ix) * nd;
-        const uint8_t *b11 = bm + ((long long)iy1 * nlx + ix1) * nd;
-        const float c00 = fmaf(fv, (float)b00[iv1] - (float)b00[iv], (float)b00[iv]);
-        const float c01 = fmaf(fv, (float)b01[iv1] - (float)b01[iv], (float)b01[iv]);
-        const float c10 = fmaf(fv, (float)b10[iv1] - (float)b10[iv], (float)b10[iv]);
-        const float c11 = fmaf(fv, (float)b11[iv1] - (float)b11[iv], (float)b11[iv]);
+        const int dy = iy + 1 < P->lines_y ? sy : 0;
+        const uint8_t *b = src + ix * sx + iy * sy + iv * sv;
+        const float c00 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
+        const float c01 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
+        const float c10 = fmaf(fv, (float)b[dy + dv] - (float)b[dy], (float)b[dy]);
+        const float c11 = fmaf(fv, (float)b[dy + dx + dv] - (float)b[dy + dx], (float)b[dy + dx]);
         const float c0 = fmaf(fx, c01 - c00, c00), c1 = fmaf(fx, c11 - c10, c10);
         val = fmaf(fy, c1 - c0, c0);
     } else {
-        const uint8_t *b0 = bm + (long long)ix * nd;
-        const uint8_t *b1 = bm + (long long)ix1 * nd;
-        const float c0 = fmaf(fv, (float)b0[iv1] - (float)b0[iv], (float)b0[iv]);
-        const float c1 = fmaf(fv, (float)b1[iv1] - (float)b1[iv], (float)b1[iv]);
+        const uint8_t *b = src + ix * sx + iv * sv;
+        const float c0 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
+        const float c1 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
         val = fmaf(fx, c1 - c0, c0);
     }
     return (uint8_t)fminf(fmaxf(floorf(val + 0.5f), 0.0f), 255.0f);
 }
 
-// Scan conversion: blockIdx.y selects the frame; each thread writes 4 consecutive x.
 __global__ void __launch_bounds__(256) scanconvert_kernel(const __grid_constant__ ScanLaunch L) {
+    __shared__ __align__(16) uint8_t box[kScanBox];
+    __shared__ int red[6][8];
     const ScanFrame &F = L.f[blockIdx.y];
     const DevPlan *P = F.plan;
+    const bool is3d = P->geometry == SUPRA_GEOM_PYRAMID;
+    const int TX = is3d ? 16 : 64, TY = is3d ? 16 : 1, TZ = is3d ? 8 : 32;
     const int nx = P->gnx, ny = P->gny, nz = P->gnz;
-    const int qx = (nx + 3) >> 2;
-    const long long nquads = (long long)qx * ny * nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nquads;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int xq = (int)(q % qx);
-        const long long rest = q / qx;
-        const int iy = (int)(rest % ny), iz = (int)(rest / ny);
-        const float y = fmaf((float)iy, P->gsy, P->goy), z = fmaf((float)iz, P->gsz, P->goz);
-        uint8_t out[4];
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + TZ - 1) / TZ;
+    const int t = threadIdx.x;
+    const int nlx = P->lines_x, nly = P->lines_y, nd = P->n_depth;
+    for (int tile = blockIdx.x; tile < ntx * nty * ntz; tile += gridDim.x) {
+        const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+        // this thread: x = x0 .. x0 + 3, y, z = z0 and z0 + TZ / 2
+        const int x0 = tx * TX + (t % (TX / 4)) * 4;
+        const int y = ty * TY + (is3d ? (t / 4) % 16 : 0);
+        const int zr = is3d ? t / 64 : t / 16;
+        float pu[8], pw[8], pv[8];
+        bool pin[8];
+        int lo_x = 1 << 30, hi_x = -1, lo_y = 1 << 30, hi_y = -1, lo_v = 1 << 30, hi_v = -1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int ix = xq * 4 + k;
-            out[k] = ix < nx ? scan_point(P, F.bm, fmaf((float)ix, P->gsx, P->gox), y, z) : 0;
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + (k & 3), z = tz * TZ + zr + (k >> 2) * (TZ / 2);
+            pin[k] = false;
+            pu[k] = pw[k] = pv[k] = 0.f;
+            if (x < nx && y < ny && z < nz) {
+                pin[k] = scan_coords(P, fmaf((float)x, P->gsx, P->gox), fmaf((float)y, P->gsy, P->goy),
+                                     fmaf((float)z, P->gsz, P->goz), pu[k], pw[k], pv[k]);
+            }
+            if (pin[k]) {
+                int i0;
+                float f;
+                lerp_axis(pu[k], nlx, i0, f);
+                lo_x = min(lo_x, i0);
+                hi_x = max(hi_x, min(i0 + 1, nlx - 1));
+                lerp_axis(pv[k], nd, i0, f);
+                lo_v = min(lo_v, i0);
+                hi_v = max(hi_v, min(i0 + 1, nd - 1));
+                if (is3d) {
+                    lerp_axis(pw[k], nly, i0, f);
+                    lo_y = min(lo_y, i0);
+                    hi_y = max(hi_y, min(i0 + 1, nly - 1));
+                }
+            }
         }
-        uint8_t *dst = F.img + (rest * nx) + xq * 4;
-        if ((nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(dst) & 3) == 0)) {
-            *reinterpret_cast<uint32_t *>(dst) =
-                (uint32_t)out[0] | ((uint32_t)out[1] << 8) | ((uint32_t)out[2] << 16) | ((uint32_t)out[3] << 24);
+        if (!is3d) lo_y = hi_y = 0;
+        // block-wide bounding box
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo_x = min(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+            hi_x = max(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+            lo_y = min(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+            hi_y = max(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+            lo_v = min(lo_v, __shfl_xor_sync(0xffffffffu, lo_v, o));
+            hi_v = max(hi_v, __shfl_xor_sync(0xffffffffu, hi_v, o));
+        }
+        if ((t & 31) == 0) {
+            red[0][t >> 5] = lo_x;
+            red[1][t >> 5] = hi_x;
+            red[2][t >> 5] = lo_y;
+            red[3][t >> 5] = hi_y;
+            red[4][t >> 5] = lo_v;
+            red[5][t >> 5] = hi_v;
+        }
+        __syncthreads();
+        int bx0 = red[0][0], bx1 = red[1][0], by0 = red[2][0], by1 = red[3][0], bv0 = red[4][0], bv1 = red[5][0];
+        for (int w8 = 1; w8 < 8; ++w8) {
+            bx0 = min(bx0, red[0][w8]);
+            bx1 = max(bx1, red[1][w8]);
+            by0 = min(by0, red[2][w8]);
+            by1 = max(by1, red[3][w8]);
+            bv0 = min(bv0, red[4][w8]);
+            bv1 = max(bv1, red[5][w8]);
+        }
+        const bool any = bx1 >= bx0;
+        // depth runs are contiguous in bm: stage whole 4-byte words when lines start 4-byte aligned
+        const bool words = (nd & 3) == 0 && (reinterpret_cast<uintptr_t>(F.bm) & 3) == 0;
+        if (words) bv0 &= ~3;
+        const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
+        const int nbv = words ? ((bv1 - bv0) | 3) + 1 : bv1 - bv0 + 1;   // staged depths per line
+        const bool staged = any && (long long)nbx * nby * nbv <= kScanBox;
+        if (staged) {
+            // box[(iy - by0) * nbx * nbv + (ix - bx0) * nbv + (iv - bv0)]
+            const int rows = nbx * nby;
+            if (words) {
+                const int nw = nbv >> 2, total = rows * nw;
+                for (int base = 0; base < total; base += 256 * 4) {
+                    uint32_t r[4];
+                    int dsti[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {   // all loads in flight before the stores
+                        const int id = base + t + 256 * u;
+                        dsti[u] = -1;
+                        if (id < total) {
+                            const int row = id / nw, wi = id - row * nw;
+                            const int iy = by0 + row / nbx, ix = bx0 + row % nbx;
+                            r[u] = __ldg(reinterpret_cast<const uint32_t *>(F.bm + ((long long)iy * nlx + ix) * nd + bv0) + wi);
+                            dsti[u] = id;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (dsti[u] >= 0) reinterpret_cast<uint32_t *>(box)[dsti[u]] = r[u];
+                }
+            } else {
+                for (int rrow = t / 32; rrow < rows; rrow += 8) {
+                    const int iy = by0 + rrow / nbx, ix = bx0 + rrow % nbx;
+                    const uint8_t *src = F.bm + ((long long)iy * nlx + ix) * nd + bv0;
+                    uint8_t *dst = box + rrow * nbv;
+                    for (int k = t & 31; k < nbv; k += 32) dst[k] = src[k];
+                }
+            }
+        }
+        __syncthreads();
+        uint8_t outv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            outv[k] = 0;
+            if (!pin[k]) continue;
+            if (staged)
+                outv[k] = lerp_lines(P, box - (bx0 * nbv + by0 * nbx * nbv + bv0), nbv, nbx * nbv, 1, pu[k], pw[k],
+                                     pv[k]);
+            else
+                outv[k] = lerp_lines(P, F.bm, nd, nlx * nd, 1, pu[k], pw[k], pv[k]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int z = tz * TZ + zr + h * (TZ / 2);
+            if (y >= ny || z >= nz || x0 >= nx) continue;
+            uint8_t *dst = F.img + ((long long)z * ny + y) * nx + x0;
+            if (x0 + 4 <= nx && (reinterpret_cast<uintptr_t>(dst) & 3) == 0) {
+                *reinterpret_cast<uint32_t *>(dst) = (uint32_t)outv[4 * h] | ((uint32_t)outv[4 * h + 1] << 8) |
+                                                      ((uint32_t)outv[4 * h + 2] << 16) |
+                                                      ((uint32_t)outv[4 * h + 3] << 24);
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (x0 + k < nx) dst[k] = outv[4 * h + k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Linear layouts: the inverse map is separable (u from x, v from z).  A CTA
+// covers 32 columns x 64 rows.  Each warp takes 4 columns; its lanes walk 32
+// consecutive rows of one column at a time, so both lines it interpolates are
+// read within one or two cache lines per load; the tile goes through shared
+// memory so that rows are written out coalesced.  Same arithmetic as
+// scan_coords / lerp_lines.
+__global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_constant__ ScanLaunch L) {
+    __shared__ uint8_t tile[64][33];
+    const ScanFrame &F = L.f[blockIdx.y];
+    const DevPlan *P = F.plan;
+    const int nx = P->gnx, nz = P->gnz, nlx = P->lines_x, nd = P->n_depth;
+    const int cols = (nx + 31) >> 5;
+    const int xb = (blockIdx.x % cols) * 32, zb = (blockIdx.x / cols) * 64;
+    if (zb >= nz) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < 4; ++c) {
+        const int xl = warp * 4 + c, x = xb + xl;
+        const float u = (fmaf((float)x, P->gsx, P->gox) - P->u0) * P->du_inv;
+        const bool in_u = x < nx && u >= -kInsideEps && u <= (float)(nlx - 1) + kInsideEps;
+        int ix;
+        float fx;
+        lerp_axis(u, nlx, ix, fx);
+        const int dx = ix + 1 < nlx ? nd : 0;
+        const uint8_t *line = F.bm + (long long)ix * nd;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int zl = h * 32 + lane, z = zb + zl;
+            const float rz = fmaf((float)z, P->gsz, P->goz) - P->apz;
+            const float v = (rz - P->v0) * P->dv_inv;
+            uint8_t out = 0;
+            if (in_u && z < nz && v >= -kInsideEps && v <= (float)(nd - 1) + kInsideEps) {
+                int iv;
+                float fv;
+                lerp_axis(v, nd, iv, fv);
+                const int dv = iv + 1 < nd ? 1 : 0;
+                const uint8_t *b = line + iv;
+                const float c0 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
+                const float c1 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
+                out = (uint8_t)fminf(fmaxf(floorf(fmaf(fx, c1 - c0, c0) + 0.5f), 0.0f), 255.0f);
+            }
+            tile[zl][xl] = out;
+        }
+    }
+    __syncthreads();
+    // 64 rows x 32 bytes: thread -> (row, 8-byte chunk)
+    const int row = threadIdx.x >> 2, ch = (threadIdx.x & 3) * 8, z = zb + row;
+    if (z < nz) {
+        uint8_t *dst = F.img + (long long)z * nx + xb + ch;
+        if (xb + ch + 8 <= nx && (reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+            uint2 w;
+            w.x = (uint32_t)tile[row][ch] | ((uint32_t)tile[row][ch + 1] << 8) | ((uint32_t)tile[row][ch + 2] << 16) |
+                  ((uint32_t)tile[row][ch + 3] << 24);
+            w.y = (uint32_t)tile[row][ch + 4] | ((uint32_t)tile[row][ch + 5] << 8) |
+                  ((uint32_t)tile[row][ch + 6] << 16) | ((uint32_t)tile[row][ch + 7] << 24);
+            *reinterpret_cast<uint2 *>(dst) = w;
         } else {
-            for (int k = 0; k < 4; ++k)
-                if (xq * 4 + k < nx) dst[k] = out[k];
+            for (int k = 0; k < 8; ++k)
+                if (xb + ch + k < nx) dst[k] = tile[row][ch + k];
         }
     }
 }

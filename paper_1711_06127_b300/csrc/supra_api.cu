@@ -176,17 +176,52 @@ int launch_das(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
     }
 }
 
-int launch_scan(const ScanLaunch &S, cudaStream_t st) {
-    if (S.n == 0) return SUPRA_OK;
-    // frames are independent along grid.y; about 8 CTAs per SM in total
-    int blocks_x = 1;
+// Frames of one scan-conversion launch and their host-side plan records (grid sizing).
+struct ScanBatch {
+    ScanLaunch launch{};
+    const DevPlan *host[kMaxScanFrames] = {};
+    void add(const supra_plan *p, const uint8_t *bm, uint8_t *img);
+};
+
+int launch_scan(const ScanBatch &S, cudaStream_t st) {
+    if (S.launch.n == 0) return SUPRA_OK;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    blocks_x = std::max(1, (sms * 8 + S.n - 1) / S.n);
-    dim3 grid(blocks_x, S.n);
-    scanconvert_kernel<<<grid, 256, 0, st>>>(S);
-    return check_cuda(cudaGetLastError());
+    // linear layouts go to the separable kernel, the others to the tiled one
+    ScanLaunch lin{}, gen{};
+    long long lin_blocks = 1, gen_tiles = 1;
+    for (int k = 0; k < S.launch.n; ++k) {
+        const DevPlan &H = *S.host[k];
+        if (H.geometry == SUPRA_GEOM_LINEAR) {
+            lin.f[lin.n++] = S.launch.f[k];
+            lin_blocks = std::max(lin_blocks, (long long)((H.gnx + 31) / 32) * ((H.gnz + 63) / 64));
+        } else {
+            gen.f[gen.n++] = S.launch.f[k];
+            const bool is3d = H.geometry == SUPRA_GEOM_PYRAMID;
+            const int TX = is3d ? 16 : 64, TY = is3d ? 16 : 1, TZ = is3d ? 8 : 32;
+            gen_tiles = std::max(gen_tiles, (long long)((H.gnx + TX - 1) / TX) * ((H.gny + TY - 1) / TY) *
+                                                ((H.gnz + TZ - 1) / TZ));
+        }
+    }
+    if (lin.n) {
+        // every CTA of the largest frame; smaller frames' extra CTAs return at once
+        if (lin_blocks > 0x7fffffffLL) return SUPRA_EINVAL;
+        scanconvert_linear_kernel<<<dim3((unsigned)lin_blocks, lin.n), 256, 0, st>>>(lin);
+        const int rc = check_cuda(cudaGetLastError());
+        if (rc) return rc;
+    }
+    if (gen.n) {
+        const int per_frame = (int)std::max(1LL, std::min(gen_tiles, (long long)(sms * 16 + gen.n - 1) / gen.n));
+        scanconvert_kernel<<<dim3(per_frame, gen.n), 256, 0, st>>>(gen);
+        return check_cuda(cudaGetLastError());
+    }
+    return SUPRA_OK;
+}
+
+void ScanBatch::add(const supra_plan *p, const uint8_t *bm, uint8_t *img) {
+    host[launch.n] = &p->host;
+    launch.f[launch.n++] = ScanFrame{p->dev, bm, img};
 }
 
 }  // namespace
@@ -589,9 +624,8 @@ int supra_logcompress(const supra_plan *plan, const float *env, uint8_t *bm, voi
 
 int supra_scanconvert(const supra_plan *plan, const uint8_t *bm, uint8_t *img, void *stream) {
     if (!plan || !bm || !img || !plan->host.has_grid) return SUPRA_EINVAL;
-    ScanLaunch S{};
-    S.n = 1;
-    S.f[0] = ScanFrame{plan->dev, bm, img};
+    ScanBatch S;
+    S.add(plan, bm, img);
     return launch_scan(S, static_cast<cudaStream_t>(stream));
 }
 
@@ -691,14 +725,14 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
         }
     }
     // scan conversion of the frames with a grid
-    ScanLaunch S{};
+    ScanBatch S;
     for (int f = 0; f < n; ++f) {
         if (!plans[f]->host.has_grid) continue;
-        S.f[S.n++] = ScanFrame{plans[f]->dev, bm[f], out[f]};
-        if (S.n == kMaxScanFrames) {
+        S.add(plans[f], bm[f], out[f]);
+        if (S.launch.n == kMaxScanFrames) {
             const int rc = launch_scan(S, st);
             if (rc) return rc;
-            S.n = 0;
+            S.launch.n = 0;
         }
     }
     return launch_scan(S, st);
