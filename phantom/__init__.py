@@ -315,6 +315,7 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
     zf = torch.linalg.norm(axis, dim=1).clamp_min(1e-9)
     axis = axis / zf[:, None]
     Ftx = zf / width
+    gpu_lists = []   # (transmit, pair) lists for the GPU accumulation
     # transmit beam weight for every (transmit, scatterer), kept where significant
     tx_rows = max(1, (1 << 24) // max(1, P.shape[0]))
     for t0 in range(0, n_tx, tx_rows):
@@ -329,6 +330,9 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
             continue
         amp = (A[ss] * b[tt, ss]).to(f64)
         tt = tt + t0
+        if dev.type == "cuda":
+            gpu_lists.append((tt, torch.cat([P[ss].float(), amp.float()[:, None]], dim=1)))
+            continue
         dtx = torch.linalg.norm(P[ss] - O[tt], dim=1)
         npair = tt.numel()
         pair_rows = max(1, chunk // (n_el * J))
@@ -345,6 +349,9 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
             idx = base[..., None] + k.long()
             buf.index_add_(0, idx[ok], val[ok].to(torch.float32))
 
+    if dev.type == "cuda" and gpu_lists:
+        _gpu_echoes(setup, gpu_lists, sig, half, J, buf)
+
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed) * 7919 + 17)
     rms = torch.sqrt(torch.mean(buf.double() ** 2)).item()
@@ -356,6 +363,40 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
         buf *= peak / pk
     out = torch.round(buf).clamp_(-32768, 32767).to(torch.int16)
     return out.view(n_tx, n_el, n_s)
+
+
+_synth_lib = None
+
+
+def _gpu_echoes(setup, lists, sig, half, J, buf):
+    """Accumulates the echoes of (transmit, scatterer) pairs on the GPU
+    (synth_cuda.cu) into buf, float [n_tx * n_el * n_s]."""
+    import ctypes
+
+    import torch
+
+    global _synth_lib
+    if _synth_lib is None:
+        from . import build
+
+        _synth_lib = ctypes.CDLL(build.build())
+        _synth_lib.phantom_echoes.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 4 + [ctypes.c_float] * 5 + \
+            [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    dev = buf.device
+    tt = torch.cat([l[0] for l in lists])
+    pairs = torch.cat([l[1] for l in lists]).contiguous()
+    order = torch.argsort(tt, stable=True)
+    tt, pairs = tt[order], pairs[order].contiguous()
+    counts = torch.bincount(tt, minlength=setup.n_tx)
+    start = torch.zeros(setup.n_tx + 1, dtype=torch.int32, device=dev)
+    start[1:] = torch.cumsum(counts, 0).to(torch.int32)
+    elem = torch.as_tensor(setup.elem_pos, dtype=torch.float32, device=dev).contiguous()
+    txo = torch.as_tensor(setup.tx_origin, dtype=torch.float32, device=dev).contiguous()
+    rc = _synth_lib.phantom_echoes(setup.n_tx, setup.n_el, setup.n_samples, elem.data_ptr(), txo.data_ptr(),
+                                   start.data_ptr(), pairs.data_ptr(), setup.c, setup.fs, setup.fc, sig, half, J,
+                                   buf.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"phantom_echoes failed with CUDA error {rc}")
 
 
 def random_channels(setup: Setup, seed: int, amplitude: int = 8000):

@@ -251,3 +251,62 @@ def test_contiguous_batch_uses_tensor_copies_and_matches():
     outs_l = supra.bmode_batched([plan_l] * 8, list(batch[:8]))
     ref_l = oracle.bmode(dict(p, grid=None), batch[3].cpu().numpy())
     assert_gray(outs_l[3].cpu().numpy(), ref_l, what="lines frame 3")
+
+
+def test_config1_bmode_lines_full_size():
+    s = phantom.config1()
+    p = s.params()
+    ch = phantom.synth_channels(s, phantom.default_phantom(s, 1), 1)
+    plan = supra.Plan(**p)
+    got = plan.bmode(ch.cuda()).cpu().numpy()
+    assert_gray(got, oracle.bmode(p, ch.numpy()), what="64-element frame")
+
+
+def test_config3_volume_full_size_sampled():
+    # 32x32 matrix array, 64x64 lines on a +-30 deg pyramid, 1536 samples: 12 GiB of records per
+    # volume.  Sampled lines (RF, log-compressed lines) and sampled voxels of the 256^3 volume are
+    # checked against the oracle, which reads only the transmit records it needs.
+    s = phantom.config3()
+    p = s.params()
+    ch = phantom.synth_channels(s, phantom.default_phantom(s, 3000), 3000, device="cuda")
+    plan = supra.Plan(**p)
+    plan_l = supra.Plan(**dict(p, grid=None))
+    vol = plan.bmode(ch).cpu().numpy()
+    rf = plan.beamform(ch).cpu().numpy()
+    bm = plan_l.bmode(ch).cpu().numpy()
+    torch.cuda.synchronize()
+    nd = s.n_depth
+    rng = np.random.default_rng(7)
+
+    def oracle_lines(lines):
+        out = {}
+        for l in lines:
+            block = ch[int(s.line_tx[l])].cpu().numpy()
+            out[l] = oracle.das_points(p, [l] * nd, np.arange(nd), [block] * nd)
+        return out
+
+    lines = sorted(set(rng.integers(0, s.n_lines, 10).tolist()) | {32 * 64 + 32})
+    rf_o = oracle_lines(lines)
+    ref = np.stack([rf_o[l] for l in lines])
+    assert max_norm_err(rf[lines], ref) <= RF_TOL
+    bm_o = oracle.logcompress(oracle.envelope(p, ref), p["log_ref"], p["dyn_range_db"])
+    assert_gray(bm[lines], bm_o, what="pyramid lines")
+    # voxels: the lines each sampled voxel interpolates, through the oracle's own chain
+    pts_all = oracle.grid_points(p["grid"]).reshape(-1, 3)
+    ux, uy, v, ok = oracle.scan_coordinates(p, pts_all)
+    inside = np.nonzero(ok)[0]
+    pick = rng.choice(inside, 48, replace=False)
+    need = set()
+    for k in pick:
+        ix, iy = min(int(np.floor(max(ux[k], 0))), s.lines_x - 2), min(int(np.floor(max(uy[k], 0))), s.lines_y - 2)
+        for dy in (0, 1):
+            for dx in (0, 1):
+                need.add((iy + dy) * s.lines_x + ix + dx)
+    rf_n = oracle_lines(sorted(need))
+    bm_full = np.zeros((s.n_lines, nd), np.uint8)
+    for l, r in rf_n.items():
+        bm_full[l] = oracle.logcompress(oracle.envelope(p, r[None]), p["log_ref"], p["dyn_range_db"])[0]
+    want = oracle.scanconvert(p, bm_full, pts_all[pick])
+    got = vol.reshape(-1)[pick]
+    d = np.abs(got.astype(int) - want.astype(int))
+    assert np.mean(d <= 1) >= 0.97 and d.max() <= 2, (np.mean(d <= 1), d.max())
