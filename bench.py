@@ -315,6 +315,34 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     achieved = alg_bytes / (das_ms * 1e-3) / 1e9
 
+    # ---- the 3D workload: one 64x64-line pyramid volume (12 GiB of records) per launch
+    vol3d = None
+    if not args.skip_3d:
+        s3 = phantom.config3()
+        plan3 = supra.Plan(**s3.params())
+        ch3 = phantom.synth_channels(s3, phantom.default_phantom(s3, 3000), 3000, device=dev)
+        out3 = torch.empty(plan3.out_shape, dtype=torch.uint8, device=dev)
+        ws3 = torch.empty(max(1, supra.workspace_size([plan3])), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            plan3.bmode(ch3, out3, ws3, stream)
+        e3 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        n3 = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        e3[0].record(stream)
+        for _ in range(n3):
+            plan3.bmode(ch3, out3, ws3, stream)
+        e3[1].record(stream)
+        torch.cuda.synchronize()
+        ms3 = e3[0].elapsed_time(e3[1]) / n3
+        i3 = plan3.info
+        vol3d = {"workload": s3.name, "ms_per_volume": ms3, "volumes_per_s": 1e3 / ms3,
+                 "samples_channels_per_s": i3["n_tx"] * i3["n_el"] * i3["n_samples"] / (ms3 * 1e-3),
+                 "aperture_gb_per_s": (i3["aperture_bytes"] + i3["image_bytes"]) / (ms3 * 1e-3) / 1e9,
+                 "frac_of_hbm_peak": (i3["aperture_bytes"] + i3["image_bytes"]) / (ms3 * 1e-3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                 "note": "one volume per launch (no frame batching), records resident"}
+        del ch3, out3, ws3, plan3
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI from pinned host memory
     e2e_steps = 0 if args.skip_e2e else max(1, min(args.steps, args.e2e_steps))
     if e2e_steps:
@@ -369,12 +397,13 @@ def run_ours(args):
             "latency_ms": {"p50": p50, "p99": p99, "note": "per step; the 64 frames of a step complete together"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": kernel_traffic(),
-                         "kernel": "das_kernel<8,1> (beamform + envelope + log)", "kernel_ms": das_ms,
+                         "kernel": "das_kernel<16,1> (beamform + envelope + log, 16 frames per CTA)", "kernel_ms": das_ms,
                          "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
             "full_array_gbs": BATCH * info["channel_bytes"] / (das_ms * 1e-3) / 1e9,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
+            "volume_3d": vol3d,
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
         }
@@ -397,6 +426,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=BATCH, help="frames per step (64 = the workload)")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-3d", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
