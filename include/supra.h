@@ -210,6 +210,24 @@ SUPRA_API int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *ou
 SUPRA_API int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t *const *ch, uint8_t *const *out,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* Exact minimum-variance (Capon) beamformer.  The paper has no MV node; it
+ * labels the training data of the learned apodization and serves as its
+ * fallback and judge.  Per pixel: the delayed, interpolated samples x of the
+ * elements inside the F-number aperture (the delays and aperture of
+ * supra_beamform, no apodization), M of them in element order; subapertures
+ * x_l = x[l : l + L], L = min(subaperture, M), K = M - L + 1;
+ * R = (1/K) sum_l x_l x_l^T + loading * (trace(R) / L) * I (loading relative
+ * to the mean eigenvalue); w = R^{-1} 1 / (1^T R^{-1} 1);
+ * rf = w^T (1/K) sum_l x_l.  M < 2: the delay-and-sum value.  Solved in FP32
+ * when subaperture / loading <= 1e4 (the loading bounds the condition number
+ * by 1 + L/loading), else in FP64.
+ *   subaperture: 1..32; loading > 0, finite (0.01 is the usual choice)
+ *   ch: int16 [n_tx][n_el][n_samples], rf: float [n_lines][n_depth] (device)
+ * Errors: SUPRA_EINVAL (arguments; an aperture that can hold more than 256
+ * elements). */
+SUPRA_API int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const int16_t *ch, float *rf,
+                       void *stream);
+
 /* supra_bmode for callers that may not allocate device memory.  The paper has
  * no counterpart: it exists because some callers cannot provide the device
  * workspace supra_bmode needs -- e.g. a real-time acquisition loop that must

@@ -311,3 +311,49 @@ def bmode(p: dict, ch) -> np.ndarray:
         return bm
     img = scanconvert(p, bm)
     return img[:, 0, :] if p["grid"]["n"][1] == 1 else img
+
+
+# ----------------------------------------------------------------------------- minimum variance
+
+def mv_weights(x: np.ndarray, L: int, loading: float | None = None):
+    """Minimum-variance (Capon) weights of one pixel from its delayed samples x
+    (active elements in element order): subapertures x_l = x[l : l + L],
+    l = 0..K-1 with K = M - L + 1 (L clipped to M); R = (1/K) sum_l x_l x_l^T;
+    diagonal loading relative to the mean eigenvalue,
+    R + loading * (trace(R) / L) * I (default loading 0.01); steering vector 1
+    (the data are already delayed); w = R^{-1} 1 / (1^T R^{-1} 1).  Not part of
+    the paper: the spatially smoothed MV estimator the learned apodization is
+    trained on.  Returns (w, xbar) with xbar = (1/K) sum_l x_l."""
+    x = np.asarray(x, np.float64)
+    M = len(x)
+    L = min(int(L), M)
+    K = M - L + 1
+    X = np.stack([x[l:l + L] for l in range(K)])
+    R = X.T @ X / K
+    delta = 0.01 if loading is None else float(loading)
+    R = R + delta * (np.trace(R) / L) * np.eye(L)
+    z = np.linalg.solve(R, np.ones(L))
+    return z / z.sum(), X.mean(axis=0)
+
+
+def mv_point(p: dict, ch_tx, line: int, i: int, L: int = 32, loading: float | None = None) -> float:
+    """MV output y = w^T xbar at (line, depth i); fewer than two active
+    elements fall back to the delay-and-sum value."""
+    x, _ = delayed_samples(p, ch_tx, line, i)
+    if len(x) < 2:
+        return float(das_points(p, [line], [i], [ch_tx])[0])
+    w, xbar = mv_weights(x, L, loading)
+    return float(w @ xbar)
+
+
+def mv(p: dict, ch, L: int = 32, loading: float | None = None, lines=None, depths=None) -> np.ndarray:
+    """MV beamformed lines [n_lines, n_depth] (or the selected lines x depths)."""
+    ch = np.asarray(ch)
+    lines = range(len(p["line_tx"])) if lines is None else lines
+    depths = range(int(p["n_depth"])) if depths is None else depths
+    out = np.zeros((len(lines), len(depths)))
+    for a, l in enumerate(lines):
+        ch_tx = ch[int(p["line_tx"][l])]
+        for b, i in enumerate(depths):
+            out[a, b] = mv_point(p, ch_tx, l, i, L, loading)
+    return out

@@ -25,7 +25,8 @@ GEOMETRIES = {"linear": 0, "sector": 1, "pyramid": 2}
 
 EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "supra_beamform", "supra_envelope",
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
-           "supra_bmode_batched", "supra_bmode_noalloc", "supra_device_status", "supra_strerror", "supra_version")
+           "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_device_status", "supra_strerror",
+           "supra_version")
 
 
 class SupraError(RuntimeError):
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_bmode_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P,
                                         ctypes.c_size_t, P]
     lib.supra_bmode_noalloc.argtypes = [P, P, P, P]
+    lib.supra_mv.argtypes = [P, ctypes.c_int32, ctypes.c_float, P, P, P]
     lib.supra_device_status.argtypes = [ctypes.c_int32]
     lib.supra_strerror.argtypes = [ctypes.c_int]
     lib.supra_strerror.restype = ctypes.c_char_p
@@ -259,6 +261,20 @@ class Plan:
                                         _dev_tensor(img, torch.uint8, self.image_shape, "img"), _stream_ptr(stream)),
                "supra_scanconvert")
         return img
+
+    def mv(self, ch, subaperture=32, loading=None, rf=None, stream=None):
+        """Exact minimum-variance beamformer (supra_mv); loading (relative to the
+        mean eigenvalue of the covariance) defaults to 0.01."""
+        import torch
+
+        if loading is None:
+            loading = 0.01
+        if rf is None:
+            rf = torch.empty(self.line_shape, dtype=torch.float32, device=ch.device)
+        _check(load().supra_mv(self.handle, int(subaperture), float(loading),
+                               _dev_tensor(ch, torch.int16, self.ch_shape, "ch"),
+                               _dev_tensor(rf, torch.float32, self.line_shape, "rf"), _stream_ptr(stream)), "supra_mv")
+        return rf
 
     # ---- fused chain -----------------------------------------------------
     def bmode(self, ch, out=None, workspace=None, stream=None):

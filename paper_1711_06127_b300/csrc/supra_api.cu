@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "das_kernel.cuh"
 #include "post_kernels.cuh"
+#include "mv_kernel.cuh"
 
 using namespace supra;
 
@@ -21,6 +22,7 @@ struct supra_plan {
     void *blob = nullptr;   // one device allocation holding every table
     supra_plan_info info{};
     int device = 0;
+    int max_active = 0;     // upper bound on the elements inside one pixel's aperture
 };
 
 namespace {
@@ -576,6 +578,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     I.image_bytes = grid ? (long long)grid->nx * grid->ny * grid->nz : I.bmode_bytes;
     I.has_grid = grid != nullptr;
     I.depth_tile = kDepthTile;
+    for (const short4 &bb : box) plan->max_active = std::max(plan->max_active, (bb.y - bb.x + 1) * (bb.w - bb.z + 1));
     *out = plan;
     return SUPRA_OK;
 }
@@ -745,6 +748,23 @@ int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *w
     uint8_t *o[1] = {out};
     if (!plan) return SUPRA_EINVAL;
     return supra_bmode_batched(1, p, c, o, workspace, workspace_bytes, stream);
+}
+
+int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const int16_t *ch, float *rf, void *stream) {
+    if (!plan || !ch || !rf) return SUPRA_EINVAL;
+    if (subaperture < 1 || subaperture > kMvMaxL || !(loading > 0.0f) || !std::isfinite(loading)) return SUPRA_EINVAL;
+    if (plan->max_active > kMvMaxM) return SUPRA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((double)subaperture / loading <= 1e4) {
+        constexpr int w = mv_warps<float>();
+        const dim3 grid((plan->host.n_depth + w - 1) / w, plan->host.n_lines);
+        mv_kernel<float><<<grid, w * 32, 0, st>>>(plan->dev, ch, rf, subaperture, loading);
+    } else {
+        constexpr int w = mv_warps<double>();
+        const dim3 grid((plan->host.n_depth + w - 1) / w, plan->host.n_lines);
+        mv_kernel<double><<<grid, w * 32, 0, st>>>(plan->dev, ch, rf, subaperture, loading);
+    }
+    return check_cuda(cudaGetLastError());
 }
 
 int supra_device_status(int32_t clear) {
