@@ -406,3 +406,48 @@ def random_channels(setup: Setup, seed: int, amplitude: int = 8000):
     g = torch.Generator().manual_seed(int(seed))
     return torch.randint(-amplitude, amplitude + 1, (setup.n_tx, setup.n_el, setup.n_samples),
                          generator=g, dtype=torch.int32).to(torch.int16)
+
+
+# ----------------------------------------------------------------------------- learned apodization inputs
+
+APOD_SIZES = ((64, 128), (64,), (64, 64), (64,), (128, 64), (128,))   # W1, b1, W2, b2, W3, b3
+
+
+def apod_init(seed: int, out_scale: float = 0.0, bias_scale: float = 0.0) -> np.ndarray:
+    """Seeded initial parameters of the per-pixel apodization network, float32
+    flat vector in the order W1, b1, W2, b2, W3, b3 ([out][in] row-major).
+    Hidden weights: He-normal (std sqrt(2 / fan_in)).  Output weights: normal
+    with std out_scale / sqrt(64) (0 -> all-zero output layer, i.e. a uniform
+    apodization over the aperture at the start).  Biases: normal with std
+    bias_scale."""
+    rng = np.random.default_rng(int(seed))
+    parts = []
+    for k, shape in enumerate(APOD_SIZES):
+        if len(shape) == 2:
+            std = math.sqrt(2.0 / shape[1]) if k < 4 else out_scale / math.sqrt(shape[1])
+        else:
+            std = bias_scale
+        parts.append((rng.standard_normal(shape) * std).ravel())
+    return np.concatenate(parts).astype(np.float32)
+
+
+def apod_random_batch(seed: int, n: int, min_active: int = 2, n_el: int = 128):
+    """Random network inputs for gradient checks: raw samples X[n,128] (bf16
+    representable, zero off the mask), masks[n,128] (a contiguous run of at
+    least min_active elements, as an F-number aperture gives), norms ||x|| and
+    targets t in [-1, 1]."""
+    rng = np.random.default_rng(int(seed))
+    X = np.zeros((n, 128), np.float32)
+    mask = np.zeros((n, 128), bool)
+    for b in range(n):
+        w = int(rng.integers(min_active, n_el + 1))
+        s = int(rng.integers(0, n_el - w + 1))
+        mask[b, s:s + w] = True
+        X[b, s:s + w] = rng.normal(0.0, 1000.0, w)
+    # round to bfloat16 (keep the top 16 bits, round to nearest even)
+    u = X.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    X = u.astype(np.uint32).view(np.float32)
+    norm = np.sqrt(np.sum(X.astype(np.float64) ** 2, axis=1))
+    t = rng.uniform(-1.0, 1.0, n)
+    return X, mask, norm, t

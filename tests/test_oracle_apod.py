@@ -1,0 +1,119 @@
+"""Pins of the learned-apodization oracle (network, loss, gradient, Adam).
+The network is not in the paper; every pin here follows from the definitions
+(finite differences, softmax invariants, special cases that reduce to
+delay-and-sum, Adam's closed form under a constant gradient)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import apod
+import phantom
+
+
+def _inputs(seed, n, min_active=2):
+    X, mask, norm, t = phantom.apod_random_batch(seed, n, min_active)
+    return X.astype(np.float64) / norm[:, None], mask, t
+
+
+def test_parameter_count_and_layout():
+    assert apod.N_PARAMS == 20480 + 256
+    p = phantom.apod_init(1, out_scale=1.0, bias_scale=0.1)
+    d = apod.unpack(p)
+    assert d["W1"].shape == (64, 128) and d["W3"].shape == (128, 64) and d["b3"].shape == (128,)
+    np.testing.assert_array_equal(apod.pack(d), p.astype(np.float64))
+
+
+def test_gradient_matches_central_differences():
+    params = phantom.apod_init(3, out_scale=2.0, bias_scale=0.2).astype(np.float64)
+    Xh, mask, t = _inputs(4, 6)
+    loss, g = apod.loss_and_grad(params, Xh, mask, t)
+    rng = np.random.default_rng(5)
+    idx = np.concatenate([rng.choice(apod.N_PARAMS, 500, replace=False),
+                          np.arange(8192, 8192 + 64), np.arange(12352, 12352 + 64), np.arange(20608, 20736)])
+    h = 1e-6
+    fd = np.empty(len(idx))
+    for j, k in enumerate(idx):
+        pp, pm = params.copy(), params.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd[j] = (apod.loss_and_grad(pp, Xh, mask, t)[0] - apod.loss_and_grad(pm, Xh, mask, t)[0]) / (2 * h)
+    scale = np.max(np.abs(g[idx]))
+    assert scale > 0
+    np.testing.assert_allclose(fd, g[idx], rtol=0, atol=1e-6 * scale + 1e-12)
+    # every layer receives gradient
+    d = apod.unpack(g)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert np.max(np.abs(d[name])) > 0, name
+
+
+def test_softmax_weights_are_a_distribution_on_the_mask():
+    params = phantom.apod_init(6, out_scale=3.0, bias_scale=0.5)
+    Xh, mask, _ = _inputs(7, 20)
+    mask[3] = False                      # an empty aperture: no weights, output 0
+    Xh[3] = 0.0
+    yh, w, _ = apod.forward(params, Xh, mask)
+    assert np.all(w[~mask] == 0.0) and np.all(w >= 0.0)
+    s = w.sum(axis=1)
+    np.testing.assert_allclose(s[np.arange(20) != 3], 1.0, rtol=1e-12)
+    assert s[3] == 0.0 and yh[3] == 0.0
+    # the output is a convex combination of the masked inputs
+    lo = np.where(mask, Xh, np.inf).min(axis=1)
+    hi = np.where(mask, Xh, -np.inf).max(axis=1)
+    k = np.arange(20) != 3
+    assert np.all(yh[k] >= lo[k] - 1e-12) and np.all(yh[k] <= hi[k] + 1e-12)
+
+
+def test_output_bias_gradient_sums_to_zero():
+    # a constant shift of all logits leaves the softmax unchanged, so the
+    # gradient of b3 sums to zero per pixel (a sign or term error breaks this)
+    params = phantom.apod_init(8, out_scale=1.0, bias_scale=0.3)
+    Xh, mask, t = _inputs(9, 10)
+    _, g = apod.loss_and_grad(params, Xh, mask, t)
+    gb3 = apod.unpack(g)["b3"]
+    assert abs(gb3.sum()) <= 1e-12 * np.max(np.abs(gb3)) * 128
+
+
+def test_single_active_element_has_no_gradient():
+    params = phantom.apod_init(10, out_scale=1.0, bias_scale=0.3)
+    Xh = np.zeros((1, 128))
+    mask = np.zeros((1, 128), bool)
+    Xh[0, 40], mask[0, 40] = -1.0, True
+    yh, w, _ = apod.forward(params, Xh, mask)
+    assert w[0, 40] == 1.0 and yh[0] == -1.0
+    loss, g = apod.loss_and_grad(params, Xh, mask, np.array([0.25]))
+    assert loss == pytest.approx(1.5625) and np.all(g == 0.0)
+
+
+def test_invalid_pixels_do_not_contribute():
+    params = phantom.apod_init(11, out_scale=1.0, bias_scale=0.1)
+    Xh, mask, t = _inputs(12, 8)
+    valid = np.array([1, 0, 1, 1, 0, 1, 1, 1], bool)
+    l1, g1 = apod.loss_and_grad(params, Xh, mask, t, valid)
+    l2, g2 = apod.loss_and_grad(params, Xh[valid], mask[valid], t[valid])
+    assert l1 == pytest.approx(l2, rel=1e-12)
+    np.testing.assert_allclose(g1, g2, rtol=1e-12, atol=1e-18)
+
+
+def test_adam_constant_gradient_closed_form():
+    # with a constant gradient g, the bias-corrected moments are exactly g and
+    # g^2 at every step, so each step moves by lr * g / (|g| + eps)
+    p0 = np.array([0.5, -1.0, 2.0, 0.0])
+    g = np.array([0.3, -2.0, 1e-9, 0.0])
+    lr, eps = 1e-2, 1e-8
+    p, m, v = p0.copy(), np.zeros(4), np.zeros(4)
+    for s in range(1, 6):
+        p, m, v = apod.adam(p, m, v, g, s, lr, eps=eps)
+    np.testing.assert_allclose(p, p0 - 5 * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_zero_output_layer_is_rectangular_das():
+    # W3 = 0, b3 = 0: uniform weights over the aperture, y = mean of the
+    # delayed samples = delay-and-sum with a rectangular window
+    s = phantom.linear_setup(16, 0.3e-3, 4, 300, fc=5e6, fs=40e6)
+    p = dict(s.params(), window="rect")
+    ch = phantom.random_channels(s, 21).numpy()
+    params = phantom.apod_init(22)
+    lines, depths = [0, 2, 3], list(range(0, 300, 13))
+    y = apod.beamform(p, ch, params, lines, depths)
+    ref = np.array([[oracle.das_points(p, [l], [i], [ch[s.line_tx[l]]])[0] for i in depths] for l in lines])
+    np.testing.assert_allclose(y, ref, rtol=1e-9, atol=1e-9 * np.max(np.abs(ref)))
