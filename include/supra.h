@@ -228,6 +228,59 @@ SUPRA_API int supra_bmode_batched(int32_t n, const supra_plan *const *plans, con
 SUPRA_API int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const int16_t *ch, float *rf,
                        void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned apodization.  The paper has no learned beamformer; this per-pixel
+ * network stands in for supra_mv at delay-and-sum cost.  For each pixel, x =
+ * the delayed samples of all n_el <= 128 elements (delays and F-number
+ * aperture of supra_beamform, 0 outside the aperture), xh = x / ||x||:
+ *   h1 = relu(W1 xh + b1), h2 = relu(W2 h1 + b2), z = W3 h2 + b3,
+ *   w = softmax of z over the aperture, y = sum_e w_e x_e.
+ * params: float [SUPRA_APOD_PARAMS] (device) = W1 [64][128], b1 [64],
+ * W2 [64][64], b2 [64], W3 [128][64], b3 [128], row-major [out][in].  The
+ * products run on BF16 tensor cores with FP32 accumulation (weights and
+ * activations rounded to BF16); softmax and output in FP32.
+ * Training data: a feature row per pixel = BF16 [128] (xh), mask = uint32 [4]
+ * (bit e of word e / 32 = element e in the aperture), norm = ||x|| (float),
+ * label = the target beamformed value (e.g. supra_mv); the loss is the mean
+ * over pixels with ||x|| > 0 of (sum_e w_e xh_e - label / ||x||)^2.
+ * Rows of pixel k: base + k * stride (stride >= 1 rows).  feat and mask must
+ * be 16-byte aligned.  All pointers are device pointers.
+ * ------------------------------------------------------------------------ */
+#define SUPRA_APOD_PARAMS 20736
+#define SUPRA_APOD_INPUTS 128
+
+/* Feature rows of every pixel of a frame, pixel index line * n_depth + i:
+ * feat bf16 [n_lines * n_depth][128], mask uint32 [..][4], norm float [..].
+ * Errors: SUPRA_EINVAL (n_el > 128, misaligned pointers). */
+SUPRA_API int supra_apod_features(const supra_plan *plan, const int16_t *ch, uint16_t *feat, uint32_t *mask,
+                                  float *norm, void *stream);
+
+/* Network on n feature rows: y[k * stride] = ||x|| * sum_e w_e xh_e. */
+SUPRA_API int supra_apod_forward(const float *params, int64_t n, int64_t stride, const uint16_t *feat,
+                                 const uint32_t *mask, const float *norm, float *y, void *stream);
+
+/* Bytes of workspace supra_apod_grad needs on the current device (per-CTA
+ * partial gradients). */
+SUPRA_API size_t supra_apod_workspace_size(void);
+
+/* Loss and its gradient over n rows: grad float [SUPRA_APOD_PARAMS], loss
+ * float [1] (may be NULL).  Deterministic for a given device.
+ * Errors: SUPRA_EINVAL, SUPRA_EWORKSPACE (workspace too small). */
+SUPRA_API int supra_apod_grad(const float *params, int64_t n, int64_t stride, const uint16_t *feat,
+                              const uint32_t *mask, const float *norm, const float *label, float *grad, float *loss,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
+/* One Adam step in place (step counts from 1; bias-corrected moments m, v,
+ * each float [SUPRA_APOD_PARAMS]). */
+SUPRA_API int supra_apod_adam(float *params, float *m, float *v, const float *grad, int32_t step, float lr,
+                              float beta1, float beta2, float eps, void *stream);
+
+/* Learned-apodization beamformer: rf float [n_lines][n_depth] from int16
+ * channels [n_tx][n_el][n_samples], delays, interpolation and aperture as in
+ * supra_beamform, weights from the network (one fused kernel).
+ * Errors: SUPRA_EINVAL (n_el > 128). */
+SUPRA_API int supra_apod_mlp(const supra_plan *plan, const float *params, const int16_t *ch, float *rf, void *stream);
+
 /* supra_bmode for callers that may not allocate device memory.  The paper has
  * no counterpart: it exists because some callers cannot provide the device
  * workspace supra_bmode needs -- e.g. a real-time acquisition loop that must

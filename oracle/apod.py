@@ -19,6 +19,14 @@ in for the exact minimum-variance beamformer, written out plainly:
 Parameters are one flat vector in the order W1, b1, W2, b2, W3, b3 (row-major
 matrices, [out][in]); 20 480 weights and 256 biases.  Optimiser: Adam with bias
 correction.
+
+Precision.  The method's products are BF16 x BF16 with FP32 accumulation.
+With bf16=True the oracle rounds every product operand to BF16 (round to
+nearest even) exactly where the method defines one -- weights, the layer
+inputs h1 and h2, and the output gradients dz, dz2, dz1 -- and keeps FP64 for
+everything else, so the ReLU decisions are taken on the same values as the
+kernels take them.  Biases, softmax, loss and Adam are never rounded.  With
+bf16=False (default) everything is FP64.
 """
 from __future__ import annotations
 
@@ -30,6 +38,19 @@ N_IN, N_H1, N_H2 = 128, 64, 64
 SHAPES = (("W1", (N_H1, N_IN)), ("b1", (N_H1,)), ("W2", (N_H2, N_H1)), ("b2", (N_H2,)),
           ("W3", (N_IN, N_H2)), ("b3", (N_IN,)))
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def round_bf16(a) -> np.ndarray:
+    """Nearest BFloat16 value (ties to even) of each element, as float64:
+    the float32 value's top 16 bits after round-to-nearest-even."""
+    f = np.asarray(a, np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _q(a, bf16: bool):
+    return round_bf16(a) if bf16 else np.asarray(a, np.float64)
 
 
 def unpack(params) -> dict:
@@ -59,17 +80,23 @@ def features(p: dict, ch_tx, line: int, i: int):
     return x, mask
 
 
-def forward(params, X, mask):
+def forward(params, X, mask, bf16: bool = False, x_scale=None):
     """Network on a batch: X[B,128] normalised inputs xh, mask[B,128].
-    Returns (yh[B], w[B,128], cache)."""
+    x_scale[B] (optional): X holds unnormalised samples and xh = X * x_scale,
+    applied after the first product (the fused beamformer's form).
+    Returns (yh[B], w[B,128], cache); yh = sum_e w_e X_e."""
     P = unpack(params)
-    X = np.asarray(X, np.float64)
+    X = _q(X, bf16)
     mask = np.asarray(mask, bool)
-    z1 = X @ P["W1"].T + P["b1"]
-    h1 = np.maximum(z1, 0.0)
-    z2 = h1 @ P["W2"].T + P["b2"]
-    h2 = np.maximum(z2, 0.0)
-    z = h2 @ P["W3"].T + P["b3"]
+    W1, W2, W3 = (_q(P[k], bf16) for k in ("W1", "W2", "W3"))
+    z1 = X @ W1.T
+    if x_scale is not None:
+        z1 = z1 * np.asarray(x_scale, np.float64)[:, None]
+    z1 = z1 + P["b1"]
+    h1 = _q(np.maximum(z1, 0.0), bf16)
+    z2 = h1 @ W2.T + P["b2"]
+    h2 = _q(np.maximum(z2, 0.0), bf16)
+    z = h2 @ W3.T + P["b3"]
     # masked softmax, shifted by the masked maximum
     zm = np.where(mask, z, -np.inf)
     zmax = np.max(zm, axis=1, keepdims=True)
@@ -81,29 +108,32 @@ def forward(params, X, mask):
     return yh, w, (X, z1, h1, z2, h2, w)
 
 
-def loss_and_grad(params, X, mask, t, valid=None):
+def loss_and_grad(params, X, mask, t, valid=None, bf16: bool = False):
     """Mean squared error over the valid pixels and its gradient with respect to
-    the flat parameters (reverse-mode chain rule written out layer by layer)."""
+    the flat parameters (reverse-mode chain rule written out layer by layer).
+    The per-pixel output gradients are formed unnormalised (2 (yh - t)) and the
+    sums divided by the pixel count at the end."""
     P = unpack(params)
     t = np.asarray(t, np.float64)
     valid = np.ones(len(t), bool) if valid is None else np.asarray(valid, bool)
     n = int(valid.sum())
-    yh, w, (X, z1, h1, z2, h2, _) = forward(params, X, mask)
+    yh, w, (X, z1, h1, z2, h2, _) = forward(params, X, mask, bf16)
     if n == 0:
         return 0.0, np.zeros(N_PARAMS)
+    W2, W3 = _q(P["W2"], bf16), _q(P["W3"], bf16)
     r = np.where(valid, yh - t, 0.0)
     loss = float(np.sum(r * r) / n)
-    dyh = 2.0 * r / n                                   # d loss / d yh
+    dyh = 2.0 * r                                       # n * d loss / d yh
     # yh = sum_e w_e x_e, w = softmax(z):  d yh / d z_e = w_e (x_e - yh)
-    dz = w * (X - yh[:, None]) * dyh[:, None]
+    dz = _q(w * (X - yh[:, None]) * dyh[:, None], bf16)
     g = {"W3": dz.T @ h2, "b3": dz.sum(axis=0)}
-    dh2 = dz @ P["W3"]
-    dz2 = dh2 * (z2 > 0)
+    dh2 = dz @ W3
+    dz2 = _q(dh2 * (z2 > 0), bf16)
     g["W2"], g["b2"] = dz2.T @ h1, dz2.sum(axis=0)
-    dh1 = dz2 @ P["W2"]
-    dz1 = dh1 * (z1 > 0)
+    dh1 = dz2 @ W2
+    dz1 = _q(dh1 * (z1 > 0), bf16)
     g["W1"], g["b1"] = dz1.T @ X, dz1.sum(axis=0)
-    return loss, pack(g)
+    return loss, pack(g) / n
 
 
 def adam(params, m, v, grad, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -137,11 +167,18 @@ def batch(p: dict, ch, labels=None, lines=None, depths=None):
     return np.array(xs), np.array(ms), np.array(ns), (np.array(ts) if labels is not None else None)
 
 
-def beamform(p: dict, ch, params, lines=None, depths=None) -> np.ndarray:
+def beamform(p: dict, ch, params, lines=None, depths=None, bf16: bool = False) -> np.ndarray:
     """Learned-apodization output y = sum_e w_e x_e at the selected pixels,
-    [len(lines), len(depths)]."""
+    [len(lines), len(depths)].  With bf16=True the raw samples x enter the
+    first product in BF16 and 1 / ||x|| scales its result (the fused
+    beamformer's form); y = sum_e w_e bf16(x_e)."""
     lines = list(range(len(p["line_tx"]))) if lines is None else list(lines)
     depths = list(range(int(p["n_depth"]))) if depths is None else list(depths)
     X, mask, norm, _ = batch(p, ch, None, lines, depths)
+    if bf16:
+        raw = X * norm[:, None]
+        inv = np.divide(1.0, norm, out=np.zeros_like(norm), where=norm > 0)
+        y, _, _ = forward(params, raw, mask, True, x_scale=inv)
+        return y.reshape(len(lines), len(depths))
     yh, _, _ = forward(params, X, mask)
     return (yh * norm).reshape(len(lines), len(depths))

@@ -25,8 +25,10 @@ GEOMETRIES = {"linear": 0, "sector": 1, "pyramid": 2}
 
 EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "supra_beamform", "supra_envelope",
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
-           "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_device_status", "supra_strerror",
-           "supra_version")
+           "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_apod_features", "supra_apod_forward",
+           "supra_apod_workspace_size", "supra_apod_grad", "supra_apod_adam", "supra_apod_mlp",
+           "supra_device_status", "supra_strerror", "supra_version")
+APOD_PARAMS, APOD_INPUTS = 20736, 128
 
 
 class SupraError(RuntimeError):
@@ -100,6 +102,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                         ctypes.c_size_t, P]
     lib.supra_bmode_noalloc.argtypes = [P, P, P, P]
     lib.supra_mv.argtypes = [P, ctypes.c_int32, ctypes.c_float, P, P, P]
+    I64, F = ctypes.c_int64, ctypes.c_float
+    lib.supra_apod_features.argtypes = [P, P, P, P, P, P]
+    lib.supra_apod_forward.argtypes = [P, I64, I64, P, P, P, P, P]
+    lib.supra_apod_workspace_size.argtypes = []
+    lib.supra_apod_workspace_size.restype = ctypes.c_size_t
+    lib.supra_apod_grad.argtypes = [P, I64, I64, P, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.supra_apod_adam.argtypes = [P, P, P, P, ctypes.c_int32, F, F, F, F, P]
+    lib.supra_apod_mlp.argtypes = [P, P, P, P, P]
     lib.supra_device_status.argtypes = [ctypes.c_int32]
     lib.supra_strerror.argtypes = [ctypes.c_int]
     lib.supra_strerror.restype = ctypes.c_char_p
@@ -275,6 +285,37 @@ class Plan:
                                _dev_tensor(ch, torch.int16, self.ch_shape, "ch"),
                                _dev_tensor(rf, torch.float32, self.line_shape, "rf"), _stream_ptr(stream)), "supra_mv")
         return rf
+
+    def apod(self, ch, params, rf=None, stream=None):
+        """Learned-apodization beamformer (supra_apod_mlp): params float32
+        [APOD_PARAMS] on the device."""
+        import torch
+
+        if rf is None:
+            rf = torch.empty(self.line_shape, dtype=torch.float32, device=ch.device)
+        _check(load().supra_apod_mlp(self.handle, _dev_tensor(params, torch.float32, (APOD_PARAMS,), "params"),
+                                     _dev_tensor(ch, torch.int16, self.ch_shape, "ch"),
+                                     _dev_tensor(rf, torch.float32, self.line_shape, "rf"), _stream_ptr(stream)),
+               "supra_apod_mlp")
+        return rf
+
+    def apod_features(self, ch, feat=None, mask=None, norm=None, stream=None):
+        """Network inputs of every pixel (supra_apod_features): feat bfloat16
+        [n_lines * n_depth, 128] (x / ||x||), mask int32 [.., 4] (aperture
+        bits), norm float32 [..]."""
+        import torch
+
+        P = self.n_lines * self.n_depth
+        dev = ch.device
+        feat = torch.empty((P, APOD_INPUTS), dtype=torch.bfloat16, device=dev) if feat is None else feat
+        mask = torch.empty((P, 4), dtype=torch.int32, device=dev) if mask is None else mask
+        norm = torch.empty((P,), dtype=torch.float32, device=dev) if norm is None else norm
+        _check(load().supra_apod_features(self.handle, _dev_tensor(ch, torch.int16, self.ch_shape, "ch"),
+                                          _dev_tensor(feat, torch.bfloat16, (P, APOD_INPUTS), "feat"),
+                                          _dev_tensor(mask, torch.int32, (P, 4), "mask"),
+                                          _dev_tensor(norm, torch.float32, (P,), "norm"), _stream_ptr(stream)),
+               "supra_apod_features")
+        return feat, mask, norm
 
     # ---- fused chain -----------------------------------------------------
     def bmode(self, ch, out=None, workspace=None, stream=None):

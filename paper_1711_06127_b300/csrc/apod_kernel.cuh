@@ -1,0 +1,521 @@
+// apod_kernel.cuh -- learned apodization: a per-pixel network that maps the
+// delayed channel samples of the aperture to softmax-normalised element
+// weights.  Not in the paper; it stands in for the exact minimum-variance
+// beamformer (it is trained on MV outputs) at delay-and-sum cost.
+//
+//   xh = x / ||x||,  h1 = relu(W1 xh + b1),  h2 = relu(W2 h1 + b2),
+//   z = W3 h2 + b3,  w = softmax of z over the aperture,  y = sum_e w_e x_e.
+//
+// One CTA = 128 threads = one tile of 128 pixels; thread t owns pixel t, which
+// is also TMEM lane t of every M = 128 accumulator.  The three layers and, in
+// training, the two activation-gradient products and the three weight-gradient
+// products run as BF16 tcgen05 MMAs with FP32 accumulators in tensor memory;
+// ReLU, the masked softmax and its backward pass run per thread between them.
+// Weight gradients accumulate in tensor memory across all tiles of a CTA and
+// are written once, as per-CTA partials (deterministic reduction afterwards).
+//
+// Bias gradients come from the same MMAs: the B operands of the weight-gradient
+// products carry 16 extra columns of ones ([H2 | 1], [H1 | 1], [X | 1]), so the
+// accumulator column past the weights is sum over pixels of the output
+// gradient.  The 64-row weight-gradient products (dW2, dW1) are issued with
+// M = 128; rows 64..127 read the next buffer and are discarded.
+#pragma once
+#include <cuda_bf16.h>
+#include "common.cuh"
+#include "gather.cuh"
+#include "tc.cuh"
+
+namespace supra {
+namespace apod {
+
+constexpr int kIn = 128, kH1 = 64, kH2 = 64, kTile = 128;
+// flat parameter vector: W1 [64][128], b1, W2 [64][64], b2, W3 [128][64], b3
+constexpr int kOffW1 = 0, kOffB1 = 8192, kOffW2 = 8256, kOffB2 = 12352, kOffW3 = 12416, kOffB3 = 20608;
+constexpr int kParams = 20736;
+constexpr int kPartStride = kParams + 2;   // + loss sum, valid-pixel count
+enum { kForward = 0, kTrain = 1, kInfer = 2 };
+
+// Shared-memory images, byte offsets.  A "[rows][cols] buffer" keeps 16-byte
+// chunks of 8 columns: chunk j of row r at j * 2048 + r * 16 (128 rows).
+template <int MODE>
+struct Smem {
+    static constexpr bool T = MODE == kTrain;
+    static constexpr int W1 = 0;        // [hid1][in]:  chunk j of row n at j * 1024 + n * 16
+    static constexpr int W2 = 16384;    // [hid2][hid1]: j * 1024 + n * 16
+    static constexpr int W3 = 24576;    // [out][hid2]:  j * 2048 + n * 16
+    static constexpr int X = 40960;     // [pix][in] (+ 2 chunks of ones when training)
+    static constexpr int H1 = X + (T ? 36864 : 32768);   // [pix][hid1] (+ 2 chunks of ones)
+    static constexpr int H2 = H1 + (T ? 20480 : 16384);  // [pix][hid2] (+ 2 chunks of ones)
+    static constexpr int DZ2 = H2 + (T ? 20480 : 16384); // [pix][hid2]
+    static constexpr int DZ1 = DZ2 + (T ? 16384 : 0);    // [pix][hid1]
+    static constexpr int DZ3 = DZ1 + (T ? 16384 : 0);    // [pix][out]
+    static constexpr int BIAS = DZ3 + (T ? 32768 : 0);   // float b1[64], b2[64], b3[128]
+    static constexpr int TOTAL = BIAS + 256 * 4;
+};
+static_assert(Smem<kTrain>::TOTAL <= 227 * 1024, "training tile exceeds shared memory");
+static_assert(2 * (Smem<kInfer>::TOTAL + 1024) <= 228 * 1024, "two inference CTAs per SM");
+// dW2 / dW1 read 128 rows (32 KB) from DZ2 / DZ1: the next buffers must follow
+static_assert(Smem<kTrain>::DZ1 == Smem<kTrain>::DZ2 + 16384 && Smem<kTrain>::DZ3 == Smem<kTrain>::DZ1 + 16384,
+              "padded weight-gradient operands");
+
+// tensor-memory columns
+constexpr uint32_t kT64 = 0, kT128 = 64, kDW3 = 192, kDW2 = 272, kDW1 = 352;
+
+struct Args {
+    const float *params;
+    // kForward / kTrain: feature rows (bf16 [.][128]), masks (u32 [.][4]), norms, labels
+    const uint16_t *feat;
+    const uint32_t *mask;
+    const float *norm;
+    const float *label;
+    long long n, stride;   // pixels; rows between consecutive pixels
+    float *y;              // kForward: y = ||x|| * yh per pixel
+    float *partial;        // kTrain: [gridDim.x][kPartStride]
+    // kInfer
+    const DevPlan *plan;
+    const int16_t *ch;
+    float *rf;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ uint4 pack8(const float *v) {
+    return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+__device__ __forceinline__ void unpack8(uint4 u, float *v) {
+    v[0] = bf_lo(u.x), v[1] = bf_hi(u.x), v[2] = bf_lo(u.y), v[3] = bf_hi(u.y);
+    v[4] = bf_lo(u.z), v[5] = bf_hi(u.z), v[6] = bf_lo(u.w), v[7] = bf_hi(u.w);
+}
+__device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int row) {
+    return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
+}
+
+// K steps of one MMA chain, issued by one thread (2 core matrices along K per step).
+__device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo, uint32_t a_sbo, uint32_t b,
+                                          uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc, int ksteps, bool acc) {
+    for (int s = 0; s < ksteps; ++s)
+        tc::mma_bf16(d, tc::smem_desc(a + 2u * s * a_lbo, a_lbo, a_sbo), tc::smem_desc(b + 2u * s * b_lbo, b_lbo, b_sbo),
+                     idesc, acc || s > 0);
+}
+
+template <int MODE>
+__device__ __forceinline__ void stage_weights(const float *__restrict__ prm, unsigned char *sm, int t) {
+    using S = Smem<MODE>;
+    for (int k = t; k < kH1 * kIn; k += kTile) {
+        const int n = k >> 7, i = k & 127;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + S::W1 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
+            __float2bfloat16_rn(prm[kOffW1 + k]);
+    }
+    for (int k = t; k < kH2 * kH1; k += kTile) {
+        const int n = k >> 6, i = k & 63;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + S::W2 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
+            __float2bfloat16_rn(prm[kOffW2 + k]);
+    }
+    for (int k = t; k < kIn * kH2; k += kTile) {
+        const int n = k >> 6, i = k & 63;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + S::W3 + (i >> 3) * 2048 + n * 16 + (i & 7) * 2) =
+            __float2bfloat16_rn(prm[kOffW3 + k]);
+    }
+    float *bias = reinterpret_cast<float *>(sm + S::BIAS);
+    for (int k = t; k < 256; k += kTile)
+        bias[k] = k < 64 ? prm[kOffB1 + k] : k < 128 ? prm[kOffB2 + k - 64] : prm[kOffB3 + k - 128];
+}
+
+// Wait for the next commit of the MMA barrier; false after ~1 s.
+__device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t &phase) {
+    const bool ok = mbar_wait_bounded(bar, phase & 1u, 1LL << 31);
+    ++phase;
+    tc::fence_after_sync();
+    return ok;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(const Args a) {
+    using S = Smem<MODE>;
+    constexpr uint32_t kCols = MODE == kTrain ? 512 : 256;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float red[2][4];
+    const int t = threadIdx.x, warp = t >> 5;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
+    stage_weights<MODE>(a.params, sm, t);
+    if (MODE == kTrain) {
+        const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        chunk(sm, S::X, 16, t) = ones;
+        chunk(sm, S::X, 17, t) = ones;
+        chunk(sm, S::H1, 8, t) = ones;
+        chunk(sm, S::H1, 9, t) = ones;
+        chunk(sm, S::H2, 8, t) = ones;
+        chunk(sm, S::H2, 9, t) = ones;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_base, lane = (uint32_t)(32 * warp) << 16;
+    const uint32_t sb = tc::smem_u32(sm);
+    const float *b1 = reinterpret_cast<const float *>(sm + S::BIAS), *b2 = b1 + 64, *b3 = b1 + 128;
+    constexpr uint32_t kI64 = tc::idesc_bf16(128, 64, false, false), kI128 = tc::idesc_bf16(128, 128, false, false);
+
+    long long n_tiles;
+    int nblk = 1, nd = 0;
+    if (MODE == kInfer) {
+        nd = a.plan->n_depth;
+        nblk = (nd + kTile - 1) / kTile;
+        n_tiles = (long long)a.plan->n_lines * nblk;
+    } else {
+        n_tiles = (a.n + kTile - 1) / kTile;
+    }
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    float loss_acc = 0.0f, cnt_acc = 0.0f;
+
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // ---- inputs: one row of X per thread
+        uint32_t mk[4] = {0u, 0u, 0u, 0u};
+        float nrm = 0.0f, tgt = 0.0f;
+        bool row_ok;
+        long long p = 0;
+        int line = 0, i = 0;
+        if (MODE == kInfer) {
+            line = (int)(tile / nblk);
+            i = (int)(tile % nblk) * kTile + t;
+            row_ok = i < nd;
+            float n2 = 0.0f;
+            const int n_el = a.plan->n_el;
+            PixelGeo g;
+            if (row_ok) g = pixel_geo(a.plan, a.ch, line, i);
+#pragma unroll 1
+            for (int c = 0; c < 16; ++c) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int e = 8 * c + j;
+                    bool act = false;
+                    v[j] = (row_ok && e < n_el) ? element_sample(a.plan, g, e, act) : 0.0f;
+                    n2 = fmaf(v[j], v[j], n2);
+                    if (act) mk[e >> 5] |= 1u << (e & 31);
+                }
+                chunk(sm, S::X, c, t) = pack8(v);
+            }
+            nrm = sqrtf(n2);
+        } else {
+            p = tile * kTile + t;
+            row_ok = p < a.n;
+            const long long row = p * a.stride;
+            if (row_ok) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + row * kIn);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) chunk(sm, S::X, c, t) = __ldg(src + c);
+                const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + row);
+                mk[0] = m4.x, mk[1] = m4.y, mk[2] = m4.z, mk[3] = m4.w;
+                nrm = __ldg(a.norm + row);
+                if (MODE == kTrain) tgt = nrm > 0.0f ? __ldg(a.label + row) / nrm : 0.0f;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) chunk(sm, S::X, c, t) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        const bool valid = row_ok && nrm > 0.0f;
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc::fence_after_sync();
+
+        // ---- Z1 = X W1^T
+        if (t == 0) {
+            mma_chain(tm + kT64, sb + S::X, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
+            tc::mma_commit(&bar);
+        }
+        ok = mma_wait(&bar, phase) && ok;
+        const float scale = (MODE == kInfer) ? (nrm > 0.0f ? 1.0f / nrm : 0.0f) : 1.0f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float v[32];
+            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = fmaxf(fmaf(v[j], scale, b1[32 * q + j]), 0.0f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) chunk(sm, S::H1, 4 * q + c, t) = pack8(v + 8 * c);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc::fence_after_sync();
+
+        // ---- Z2 = H1 W2^T
+        if (t == 0) {
+            mma_chain(tm + kT64, sb + S::H1, 2048, 128, sb + S::W2, 1024, 128, kI64, 4, false);
+            tc::mma_commit(&bar);
+        }
+        ok = mma_wait(&bar, phase) && ok;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float v[32];
+            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + b2[32 * q + j], 0.0f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) chunk(sm, S::H2, 4 * q + c, t) = pack8(v + 8 * c);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc::fence_after_sync();
+
+        // ---- Z3 = H2 W3^T, masked softmax, output (and its gradient)
+        if (t == 0) {
+            mma_chain(tm + kT128, sb + S::H2, 2048, 128, sb + S::W3, 2048, 128, kI128, 4, false);
+            tc::mma_commit(&bar);
+        }
+        ok = mma_wait(&bar, phase) && ok;
+        float zmax = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[32];
+            tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if ((mk[q] >> j) & 1u) zmax = fmaxf(zmax, v[j] + b3[32 * q + j]);
+        }
+        float se = 0.0f, sx = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[32], x[32];
+            tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, t), x + 8 * c);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
+                se += ez;
+                sx = fmaf(ez, x[j], sx);
+            }
+        }
+        const float yh = se > 0.0f ? sx / se : 0.0f;
+        if (MODE == kForward) {
+            if (row_ok) a.y[p * a.stride] = yh * nrm;
+        } else if (MODE == kInfer) {
+            if (row_ok) a.rf[(long long)line * nd + i] = yh;
+        } else {
+            const float r = valid ? yh - tgt : 0.0f;
+            loss_acc = fmaf(r, r, loss_acc);
+            cnt_acc += valid ? 1.0f : 0.0f;
+            const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[32], x[32];
+                tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, t), x + 8 * c);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float pe = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
+                    v[j] = pe * (x[j] - yh) * g;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, t) = pack8(v + 8 * c);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc::fence_after_sync();
+        if (MODE != kTrain) continue;
+
+        // ---- dH2 = dZ3 W3;  [dW3 | db3] += dZ3^T [H2 | 1]
+        if (t == 0) {
+            mma_chain(tm + kT64, sb + S::DZ3, 2048, 128, sb + S::W3, 128, 2048, tc::idesc_bf16(128, 64, false, true), 8,
+                      false);
+            mma_chain(tm + kDW3, sb + S::DZ3, 128, 2048, sb + S::H2, 128, 2048, tc::idesc_bf16(128, 80, true, true), 8,
+                      !first);
+            tc::mma_commit(&bar);
+        }
+        ok = mma_wait(&bar, phase) && ok;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float v[32], h[32];
+            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H2, 4 * q + c, t), h + 8 * c);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ2, 4 * q + c, t) = pack8(v + 8 * c);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc::fence_after_sync();
+
+        // ---- dH1 = dZ2 W2;  [dW2 | db2] += dZ2^T [H1 | 1]
+        if (t == 0) {
+            mma_chain(tm + kT64, sb + S::DZ2, 2048, 128, sb + S::W2, 128, 1024, tc::idesc_bf16(128, 64, false, true), 4,
+                      false);
+            mma_chain(tm + kDW2, sb + S::DZ2, 128, 2048, sb + S::H1, 128, 2048, tc::idesc_bf16(128, 80, true, true), 8,
+                      !first);
+            tc::mma_commit(&bar);
+        }
+        ok = mma_wait(&bar, phase) && ok;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float v[32], h[32];
+            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H1, 4 * q + c, t), h + 8 * c);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ1, 4 * q + c, t) = pack8(v + 8 * c);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc::fence_after_sync();
+
+        // ---- [dW1 | db1] += dZ1^T [X | 1]; complete before X and DZ1 are rewritten
+        if (t == 0) {
+            mma_chain(tm + kDW1, sb + S::DZ1, 128, 2048, sb + S::X, 128, 2048, tc::idesc_bf16(128, 144, true, true), 8,
+                      !first);
+            tc::mma_commit(&bar);
+        }
+        ok = mma_wait(&bar, phase) && ok;
+        first = false;
+    }
+    ok = __syncthreads_and(ok);   // the last wait of a tile is not followed by a barrier
+    if (!ok && t == 0) set_status(SUPRA_ETIMEOUT);
+
+    if (MODE == kTrain) {
+        float *part = a.partial + (long long)blockIdx.x * kPartStride;
+        // weight and bias gradients (unnormalised sums over this CTA's pixels)
+        float v[32], w[16];
+        if (ok && !first) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                tc::tmem_ld32(tm + lane + kDW3 + 32 * q, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) part[kOffW3 + t * 64 + 32 * q + j] = v[j];
+            }
+            tc::tmem_ld16(tm + lane + kDW3 + 64, w);
+            part[kOffB3 + t] = w[0];
+            if (warp < 2) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    tc::tmem_ld32(tm + lane + kDW2 + 32 * q, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) part[kOffW2 + t * 64 + 32 * q + j] = v[j];
+                }
+                tc::tmem_ld16(tm + lane + kDW2 + 64, w);
+                part[kOffB2 + t] = w[0];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    tc::tmem_ld32(tm + lane + kDW1 + 32 * q, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) part[kOffW1 + t * 128 + 32 * q + j] = v[j];
+                }
+                tc::tmem_ld16(tm + lane + kDW1 + 128, w);
+                part[kOffB1 + t] = w[0];
+            }
+        } else {
+            for (int k = t; k < kParams; k += kTile) part[k] = 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+            cnt_acc += __shfl_xor_sync(0xffffffffu, cnt_acc, o);
+        }
+        if ((t & 31) == 0) red[0][warp] = loss_acc, red[1][warp] = cnt_acc;
+        __syncthreads();
+        if (t == 0) {
+            part[kParams] = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+            part[kParams + 1] = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tm, kCols);
+}
+
+// Network inputs of every pixel of a frame: x / ||x|| in BF16 [line * n_depth + i][128],
+// aperture mask (bit e of word e / 32) and ||x||.  Two passes over the elements
+// (norm, then normalised samples).
+__global__ void __launch_bounds__(128) features_kernel(const DevPlan *__restrict__ P, const int16_t *__restrict__ ch,
+                                                       uint16_t *__restrict__ feat, uint32_t *__restrict__ mask,
+                                                       float *__restrict__ norm) {
+    const int line = blockIdx.y, i = blockIdx.x * 128 + threadIdx.x, nd = P->n_depth;
+    if (i >= nd) return;
+    const PixelGeo g = pixel_geo(P, ch, line, i);
+    const int n_el = P->n_el;
+    float n2 = 0.0f;
+    for (int e = 0; e < n_el; ++e) {
+        bool act;
+        const float x = element_sample(P, g, e, act);
+        n2 = fmaf(x, x, n2);
+    }
+    const float nr = sqrtf(n2), inv = nr > 0.0f ? 1.0f / nr : 0.0f;
+    const long long pix = (long long)line * nd + i;
+    uint32_t mk[4] = {0u, 0u, 0u, 0u};
+    uint4 *dst = reinterpret_cast<uint4 *>(feat + pix * kIn);
+#pragma unroll 1
+    for (int c = 0; c < 16; ++c) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = 8 * c + j;
+            bool act = false;
+            v[j] = e < n_el ? element_sample(P, g, e, act) * inv : 0.0f;
+            if (act) mk[e >> 5] |= 1u << (e & 31);
+        }
+        dst[c] = pack8(v);
+    }
+    reinterpret_cast<uint4 *>(mask)[pix] = make_uint4(mk[0], mk[1], mk[2], mk[3]);
+    norm[pix] = nr;
+}
+
+// grad = sum of per-CTA partials / valid-pixel count (FP64 sums in CTA order);
+// thread kParams writes the loss.
+__global__ void reduce_kernel(const float *__restrict__ partial, int n_parts, float *__restrict__ grad,
+                              float *__restrict__ loss) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > kParams) return;
+    double cnt = 0.0, s = 0.0;
+    for (int c = 0; c < n_parts; ++c) {
+        cnt += partial[(long long)c * kPartStride + kParams + 1];
+        s += partial[(long long)c * kPartStride + j];
+    }
+    const double v = cnt > 0.0 ? s / cnt : 0.0;
+    if (j < kParams) grad[j] = (float)v;
+    else if (loss) *loss = (float)v;
+}
+
+// Adam with bias correction (c1 = 1 / (1 - beta1^step), c2 = 1 / (1 - beta2^step)).
+__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int n, float lr, float beta1, float beta2, float eps, float c1,
+                            float c2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float gj = g[j];
+    const float mj = fmaf(beta1, m[j], (1.0f - beta1) * gj);
+    const float vj = fmaf(beta2, v[j], (1.0f - beta2) * gj * gj);
+    m[j] = mj;
+    v[j] = vj;
+    p[j] -= lr * (mj * c1) / (sqrtf(vj * c2) + eps);
+}
+
+}  // namespace apod
+}  // namespace supra

@@ -13,6 +13,7 @@
 #include "das_kernel.cuh"
 #include "post_kernels.cuh"
 #include "mv_kernel.cuh"
+#include "apod_kernel.cuh"
 
 using namespace supra;
 
@@ -227,6 +228,30 @@ void ScanBatch::add(const supra_plan *p, const uint8_t *bm, uint8_t *img) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- learned-apodization launch helpers
+
+static int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <int MODE>
+static int launch_apod(const apod::Args &a, long long n_tiles, int per_sm, cudaStream_t st, int *grid_out = nullptr) {
+    const int sms = device_sms();
+    if (sms <= 0) return SUPRA_ECUDA;
+    const int grid = (int)std::min<long long>(n_tiles, (long long)sms * per_sm);
+    if (grid_out) *grid_out = grid;
+    const int smem = apod::Smem<MODE>::TOTAL;
+    if (cudaFuncSetAttribute(apod::apod_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return SUPRA_ECUDA;
+    apod::apod_kernel<MODE><<<grid, apod::kTile, smem, st>>>(a);
+    return check_cuda(cudaGetLastError());
+}
 
 extern "C" {
 
@@ -765,6 +790,72 @@ int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const i
         mv_kernel<double><<<grid, w * 32, 0, st>>>(plan->dev, ch, rf, subaperture, loading);
     }
     return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- learned apodization
+
+size_t supra_apod_workspace_size(void) {
+    return (size_t)std::max(device_sms(), 1) * apod::kPartStride * sizeof(float);
+}
+
+int supra_apod_features(const supra_plan *plan, const int16_t *ch, uint16_t *feat, uint32_t *mask, float *norm,
+                        void *stream) {
+    if (!plan || !ch || !feat || !mask || !norm) return SUPRA_EINVAL;
+    if (plan->host.n_el > apod::kIn || !aligned16(feat) || !aligned16(mask)) return SUPRA_EINVAL;
+    const dim3 grid((plan->host.n_depth + 127) / 128, plan->host.n_lines);
+    apod::features_kernel<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(plan->dev, ch, feat, mask, norm);
+    return check_cuda(cudaGetLastError());
+}
+
+int supra_apod_forward(const float *params, int64_t n, int64_t stride, const uint16_t *feat, const uint32_t *mask,
+                       const float *norm, float *y, void *stream) {
+    if (!params || !feat || !mask || !norm || !y || n <= 0 || stride < 1) return SUPRA_EINVAL;
+    if (!aligned16(feat) || !aligned16(mask)) return SUPRA_EINVAL;
+    apod::Args a{};
+    a.params = params, a.feat = feat, a.mask = mask, a.norm = norm, a.n = n, a.stride = stride, a.y = y;
+    return launch_apod<apod::kForward>(a, (n + apod::kTile - 1) / apod::kTile, 2, static_cast<cudaStream_t>(stream));
+}
+
+int supra_apod_grad(const float *params, int64_t n, int64_t stride, const uint16_t *feat, const uint32_t *mask,
+                    const float *norm, const float *label, float *grad, float *loss, void *workspace,
+                    size_t workspace_bytes, void *stream) {
+    if (!params || !feat || !mask || !norm || !label || !grad || !workspace || n <= 0 || stride < 1)
+        return SUPRA_EINVAL;
+    if (!aligned16(feat) || !aligned16(mask)) return SUPRA_EINVAL;
+    const long long tiles = (n + apod::kTile - 1) / apod::kTile;
+    const int sms = device_sms();
+    if (sms <= 0) return SUPRA_ECUDA;
+    const int grid = (int)std::min<long long>(tiles, sms);
+    if (workspace_bytes < (size_t)grid * apod::kPartStride * sizeof(float)) return SUPRA_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    apod::Args a{};
+    a.params = params, a.feat = feat, a.mask = mask, a.norm = norm, a.label = label, a.n = n, a.stride = stride;
+    a.partial = static_cast<float *>(workspace);
+    const int rc = launch_apod<apod::kTrain>(a, tiles, 1, st);
+    if (rc != SUPRA_OK) return rc;
+    apod::reduce_kernel<<<(apod::kParams + 1 + 255) / 256, 256, 0, st>>>(a.partial, grid, grad, loss);
+    return check_cuda(cudaGetLastError());
+}
+
+int supra_apod_adam(float *params, float *m, float *v, const float *grad, int32_t step, float lr, float beta1,
+                    float beta2, float eps, void *stream) {
+    if (!params || !m || !v || !grad || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return SUPRA_EINVAL;
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
+    apod::adam_kernel<<<(apod::kParams + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        params, m, v, grad, apod::kParams, lr, beta1, beta2, eps, c1, c2);
+    return check_cuda(cudaGetLastError());
+}
+
+int supra_apod_mlp(const supra_plan *plan, const float *params, const int16_t *ch, float *rf, void *stream) {
+    if (!plan || !params || !ch || !rf) return SUPRA_EINVAL;
+    if (plan->host.n_el > apod::kIn) return SUPRA_EINVAL;
+    apod::Args a{};
+    a.params = params, a.plan = plan->dev, a.ch = ch, a.rf = rf;
+    const long long tiles = (long long)plan->host.n_lines * ((plan->host.n_depth + apod::kTile - 1) / apod::kTile);
+    return launch_apod<apod::kInfer>(a, tiles, 2, static_cast<cudaStream_t>(stream));
 }
 
 int supra_device_status(int32_t clear) {

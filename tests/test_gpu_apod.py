@@ -1,0 +1,249 @@
+"""GPU parity of the learned apodization (feature rows, forward, gradient,
+Adam, fused inference) against the FP64 oracle, plus training behaviour.
+
+Tolerances.  The method's products are BF16 x BF16 with FP32 accumulation;
+softmax, loss and Adam run in FP32.  The oracle's bf16 mode rounds the same
+operands (weights, layer inputs, output gradients) and computes the rest in
+FP64, so both sides take the same ReLU decisions; what remains is FP32 against
+FP64 accumulation and exp (~1e-6 relative) and the rare BF16 rounding tie that
+the two accumulations resolve differently (one BF16 ulp, 2^-8, on one operand
+element).  Outputs and gradients: max |gpu - oracle| <= 2e-3 of the largest
+magnitude; the fused beamformer adds the FP32 delay error of the gather
+(~1e-4 of ||x|| per sample on white-noise records), 5e-3.  Against the plain
+FP64 network (no rounding) the BF16 network stays within 1e-1 (a ReLU decision
+that flips near zero moves a whole pixel's contribution).  Adam: 1e-5 relative.
+Bit equality where the same pixels are processed in the same order.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import apod as oapod
+import paper_1711_06127_b300 as supra
+from paper_1711_06127_b300 import apod
+import phantom
+from _setups import small_linear
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-3          # against the oracle's bf16 mode
+TOL_INFER = 5e-3    # fused beamformer (adds the gather's FP32 delay error)
+TOL_FP64 = 1e-1     # against the unrounded FP64 network
+
+
+def _bf16(a):
+    return torch.as_tensor(np.asarray(a, np.float32)).to(torch.bfloat16)
+
+
+def _rows(seed, n, min_active=2, zero_rows=()):
+    """Random rows for both sides: feature rows bf16(x / ||x||) on the device,
+    the same rounded values in FP64 for the oracle."""
+    X, mask, norm, t = phantom.apod_random_batch(seed, n, min_active)
+    for r in zero_rows:
+        X[r], norm[r] = 0.0, 0.0
+    xh = np.divide(X, norm[:, None], out=np.zeros_like(X), where=norm[:, None] > 0)
+    feat = _bf16(xh)
+    xh64 = feat.float().numpy().astype(np.float64)
+    words = np.zeros((n, 4), np.uint32)
+    for w in range(4):
+        words[:, w] = (mask[:, 32 * w:32 * (w + 1)].astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(1)
+    dev = dict(feat=feat.cuda(), mask=torch.as_tensor(words.view(np.int32)).cuda(),
+               norm=torch.as_tensor(norm.astype(np.float32)).cuda(),
+               label=torch.as_tensor((t * norm).astype(np.float32)).cuda())
+    return dev, xh64, mask, norm, t
+
+
+def _params(seed, **kw):
+    """Seeded parameters rounded to BF16-representable values, so that the GPU
+    (which rounds its FP32 master weights to BF16 for the tensor cores) and the
+    oracle use identical weights and take the same ReLU decisions."""
+    return _bf16(phantom.apod_init(seed, **kw)).float().numpy()
+
+
+def _data(dev):
+    return apod.Dataset(dev["feat"], dev["mask"], dev["norm"], dev["label"])
+
+
+def _max_rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-30))
+
+
+def test_features_match_the_oracle():
+    s = small_linear(48, 6, 600)
+    p = s.params()
+    ch = phantom.random_channels(s, 31)
+    plan = supra.Plan(**p)
+    feat, mask, norm = plan.apod_features(ch.cuda())
+    feat, mask, norm = feat.float().cpu().numpy(), mask.cpu().numpy().view(np.uint32), norm.cpu().numpy()
+    checked = 0
+    for l in range(s.n_lines):
+        for i in range(0, s.n_depth, 23):
+            x, m = oapod.features(p, ch.numpy()[s.line_tx[l]], l, i)
+            _, _, margin = oracle.aperture(p, l, i)
+            if np.min(np.abs(margin)) <= 1e-9:
+                continue
+            k = l * s.n_depth + i
+            bits = np.array([(mask[k, e >> 5] >> (e & 31)) & 1 for e in range(128)], bool)
+            np.testing.assert_array_equal(bits, m)
+            nrm = np.sqrt(np.sum(x * x))
+            assert norm[k] == pytest.approx(nrm, rel=1e-5, abs=1e-3)
+            if nrm > 0:
+                # BF16 rounding (2^-9 relative) plus the FP32 delay error: ~1e-5
+                # samples times slopes of up to 16000 per sample on white-noise
+                # records, ~1e-4 of ||x||
+                np.testing.assert_allclose(feat[k], x / nrm, rtol=2 ** -8, atol=2e-4)
+            checked += 1
+    assert checked > 100
+
+
+def test_forward_matches_the_oracle():
+    params = _params(40, out_scale=2.0, bias_scale=0.1)
+    dev, xh, mask, norm, _ = _rows(41, 1000, zero_rows=(5, 999))
+    y = apod.forward(torch.as_tensor(params).cuda(), dev["feat"], dev["mask"], dev["norm"]).cpu().numpy()
+    yh, _, _ = oapod.forward(params.astype(np.float64), xh, mask, bf16=True)
+    ref = yh * norm
+    assert y[5] == 0.0 and y[999] == 0.0
+    assert _max_rel(y, ref) <= TOL
+    yh64, _, _ = oapod.forward(params.astype(np.float64), xh, mask)
+    assert _max_rel(y, yh64 * norm) <= TOL_FP64
+
+
+@pytest.mark.parametrize("n", [1000, 148 * 128 * 2 + 77])
+def test_gradient_matches_the_oracle(n):
+    # n = 1000: one tile per CTA and a ragged last tile; the larger n makes every
+    # CTA accumulate several tiles in tensor memory
+    params = _params(50, out_scale=1.0, bias_scale=0.1)
+    dev, xh, mask, norm, t = _rows(51, n, zero_rows=(0, 7))
+    tr = apod.Trainer(params)
+    grad, loss = tr.compute_grad(_data(dev))
+    grad, loss = grad.cpu().numpy(), float(loss.item())
+    valid = norm > 0
+    ref_loss, ref = oapod.loss_and_grad(params.astype(np.float64), xh, mask, t, valid, bf16=True)
+    assert loss == pytest.approx(ref_loss, rel=TOL)
+    g, r = oapod.unpack(grad), oapod.unpack(ref)
+    errs = {name: _max_rel(g[name], r[name]) for name in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    assert max(errs.values()) <= TOL, errs
+    _, ref64 = oapod.loss_and_grad(params.astype(np.float64), xh, mask, t, valid)
+    assert np.linalg.norm(grad - ref64) <= TOL_FP64 * np.linalg.norm(ref64)
+    assert supra.device_status() == 0
+
+
+def test_strided_minibatch_equals_the_gathered_rows_and_is_deterministic():
+    params = phantom.apod_init(60, out_scale=1.0, bias_scale=0.1)
+    dev, *_ = _rows(61, 5000)
+    tr = apod.Trainer(params)
+    g1 = tr.compute_grad(_data(dev), base=3, stride=7)[0].clone()
+    g2 = tr.compute_grad(_data(dev), base=3, stride=7)[0].clone()
+    sub = {k: v[3::7].contiguous() for k, v in dev.items()}
+    g3 = tr.compute_grad(_data(sub))[0].clone()
+    assert torch.equal(g1, g2) and torch.equal(g1, g3)
+
+
+def test_adam_matches_the_oracle():
+    rng = np.random.default_rng(70)
+    p0 = rng.normal(0, 0.1, supra.APOD_PARAMS).astype(np.float32)
+    tr = apod.Trainer(p0, lr=3e-3)
+    p, m, v = p0.astype(np.float64), np.zeros(supra.APOD_PARAMS), np.zeros(supra.APOD_PARAMS)
+    for step in range(1, 4):
+        g = rng.normal(0, 1e-2, supra.APOD_PARAMS).astype(np.float32)
+        tr.grad.copy_(torch.as_tensor(g))
+        tr.apply()
+        p, m, v = oapod.adam(p, m, v, g.astype(np.float64), step, 3e-3)
+    np.testing.assert_allclose(tr.params.cpu().numpy(), p, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(tr.m.cpu().numpy(), m, rtol=1e-5, atol=1e-9)
+
+
+def test_fused_inference_matches_the_oracle():
+    s = small_linear(64, 8, 700)
+    p = s.params()
+    ch = phantom.random_channels(s, 80)
+    plan = supra.Plan(**p)
+    params = _params(81, out_scale=2.0, bias_scale=0.1)
+    got = plan.apod(ch.cuda(), torch.as_tensor(params).cuda()).cpu().numpy()
+    lines, depths = list(range(8)), list(range(0, 700, 11))
+    ref = oapod.beamform(p, ch.numpy(), params, lines, depths, bf16=True)
+    ref64 = oapod.beamform(p, ch.numpy(), params, lines, depths)
+    # no taper at the aperture edge: pixels with an element within 1e-9 m of the
+    # edge (FP32 and FP64 may disagree on membership, which changes the
+    # network's whole input) are left out
+    keep = np.array([[np.min(np.abs(oracle.aperture(p, l, i)[2])) > 1e-9 for i in depths] for l in lines])
+    assert keep.mean() > 0.9
+    g = got[np.ix_(lines, depths)]
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(g - ref)[keep]) <= TOL_INFER * scale
+    assert np.max(np.abs(g - ref64)[keep]) <= TOL_FP64 * scale
+    assert supra.device_status() == 0
+
+
+def test_zero_output_layer_is_rectangular_das_on_the_gpu():
+    s = small_linear(40, 6, 500)
+    p = s.params()
+    ch = phantom.random_channels(s, 90).cuda()
+    plan = supra.Plan(**p)
+    rect = supra.Plan(**dict(p, window="rect"))
+    got = plan.apod(ch, torch.as_tensor(phantom.apod_init(91)).cuda()).cpu().numpy()
+    das = rect.beamform(ch).cpu().numpy()
+    # uniform weights: the mean of the BF16-rounded samples (2^-9 relative each)
+    assert _max_rel(got, das) <= 4e-3
+
+
+def _training_data(s, seeds):
+    frames = [phantom.synth_channels(s, phantom.make_phantom(s, sd, 1500, n_points=3), sd, device="cuda")
+              for sd in seeds]
+    return frames
+
+
+def test_training_moves_the_output_toward_mv_and_resumes_from_a_checkpoint(tmp_path):
+    s = phantom.linear_setup(64, 0.3e-3, 32, 1024, fc=5e6, fs=40e6)
+    plan = supra.Plan(**s.params())
+    train = apod.make_dataset(plan, _training_data(s, range(100, 106)), lambda pl, ch: pl.mv(ch, 16))
+    evalf = _training_data(s, [200, 201])
+    params0 = phantom.apod_init(7)
+
+    def rel_err(params):
+        e = d = 0.0
+        for ch in evalf:
+            y, ref = plan.apod(ch, params).cpu().numpy(), plan.mv(ch, 16).cpu().numpy()
+            e += np.sum((y - ref) ** 2)
+            d += np.sum(ref ** 2)
+        return np.sqrt(e / d)
+
+    das_err = 0.0
+    for ch in evalf:
+        y, ref = plan.beamform(ch).cpu().numpy(), plan.mv(ch, 16).cpu().numpy()
+        das_err += np.sum((y - ref) ** 2) / np.sum(ref ** 2)
+    das_err = np.sqrt(das_err / len(evalf))
+
+    tr = apod.Trainer(params0, lr=2e-3)
+    err0 = rel_err(tr.params)
+    losses = [tr.epoch(train, 64, seed=e) for e in range(4)]
+    ck = str(tmp_path / "apod.npz")
+    tr.save(ck)
+    tr.epoch(train, 64, seed=4)
+    resumed = apod.Trainer(phantom.apod_init(999))
+    resumed.load(ck)
+    resumed.epoch(train, 64, seed=4)
+    assert torch.equal(resumed.params, tr.params) and resumed.step_count == tr.step_count
+    err = rel_err(tr.params)
+    assert losses[-1] < losses[0]
+    assert err < 0.9 * err0, (err, err0)
+    assert err < das_err, (err, das_err)
+
+
+def test_rejects_bad_arguments():
+    s = phantom.config3(lines=8)   # 1024 elements: more than the network's 128 inputs
+    plan = supra.Plan(**s.params())
+    ch = torch.zeros(plan.ch_shape, dtype=torch.int16, device="cuda")
+    with pytest.raises(supra.SupraError):
+        plan.apod(ch, torch.zeros(supra.APOD_PARAMS, device="cuda"))
+    dev, *_ = _rows(5, 64)
+    tr = apod.Trainer(phantom.apod_init(1))
+    lib = supra.load()
+    # a feature pointer that is not 16-byte aligned
+    rc = lib.supra_apod_forward(tr.params.data_ptr(), 8, 1, dev["feat"].data_ptr() + 2, dev["mask"].data_ptr(),
+                                dev["norm"].data_ptr(), tr.grad.data_ptr(), None)
+    assert rc == supra.EINVAL
+    rc = lib.supra_apod_grad(tr.params.data_ptr(), 64, 1, dev["feat"].data_ptr(), dev["mask"].data_ptr(),
+                             dev["norm"].data_ptr(), dev["label"].data_ptr(), tr.grad.data_ptr(), None,
+                             tr.ws.data_ptr(), 16, None)
+    assert rc == supra.EWORKSPACE

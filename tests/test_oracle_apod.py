@@ -117,3 +117,51 @@ def test_zero_output_layer_is_rectangular_das():
     y = apod.beamform(p, ch, params, lines, depths)
     ref = np.array([[oracle.das_points(p, [l], [i], [ch[s.line_tx[l]]])[0] for i in depths] for l in lines])
     np.testing.assert_allclose(y, ref, rtol=1e-9, atol=1e-9 * np.max(np.abs(ref)))
+
+
+def test_round_bf16_special_values():
+    one = 1.0
+    ulp = 2.0 ** -7                       # spacing of BF16 values in [1, 2)
+    vals = np.array([one, one + ulp, one + ulp / 2, one + 3 * ulp / 2, one + ulp / 2 + 2 ** -20, -2.5, 0.0,
+                     3.0e38, 1e-40])
+    want = np.array([one, one + ulp, one, one + 2 * ulp, one + ulp, -2.5, 0.0, 2.0 ** 128 * (1 - 2 ** -9), 0.0])
+    got = apod.round_bf16(vals)
+    np.testing.assert_array_equal(got[:6], want[:6])
+    assert got[6] == 0.0
+    # the largest finite float32 region rounds to a BF16 value within 2^-8 relative
+    assert abs(got[7] - 3.0e38) <= 2 ** -8 * 3.0e38
+    # BF16 keeps float32's exponent range: a subnormal stays within one subnormal step
+    assert abs(got[8] - 1e-40) <= 2.0 ** -133
+
+
+def test_bf16_mode_rounds_operands_only():
+    # every rounded operand is BF16-representable, and the BF16 network stays
+    # within a few BF16 ulps of the FP64 one
+    params = phantom.apod_init(13, out_scale=1.0, bias_scale=0.1)
+    Xh, mask, t = _inputs(14, 64)
+    yh64, _, c64 = apod.forward(params, Xh, mask)
+    yh16, _, c16 = apod.forward(params, Xh, mask, bf16=True)
+    for h in (c16[2], c16[4]):
+        np.testing.assert_array_equal(h, apod.round_bf16(h))
+    assert np.max(np.abs(yh16 - yh64)) <= 5e-2 * np.max(np.abs(yh64))
+    l64, g64 = apod.loss_and_grad(params, Xh, mask, t)
+    l16, g16 = apod.loss_and_grad(params, Xh, mask, t, bf16=True)
+    assert l16 == pytest.approx(l64, rel=5e-2)
+    assert np.linalg.norm(g16 - g64) <= 0.1 * np.linalg.norm(g64)
+    # with BF16-representable inputs and weights and bf16=False on both, the
+    # modes agree on the first layer exactly (no rounding there)
+    pr = apod.round_bf16(params)
+    Xr = apod.round_bf16(Xh)
+    _, _, ca = apod.forward(pr, Xr, mask)
+    _, _, cb = apod.forward(pr, Xr, mask, bf16=True)
+    np.testing.assert_array_equal(ca[1], cb[1])
+
+
+def test_unnormalised_input_with_scale_equals_normalised_input():
+    params = phantom.apod_init(15, out_scale=1.0, bias_scale=0.1)
+    X, mask, norm, _ = phantom.apod_random_batch(16, 30)
+    Xh = X.astype(np.float64) / norm[:, None]
+    yh, w, _ = apod.forward(params, Xh, mask)
+    y, w2, _ = apod.forward(params, X.astype(np.float64), mask, x_scale=1.0 / norm)
+    np.testing.assert_allclose(w2, w, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(y, yh * norm, rtol=1e-10)
