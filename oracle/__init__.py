@@ -331,7 +331,12 @@ def mv_weights(x: np.ndarray, L: int, loading: float | None = None):
     X = np.stack([x[l:l + L] for l in range(K)])
     R = X.T @ X / K
     delta = 0.01 if loading is None else float(loading)
-    R = R + delta * (np.trace(R) / L) * np.eye(L)
+    tr = np.trace(R)
+    if tr == 0.0:
+        # all samples zero: R = 0 and the loading vanishes; the weights are the
+        # infinite-loading limit (uniform) and the output is 0
+        return np.full(L, 1.0 / L), X.mean(axis=0)
+    R = R + delta * (tr / L) * np.eye(L)
     z = np.linalg.solve(R, np.ones(L))
     return z / z.sum(), X.mean(axis=0)
 

@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(mv_warps<T>() * 32) mv_kernel(const DevPlan *_
     T tr = lane < L ? R[lane][lane] : (T)0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (tr == (T)0) {   // all samples zero (e.g. delays past the record): R = 0, output 0
+        if (lane == 0) *out = 0.0f;
+        return;
+    }
     const T delta = (T)loading * tr / (T)L;
     T rr[kMvMaxL];
 #pragma unroll

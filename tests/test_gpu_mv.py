@@ -95,3 +95,12 @@ def test_mv_rejects_bad_arguments():
     for L, lo in [(0, 0.01), (33, 0.01), (8, 0.0), (8, float("nan"))]:
         with pytest.raises(supra.SupraError):
             plan.mv(ch, L, lo)
+
+
+def test_mv_all_zero_records_give_zero_without_a_device_error():
+    s = small_linear(24, 6, 300)
+    plan = supra.Plan(**s.params())
+    supra.device_status()
+    rf = plan.mv(torch.zeros(plan.ch_shape, dtype=torch.int16, device="cuda"), 8)
+    assert torch.count_nonzero(rf).item() == 0
+    assert supra.device_status() == 0

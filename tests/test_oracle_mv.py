@@ -74,3 +74,10 @@ def test_point_fallback_and_full_frame_agree():
     x, _ = oracle.delayed_samples(p, ch[1], 1, 0)
     if len(x) < 2:
         assert full[0, 0] == pytest.approx(oracle.das_points(p, [1], [0], [ch[1]])[0])
+
+
+def test_all_zero_aperture_gives_uniform_weights_and_zero_output():
+    # trace(R) = 0: no loading, singular R; the infinite-loading limit applies
+    w, xbar = oracle.mv_weights(np.zeros(20), 8)
+    np.testing.assert_array_equal(w, np.full(8, 1.0 / 8))
+    assert float(w @ xbar) == 0.0
