@@ -281,6 +281,98 @@ SUPRA_API int supra_apod_adam(float *params, float *m, float *v, const float *gr
  * Errors: SUPRA_EINVAL (n_el > 128). */
 SUPRA_API int supra_apod_mlp(const supra_plan *plan, const float *params, const int16_t *ch, float *rf, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Tuning.  Frames of one plan that are adjacent in a batch share a DAS tile
+ * (frames x 256 depths x 1 line) of up to max_group frames: larger tiles
+ * share the delay and weight arithmetic across frames, smaller ones expose
+ * more tiles to the 148 SMs.  Set before the plan is shared across threads.
+ * ------------------------------------------------------------------------ */
+SUPRA_API int supra_plan_set_max_group(supra_plan *plan, int32_t max_group);   /* 1, 2, 4, 8 or 16 */
+SUPRA_API int32_t supra_plan_get_max_group(const supra_plan *plan);
+
+/* Autotuner: times supra_bmode_batched of n frames of `plan` (device
+ * pointers as for supra_bmode_batched; outputs are overwritten) for each
+ * frames-per-tile class with CUDA events on `stream` (reps timed calls after
+ * one warm-up each), keeps the fastest in the plan and returns it with its
+ * time per call.  Synchronizes the stream. */
+SUPRA_API int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out,
+                                   void *workspace, size_t workspace_bytes, int32_t reps, void *stream,
+                                   int32_t *best_group, float *best_ms);
+
+/* ------------------------------------------------------------------------
+ * Real-time request loop.  The paper's runtime streams frames through its
+ * processing graph (Sec. 2); this server runs many acquisitions at once on one
+ * GPU: a device arena of memory_bytes is allocated at creation and every
+ * request's footprint (ingested channels, output, scratch) is reserved from
+ * it in arrival order; admitted requests of one kind form the next batch
+ * (B-mode frames of any plans in one uneven supra_bmode_batched call); batches
+ * run round-robin on n_streams streams, each captured into a CUDA graph
+ * cached per (stream, kind, plan sequence) when use_graphs is set.  Results
+ * are B-mode images (the plan's grid, else its log-compressed lines) by the
+ * request's beamformer: fused delay-and-sum, minimum variance, or learned
+ * apodization, each followed by envelope, log compression and scan
+ * conversion.  Times are seconds on the server's clock.
+ * ------------------------------------------------------------------------ */
+typedef struct supra_server supra_server;
+
+enum { SUPRA_KIND_DAS = 0, SUPRA_KIND_MV = 1, SUPRA_KIND_APOD = 2 };
+
+typedef struct {
+    size_t memory_bytes;  /* device arena for ingested channels, outputs and scratch */
+    int32_t n_streams;    /* 1..64 */
+    int32_t max_batch;    /* requests per batch (B-mode: frames per supra_bmode_batched call) */
+    int32_t use_graphs;   /* capture batches into CUDA graphs */
+} supra_server_config;
+
+typedef struct {
+    int32_t kind;                 /* SUPRA_KIND_* */
+    const supra_plan *plan;       /* resident plan, alive until the request completes */
+    const int16_t *ch;            /* device channels read in place, or NULL */
+    const int16_t *ch_host;       /* host channels (pinned for overlap) copied into the arena, or NULL */
+    uint8_t *out_host;            /* host destination of the result, or NULL: result stays in the arena */
+    const float *apod_params;     /* SUPRA_KIND_APOD: device float [SUPRA_APOD_PARAMS] */
+    int32_t mv_subaperture;       /* SUPRA_KIND_MV: 1..32 */
+    float mv_loading;             /* SUPRA_KIND_MV: > 0 */
+    int64_t tag;                  /* returned in the completion */
+} supra_request;
+
+typedef struct {
+    int64_t ticket, tag;
+    int32_t status;               /* SUPRA_OK or an error code */
+    int32_t batch_size;           /* requests in the batch it ran in */
+    const uint8_t *out;           /* device result when out_host was NULL (valid until supra_server_release) */
+    int64_t out_bytes;
+    double t_submit, t_admit, t_done;   /* arrival, memory admission, completion on the device */
+} supra_completion;
+
+typedef struct {
+    int64_t submitted, completed, batches, graph_launches, graph_instantiations, graph_updates;
+    int64_t memory_used, memory_peak;
+    int32_t pending, inflight;
+} supra_server_stats;
+
+/* Errors: SUPRA_EINVAL, SUPRA_ENOMEM (arena), SUPRA_ECUDA. */
+SUPRA_API int supra_server_create(const supra_server_config *cfg, supra_server **out);
+/* Queues one request (thread-safe).  SUPRA_EINVAL: bad request, or one that
+ * cannot fit the arena even alone. */
+SUPRA_API int supra_server_submit(supra_server *s, const supra_request *req, int64_t *ticket);
+/* Open-loop arrivals: request i is submitted at t_arrival[i] seconds
+ * (non-decreasing) after this call by a feeder thread; latencies count from
+ * the scheduled arrival.  tickets[i] (may be NULL) receives its ticket. */
+SUPRA_API int supra_server_submit_trace(supra_server *s, int32_t n, const supra_request *reqs,
+                                        const double *t_arrival, int64_t *tickets);
+/* Up to max completed requests, oldest first (non-blocking). */
+SUPRA_API int supra_server_poll(supra_server *s, supra_completion *out, int32_t max, int32_t *n);
+/* Blocks until n_submitted requests have been submitted and none is pending or
+ * running; SUPRA_ETIMEOUT after timeout_s seconds. */
+SUPRA_API int supra_server_wait(supra_server *s, int64_t n_submitted, double timeout_s);
+/* Frees the arena memory of a result kept on the device. */
+SUPRA_API int supra_server_release(supra_server *s, int64_t ticket);
+SUPRA_API int supra_server_get_stats(supra_server *s, supra_server_stats *stats);
+SUPRA_API double supra_server_now(const supra_server *s);
+/* Finishes all submitted work, then frees everything. */
+SUPRA_API void supra_server_destroy(supra_server *s);
+
 /* supra_bmode for callers that may not allocate device memory.  The paper has
  * no counterpart: it exists because some callers cannot provide the device
  * workspace supra_bmode needs -- e.g. a real-time acquisition loop that must

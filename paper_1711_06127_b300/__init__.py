@@ -27,6 +27,9 @@ EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "su
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
            "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_apod_features", "supra_apod_forward",
            "supra_apod_workspace_size", "supra_apod_grad", "supra_apod_adam", "supra_apod_mlp",
+           "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode", "supra_server_create",
+           "supra_server_submit", "supra_server_submit_trace", "supra_server_poll", "supra_server_wait",
+           "supra_server_release", "supra_server_get_stats", "supra_server_now", "supra_server_destroy",
            "supra_device_status", "supra_strerror", "supra_version")
 APOD_PARAMS, APOD_INPUTS = 20736, 128
 
@@ -110,6 +113,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_apod_grad.argtypes = [P, I64, I64, P, P, P, P, P, P, P, ctypes.c_size_t, P]
     lib.supra_apod_adam.argtypes = [P, P, P, P, ctypes.c_int32, F, F, F, F, P]
     lib.supra_apod_mlp.argtypes = [P, P, P, P, P]
+    lib.supra_plan_set_max_group.argtypes = [P, ctypes.c_int32]
+    lib.supra_plan_get_max_group.argtypes = [P]
+    lib.supra_autotune_bmode.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.c_size_t,
+                                         ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_float)]
     lib.supra_device_status.argtypes = [ctypes.c_int32]
     lib.supra_strerror.argtypes = [ctypes.c_int]
     lib.supra_strerror.restype = ctypes.c_char_p
@@ -316,6 +324,34 @@ class Plan:
                                           _dev_tensor(norm, torch.float32, (P,), "norm"), _stream_ptr(stream)),
                "supra_apod_features")
         return feat, mask, norm
+
+    # ---- tuning ------------------------------------------------------------
+    @property
+    def max_group(self) -> int:
+        return int(load().supra_plan_get_max_group(self.handle))
+
+    @max_group.setter
+    def max_group(self, g: int):
+        _check(load().supra_plan_set_max_group(self.handle, int(g)), "supra_plan_set_max_group")
+
+    def autotune(self, chs, outs=None, workspace=None, reps=3, stream=None):
+        """Times the fused chain on these frames (device tensors of this plan)
+        for each frames-per-tile class, keeps the fastest; returns (G, ms)."""
+        import torch
+
+        n = len(chs)
+        outs = [torch.empty(self.out_shape, dtype=torch.uint8, device=c.device) for c in chs] if outs is None else outs
+        need = workspace_size([self] * n)
+        if need and workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=chs[0].device)
+        PA = ctypes.c_void_p * n
+        ca = PA(*[_dev_tensor(c, torch.int16, self.ch_shape, "ch") for c in chs])
+        oa = PA(*[_dev_tensor(o, torch.uint8, self.out_shape, "out") for o in outs])
+        g, ms = ctypes.c_int32(), ctypes.c_float()
+        _check(load().supra_autotune_bmode(self.handle, n, ca, oa, workspace.data_ptr() if workspace is not None else None,
+                                           need, int(reps), _stream_ptr(stream), ctypes.byref(g), ctypes.byref(ms)),
+               "supra_autotune_bmode")
+        return int(g.value), float(ms.value)
 
     # ---- fused chain -----------------------------------------------------
     def bmode(self, ch, out=None, workspace=None, stream=None):

@@ -3,6 +3,7 @@
 // validation, launches of the beamforming / post-processing kernels, and the
 // C ABI declared in include/supra.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,7 @@ struct supra_plan {
     supra_plan_info info{};
     int device = 0;
     int max_active = 0;     // upper bound on the elements inside one pixel's aperture
+    std::atomic<int> max_group{kMaxGroup};   // frames per DAS tile (autotuned)
 };
 
 namespace {
@@ -696,7 +698,8 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
     std::vector<Grp> groups;
     for (int k = 0; k < n;) {
         Grp g{plans[k], k, 0};
-        while (k < n && plans[k] == g.p && g.n < kMaxGroup) {
+        const int gmax = std::min(kMaxGroup, std::max(1, g.p->max_group.load(std::memory_order_relaxed)));
+        while (k < n && plans[k] == g.p && g.n < gmax) {
             ++g.n;
             ++k;
         }
@@ -790,6 +793,60 @@ int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const i
         mv_kernel<double><<<grid, w * 32, 0, st>>>(plan->dev, ch, rf, subaperture, loading);
     }
     return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- tuning
+
+int supra_plan_set_max_group(supra_plan *plan, int32_t g) {
+    if (!plan || (g != 1 && g != 2 && g != 4 && g != 8 && g != 16)) return SUPRA_EINVAL;
+    plan->max_group.store(g, std::memory_order_relaxed);
+    return SUPRA_OK;
+}
+
+int32_t supra_plan_get_max_group(const supra_plan *plan) {
+    return plan ? plan->max_group.load(std::memory_order_relaxed) : SUPRA_EINVAL;
+}
+
+int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out, void *workspace,
+                         size_t workspace_bytes, int32_t reps, void *stream, int32_t *best_group, float *best_ms) {
+    if (!plan || n < 1 || !ch || !out || reps < 1) return SUPRA_EINVAL;
+    std::vector<const supra_plan *> plans(n, plan);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SUPRA_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SUPRA_ECUDA;
+    }
+    const int before = plan->max_group.load();
+    int best = before, rc = SUPRA_OK;
+    float best_t = INFINITY;
+    for (int g : {16, 8, 4, 2, 1}) {
+        if (g > 1 && g / 2 >= n) continue;   // same launches as a smaller class
+        plan->max_group.store(g);
+        rc = supra_bmode_batched(n, plans.data(), ch, out, workspace, workspace_bytes, stream);   // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc; ++r)
+            rc = supra_bmode_batched(n, plans.data(), ch, out, workspace, workspace_bytes, stream);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = SUPRA_ECUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (ms < best_t) best_t = ms, best = g;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->max_group.store(rc ? before : best);
+    if (rc) return rc;
+    if (best_group) *best_group = best;
+    if (best_ms) *best_ms = best_t;
+    return SUPRA_OK;
 }
 
 // ---------------------------------------------------------------- learned apodization
