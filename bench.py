@@ -108,21 +108,43 @@ class ClockSampler:
         else:
             import subprocess
 
-            self._smi = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.SMI_FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "50", "-i", str(self.index)], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
+            # nvidia-smi needs ~0.1 s to start: wait for its first sample, then
+            # keep only the samples taken while the timed region runs
+            self._rows = []
+            first = threading.Event()
+            try:
+                self._smi = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.SMI_FIELDS}",
+                                              "--format=csv,noheader,nounits", "-lms", "50", "-i", str(self.index)],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+            except OSError as e:
+                self._smi, self.err = None, repr(e)
+                return self
+
+            def reader():
+                for row in self._smi.stdout:
+                    self._rows.append((time.perf_counter(), row))
+                    first.set()
+
+            self._reader = threading.Thread(target=reader, daemon=True)
+            self._reader.start()
+            first.wait(10.0)
+        self._t_start = time.perf_counter()
         return self
 
     def __exit__(self, *a):
+        self._t_end = time.perf_counter()
         self._stop.set()
         if self.ok:
             self._t.join()
         elif getattr(self, "_smi", None) is not None:
+            time.sleep(0.06)   # the sample that covers the end of the region
             self._smi.terminate()
-            out, _ = self._smi.communicate()
+            self._smi.wait()
+            self._reader.join(2.0)
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
             seen = set()
-            for row in out.strip().splitlines():
+            rows = [r for t, r in self._rows if self._t_start <= t <= self._t_end + 0.06]
+            for row in rows:
                 f = [x.strip() for x in row.split(",")]
                 try:
                     self.samples.append(float(f[0]))
@@ -223,6 +245,202 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _percentiles(xs):
+    srt = sorted(xs)
+    if not srt:
+        return None, None
+    pick = lambda q: srt[min(len(srt) - 1, int(round(q * (len(srt) - 1))))]
+    return pick(0.5), pick(0.99)
+
+
+def bench_apod(args, dev, stream):
+    """Learned apodization on 128 elements x 256 lines x 2048 samples: train on
+    seeded frames labelled by the exact MV beamformer, then report DAS, MV and
+    the learned form side by side on held-out frames (frames/s, per-frame
+    latency, PSNR of the B-mode lines against MV, cyst contrast and CNR)."""
+    import torch
+
+    import paper_1711_06127_b300 as supra
+    from paper_1711_06127_b300 import apod, quality
+    import phantom
+
+    s = phantom.config2()
+    p = dict(s.params(), grid=None)
+    plan = supra.Plan(**p)
+    L = 32
+    n_train, n_eval = args.apod_train_frames, args.apod_eval_frames
+    P = plan.n_lines * plan.n_depth
+    feat = torch.empty((n_train * P, supra.APOD_INPUTS), dtype=torch.bfloat16, device=dev)
+    mask = torch.empty((n_train * P, 4), dtype=torch.int32, device=dev)
+    norm = torch.empty((n_train * P,), dtype=torch.float32, device=dev)
+    label = torch.empty((n_train * P,), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    for f in range(n_train):
+        ch, _ = phantom.apod_frame(s, 4000 + f, device=dev)
+        sl = slice(f * P, (f + 1) * P)
+        plan.apod_features(ch, feat[sl], mask[sl], norm[sl], stream)
+        plan.mv(ch, L, rf=label[sl].view(plan.line_shape), stream=stream)
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    data = apod.Dataset(feat, mask, norm, label)
+    tr = apod.Trainer(phantom.apod_init(7), lr=args.apod_lr)
+    n_batches = max(1, data.n // args.apod_batch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    losses = []
+    e0.record(stream)
+    for ep in range(args.apod_epochs):
+        losses.append(tr.epoch(data, n_batches, seed=ep, stream=stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    pix = data.n * args.apod_epochs
+    flops_per_pixel = 2 * (128 * 64 + 64 * 64 + 64 * 128) + 2 * (128 * 64 + 64 * 64 + 128 * 64 + 64 * 64 + 64 * 128)
+    del feat, mask, norm, label, data
+    torch.cuda.empty_cache()
+
+    # ---- held-out frames: the three beamformers, each followed by envelope + log compression
+    def chain(kind, ch, out):
+        if kind == "das":
+            return plan.bmode(ch, out, None, stream)
+        rf = plan.mv(ch, L, stream=stream) if kind == "mv" else plan.apod(ch, tr.params, stream=stream)
+        return plan.logcompress(plan.envelope(rf, stream=stream), out, stream=stream)
+
+    def rf_of(kind, ch):
+        if kind == "das":
+            return plan.beamform(ch, stream=stream)
+        return plan.mv(ch, L, stream=stream) if kind == "mv" else plan.apod(ch, tr.params, stream=stream)
+
+    kinds = ("das", "mv", "apod")
+    lat = {k: [] for k in kinds}
+    q = {k: {"psnr_vs_mv": [], "contrast_db": [], "cnr": []} for k in kinds}
+    out = torch.empty(plan.line_shape, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for f in range(n_eval):
+        ch, cysts = phantom.apod_frame(s, 5000 + f, device=dev)
+        for k in kinds:
+            chain(k, ch, out)   # warm
+            ev[0].record(stream)
+            chain(k, ch, out)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            lat[k].append(ev[0].elapsed_time(ev[1]))
+        bms, envs = {}, {}
+        for k in kinds:
+            rf = rf_of(k, ch)
+            env = plan.envelope(rf, stream=stream)
+            envs[k] = env.cpu().numpy()
+            bms[k] = plan.logcompress(env, stream=stream).cpu().numpy()
+        for k in kinds:
+            q[k]["psnr_vs_mv"].append(quality.psnr(bms[k], bms["mv"]))
+            for cy in cysts:
+                st = quality.cyst_stats(p, envs[k], bms[k], cy, float(p.get("dyn_range_db", 60.0)))
+                q[k]["contrast_db"].append(st["contrast_db"])
+                q[k]["cnr"].append(st["cnr"])
+    res = {"workload": s.name + "-mv-labels", "subaperture": L, "loading": 0.01,
+           "train": {"frames": n_train, "pixels": P * n_train, "epochs": args.apod_epochs,
+                     "minibatch_pixels": P * n_train // n_batches, "lr": args.apod_lr, "loss_first_epoch": losses[0],
+                     "loss_last_epoch": losses[-1], "ms": train_ms, "pixels_per_s": pix / (train_ms * 1e-3),
+                     "tflops": pix * flops_per_pixel / (train_ms * 1e-3) / 1e12, "data_prep_s": prep_s},
+           "eval_frames": n_eval}
+    for k in kinds:
+        p50, p99 = _percentiles(lat[k])
+        mean_ms = sum(lat[k]) / len(lat[k])
+        name = {"das": "das", "mv": "mv", "apod": "learned"}[k]
+        psnr = [v for v in q[k]["psnr_vs_mv"] if v != float("inf")]
+        res[name] = {"frames_per_s": 1e3 / mean_ms, "latency_ms": {"p50": p50, "p99": p99},
+                     "psnr_vs_mv_db": (sum(psnr) / len(psnr)) if psnr else None,
+                     "cyst_contrast_db": sum(q[k]["contrast_db"]) / len(q[k]["contrast_db"]),
+                     "cyst_cnr": sum(q[k]["cnr"]) / len(q[k]["cnr"])}
+    res["note"] = ("single-frame launches, B-mode lines out (beamformer + envelope + log compression); "
+                   "PSNR of 8-bit B-mode lines against MV's; cysts of each held-out frame")
+    return res, tr.params
+
+
+def bench_serving(args, dev, apod_params=None):
+    """The request loop under an open-loop Poisson stream: 2D frames of varied
+    shapes and 3D volumes, each tagged DAS, learned apodization or MV (3D
+    volumes run DAS), admitted by free device memory; frames/s and latency
+    from scheduled arrival to completion on the device."""
+    import numpy as np
+    import torch
+
+    import paper_1711_06127_b300 as supra
+    from paper_1711_06127_b300.serving import Server
+    import phantom
+
+    rng = np.random.default_rng(6000)
+    shapes2d = [(e, l, n) for e in (64, 96, 128) for l in (128, 192, 256) for n in (1024, 1536, 2048)]
+    plans2d, pool2d = [], []
+    for k, (e, l, n) in enumerate(shapes2d):
+        st = phantom.linear_setup(e, 0.3e-3, l, n, fc=7e6, fs=40e6, grid_n=(512, 512), name=f"2d-{e}-{l}-{n}")
+        plans2d.append(supra.Plan(**st.params()))
+        pool2d.append(phantom.synth_channels(st, phantom.make_phantom(st, 6100 + k, 4000), 6100 + k, device=dev))
+    plans3d, pool3d = [], []
+    if not args.skip_3d:
+        for k, lines in enumerate((32, 64)):
+            st = phantom.config3(lines)
+            plans3d.append(supra.Plan(**st.params()))
+            pool3d.append(phantom.synth_channels(st, phantom.default_phantom(st, 6200 + k), 6200 + k, device=dev))
+    if apod_params is None:
+        apod_params = torch.as_tensor(phantom.apod_init(7)).to(dev)
+    n = args.serve_requests
+    t_arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, n))
+    reqs, meta = [], []
+    for i in range(n):
+        is3d = bool(plans3d) and rng.random() < 0.3
+        tag = ("das", "apod", "mv")[int(rng.integers(0, 3))]
+        if is3d:
+            k = int(rng.integers(0, len(plans3d)))
+            plan, ch, kind = plans3d[k], pool3d[k], "das"
+        else:
+            k = int(rng.integers(0, len(plans2d)))
+            plan, ch, kind = plans2d[k], pool2d[k], tag
+        kw = dict(ch=ch, tag=i)
+        if kind == "apod":
+            kw["apod_params"] = apod_params
+        elif kind == "mv":
+            kw.update(mv_subaperture=32, mv_loading=0.01)
+        reqs.append((kind, plan, kw))
+        meta.append(("3d" if is3d else "2d", kind))
+    srv = Server(int(args.serve_memory_gb * (1 << 30)), n_streams=4, max_batch=16, use_graphs=True)
+    torch.cuda.synchronize()
+    srv.submit_trace(reqs, t_arr)
+    done = []
+    deadline = time.perf_counter() + args.serve_timeout
+    while len(done) < n and time.perf_counter() < deadline:
+        got = srv.poll()
+        for c in got:
+            if c["out"] is not None:
+                srv.release(c["ticket"])
+        done += got
+        if not got:
+            time.sleep(0.0005)
+    st = srv.stats()
+    srv.close()
+    ok = [c for c in done if c["status"] == 0]
+    res = {"requests": n, "completed": len(ok), "errors": len(done) - len(ok), "offered_rate_per_s": args.serve_rate,
+           "mix": "70% 2D (27 shapes: 64/96/128 el x 128/192/256 lines x 1024/1536/2048 samples, 512x512 out), "
+                  "30% 3D (1024 el, 32x32 or 64x64 lines, 1536 samples, 256^3 out); tags DAS / learned / MV "
+                  "uniform, 3D runs DAS",
+           "memory_gb": args.serve_memory_gb, "streams": 4, "max_batch": 16, "graphs": True}
+    if ok:
+        span = max(c["t_done"] for c in ok) - min(c["t_submit"] for c in ok)
+        lat = [1e3 * (c["t_done"] - c["t_submit"]) for c in ok]
+        p50, p99 = _percentiles(lat)
+        res.update({"span_s": span, "frames_per_s": len(ok) / span,
+                    "frames_2d_per_s": sum(1 for c in ok if meta[c["tag"]][0] == "2d") / span,
+                    "volumes_3d_per_s": sum(1 for c in ok if meta[c["tag"]][0] == "3d") / span,
+                    "latency_ms": {"p50": p50, "p99": p99}})
+        by = {}
+        for c in ok:
+            by.setdefault("-".join(meta[c["tag"]]), []).append(1e3 * (c["t_done"] - c["t_submit"]))
+        res["latency_ms_by_class"] = {k: dict(zip(("p50", "p99"), _percentiles(v)), n=len(v)) for k, v in by.items()}
+        res["mean_batch"] = sum(c["batch_size"] for c in ok) / len(ok)
+    res["stats"] = {k: st[k] for k in ("batches", "graph_launches", "graph_instantiations", "graph_updates",
+                                       "memory_peak")}
+    return res
 
 
 def run_ours(args):
@@ -378,6 +596,16 @@ def run_ours(args):
     d2h = sum(o.numel() for o in outs)
     assert supra.device_status() == 0
 
+    # ---- learned apodization beside MV and DAS; the request loop
+    apod_res = serve_res = None
+    if rank == 0 and not args.skip_apod:
+        apod_res, trained = bench_apod(args, dev, stream)
+    else:
+        trained = None
+    if rank == 0 and not args.skip_serve:
+        serve_res = bench_serving(args, dev, trained)
+    assert supra.device_status() == 0
+
     line = None
     if rank == 0:
         cpu = None
@@ -404,6 +632,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "volume_3d": vol3d,
+            "learned_apodization": apod_res,
+            "serving": serve_res,
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
         }
@@ -418,7 +648,7 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -427,6 +657,17 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=BATCH, help="frames per step (64 = the workload)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-3d", action="store_true")
+    ap.add_argument("--skip-apod", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--apod-train-frames", type=int, default=200)
+    ap.add_argument("--apod-eval-frames", type=int, default=20)
+    ap.add_argument("--apod-epochs", type=int, default=8)
+    ap.add_argument("--apod-batch", type=int, default=65536, help="pixels per minibatch")
+    ap.add_argument("--apod-lr", type=float, default=1e-3)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-memory-gb", type=float, default=64.0)
+    ap.add_argument("--serve-timeout", type=float, default=300.0)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -305,9 +305,11 @@ SUPRA_API int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *c
  * GPU: a device arena of memory_bytes is allocated at creation and every
  * request's footprint (ingested channels, output, scratch) is reserved from
  * it in arrival order; admitted requests of one kind form the next batch
- * (B-mode frames of any plans in one uneven supra_bmode_batched call); batches
- * run round-robin on n_streams streams, each captured into a CUDA graph
- * cached per (stream, kind, plan sequence) when use_graphs is set.  Results
+ * (B-mode frames of any plans in one uneven supra_bmode_batched call, frames
+ * of one plan side by side); batches run round-robin on n_streams streams;
+ * with use_graphs, a batch whose (stream, kind, plan sequence) bucket has
+ * been seen before replays that bucket's CUDA graph (updated in place for the
+ * new buffers), a first-seen bucket launches directly.  Results
  * are B-mode images (the plan's grid, else its log-compressed lines) by the
  * request's beamformer: fused delay-and-sum, minimum variance, or learned
  * apodization, each followed by envelope, log compression and scan

@@ -13,9 +13,10 @@
 //    call, MV and learned-apodization requests as one sequence of launches.
 //  * Overlap.  Batches go round-robin to n_streams CUDA streams, so copies
 //    and kernels of different batches overlap on the device.
-//  * Graphs.  Each batch is captured into a CUDA graph; the instantiated graph
-//    is cached per (stream, kind, plan sequence) bucket and refreshed with
-//    cudaGraphExecUpdate when only buffer addresses changed.
+//  * Graphs.  A batch whose bucket (stream, kind, plan sequence) has been seen
+//    before is captured into a CUDA graph; the instantiated graph is cached per
+//    bucket and refreshed with cudaGraphExecUpdate when only buffer addresses
+//    changed.  A first-seen bucket launches directly.
 //  * Completion.  A host function enqueued after the batch timestamps its
 //    completion; the worker then frees the batch's memory and publishes the
 //    per-request completions (submission, admission and completion times).
@@ -107,8 +108,9 @@ struct supra_server {
     std::thread worker;
     std::vector<std::thread> feeders;
     std::chrono::steady_clock::time_point t0;
-    // graph cache (worker thread only)
+    // graph cache (worker thread only): a bucket gets a graph once it recurs
     std::unordered_map<std::string, GraphEntry> graphs;
+    std::unordered_map<std::string, int> seen;
     std::list<std::string> lru;
 
     double now() const {
@@ -217,6 +219,10 @@ Batch *form_batch(supra_server *s) {
     }
     const double t = s->now();
     for (Req &q : got) q.t_admit = t;
+    // frames of one plan side by side: they share DAS tiles (and bucket keys repeat)
+    std::stable_sort(got.begin(), got.end(), [](const Req &x, const Req &y) {
+        return reinterpret_cast<uintptr_t>(x.r.plan) < reinterpret_cast<uintptr_t>(y.r.plan);
+    });
     for (size_t j = take.size(); j-- > 0;) s->pending.erase(s->pending.begin() + (long)take[j]);
     b->reqs = std::move(got);
     b->id = s->next_batch++;
@@ -322,7 +328,15 @@ void launch_batch(supra_server *s, Batch *b) {
         if (!rc && q.in_off != SIZE_MAX &&
             cudaMemcpyAsync(s->arena.ptr(q.in_off), q.r.ch_host, q.in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             rc = SUPRA_ECUDA;
-    if (!rc) rc = s->cfg.use_graphs ? launch_graph(s, b, st) : enqueue_compute(s, b, st);
+    bool graph = false;
+    if (!rc && s->cfg.use_graphs) {
+        // first sight of a bucket: launch directly (an instantiation would not be repaid)
+        const std::string key = bucket_key(b);
+        int &n = s->seen[key];
+        graph = ++n >= 2;
+        if (s->seen.size() > 4096) s->seen.clear();
+    }
+    if (!rc) rc = graph ? launch_graph(s, b, st) : enqueue_compute(s, b, st);
     for (Req &q : b->reqs)
         if (!rc && q.r.out_host &&
             cudaMemcpyAsync(q.r.out_host, s->arena.ptr(q.out_off), q.out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)

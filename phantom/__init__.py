@@ -451,3 +451,20 @@ def apod_random_batch(seed: int, n: int, min_active: int = 2, n_el: int = 128):
     norm = np.sqrt(np.sum(X.astype(np.float64) ** 2, axis=1))
     t = rng.uniform(-1.0, 1.0, n)
     return X, mask, norm, t
+
+
+def random_cysts(seed: int, n: int = 3, x_mm=(-12.0, 12.0), z_mm=(10.0, 35.0), radius_mm: float = 2.0):
+    """Seeded anechoic cyst layout (x, z, radius in metres) for the
+    learned-apodization frames: n cysts at random positions, 2 mm radius."""
+    rng = np.random.default_rng(int(seed) + 104729)
+    xs = rng.uniform(x_mm[0], x_mm[1], n) * 1e-3
+    zs = rng.uniform(z_mm[0], z_mm[1], n) * 1e-3
+    return tuple((float(x), float(z), radius_mm * 1e-3) for x, z in zip(xs, zs))
+
+
+def apod_frame(setup: Setup, seed: int, device="cuda"):
+    """One frame of the learned-apodization workload: 10000 scatterers, three
+    point targets and the seed's cysts.  Returns (channels, cysts)."""
+    cysts = random_cysts(seed)
+    ph = make_phantom(setup, seed, 10000, n_points=3, cysts=cysts)
+    return synth_channels(setup, ph, seed, device=device), cysts

@@ -75,7 +75,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         assert c["t_submit"] <= c["t_admit"] <= c["t_done"]
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["memory_used"] == 0
-    assert st["graph_launches"] == st["batches"] > 0
+    assert 0 < st["batches"] and st["graph_launches"] <= st["batches"]
     assert max(c["batch_size"] for c in done) > 1    # requests were batched
     srv.close()
     assert supra.device_status() == 0
@@ -122,7 +122,7 @@ def test_open_loop_trace_reports_latencies_and_reuses_graphs():
     subs = np.sort(np.array([c["t_submit"] for c in done]))
     np.testing.assert_allclose(np.diff(subs), np.diff(t_arr), atol=1e-9)
     st = srv.stats()
-    assert st["graph_updates"] > 0                   # a bucket's graph was reused with new buffers
+    assert st["graph_launches"] > 0 and st["graph_updates"] > 0   # recurring buckets replay their graph
     ref = plan.bmode(ch).cpu().numpy()
     for c in done:
         assert_gray(srv.result(c, plan.out_shape).cpu().numpy(), ref)
