@@ -94,6 +94,20 @@ __device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int r
     return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
 }
 
+// Element range of (line, depth tile): the tile's element box (conservative: elements
+// outside it are outside the aperture at every depth of the tile, their samples are 0),
+// as the contiguous index range from its first to its last element (e = iy * nx + ix;
+// a superset on matrix arrays, whose extra elements fail the per-sample aperture test).
+struct ElemBox {
+    int lo, hi;
+    __device__ __forceinline__ bool has(int e) const { return e >= lo && e <= hi; }
+    __device__ __forceinline__ bool any(int e0, int e1) const { return e1 >= lo && e0 <= hi; }
+};
+__device__ __forceinline__ ElemBox elem_box(const DevPlan *__restrict__ P, int line, int i) {
+    const short4 b = __ldg(&P->ap_box[line * P->n_tiles + i / kTD]);
+    return ElemBox{b.z * P->el_nx + b.x, b.w * P->el_nx + b.y};
+}
+
 // K steps of one MMA chain, issued by one thread (2 core matrices along K per step).
 __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo, uint32_t a_sbo, uint32_t b,
                                           uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc, int ksteps, bool acc) {
@@ -190,24 +204,30 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
             line = (int)(tile / nblk);
             i = (int)(tile % nblk) * kTile + t;
             row_ok = i < nd;
-            float n2 = 0.0f;
+            float n2v[2] = {0.0f, 0.0f};
             const int n_el = a.plan->n_el;
+            // the tile's 128 depths lie in one 256-depth delay tile: one element box for the CTA
+            const ElemBox box = elem_box(a.plan, line, (int)(tile % nblk) * kTile);
             PixelGeo g;
             if (row_ok) g = pixel_geo(a.plan, a.ch, line, i);
 #pragma unroll 1
             for (int c = 0; c < 16; ++c) {
+                if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
+                    chunk(sm, S::X, c, t) = make_uint4(0u, 0u, 0u, 0u);
+                    continue;
+                }
                 float v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int e = 8 * c + j;
                     bool act = false;
-                    v[j] = (row_ok && e < n_el) ? element_sample(a.plan, g, e, act) : 0.0f;
-                    n2 = fmaf(v[j], v[j], n2);
+                    v[j] = (row_ok && e < n_el && box.has(e)) ? element_sample(a.plan, g, e, act) : 0.0f;
+                    n2v[j & 1] = fmaf(v[j], v[j], n2v[j & 1]);
                     if (act) mk[e >> 5] |= 1u << (e & 31);
                 }
                 chunk(sm, S::X, c, t) = pack8(v);
             }
-            nrm = sqrtf(n2);
+            nrm = sqrtf(n2v[0] + n2v[1]);
         } else {
             p = tile * kTile + t;
             row_ok = p < a.n;
@@ -281,16 +301,18 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
             tc::mma_commit(&bar);
         }
         ok = mma_wait(&bar, phase) && ok;
-        float zmax = -INFINITY;
+        // reductions over the 128 outputs in 4 independent partials (latency, not order, matters)
+        float zm4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float v[32];
             tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if ((mk[q] >> j) & 1u) zmax = fmaxf(zmax, v[j] + b3[32 * q + j]);
+                if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], v[j] + b3[32 * q + j]);
         }
-        float se = 0.0f, sx = 0.0f;
+        const float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
+        float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float v[32], x[32];
@@ -300,10 +322,12 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
-                se += ez;
-                sx = fmaf(ez, x[j], sx);
+                se4[j & 3] += ez;
+                sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
             }
         }
+        const float se = (se4[0] + se4[1]) + (se4[2] + se4[3]);
+        const float sx = (sx4[0] + sx4[1]) + (sx4[2] + sx4[3]);
         const float yh = se > 0.0f ? sx / se : 0.0f;
         if (MODE == kForward) {
             if (row_ok) a.y[p * a.stride] = yh * nrm;
@@ -460,9 +484,11 @@ __global__ void __launch_bounds__(128) features_kernel(const DevPlan *__restrict
     const int line = blockIdx.y, i = blockIdx.x * 128 + threadIdx.x, nd = P->n_depth;
     if (i >= nd) return;
     const PixelGeo g = pixel_geo(P, ch, line, i);
+    const ElemBox box = elem_box(P, line, blockIdx.x * 128);
     const int n_el = P->n_el;
     float n2 = 0.0f;
-    for (int e = 0; e < n_el; ++e) {
+    const int e_end = min(n_el - 1, box.hi);
+    for (int e = max(0, box.lo); e <= e_end; ++e) {
         bool act;
         const float x = element_sample(P, g, e, act);
         n2 = fmaf(x, x, n2);
@@ -473,12 +499,16 @@ __global__ void __launch_bounds__(128) features_kernel(const DevPlan *__restrict
     uint4 *dst = reinterpret_cast<uint4 *>(feat + pix * kIn);
 #pragma unroll 1
     for (int c = 0; c < 16; ++c) {
+        if (!box.any(8 * c, 8 * c + 7)) {
+            dst[c] = make_uint4(0u, 0u, 0u, 0u);
+            continue;
+        }
         float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = 8 * c + j;
             bool act = false;
-            v[j] = e < n_el ? element_sample(P, g, e, act) * inv : 0.0f;
+            v[j] = (e < n_el && box.has(e)) ? element_sample(P, g, e, act) * inv : 0.0f;
             if (act) mk[e >> 5] |= 1u << (e & 31);
         }
         dst[c] = pack8(v);
