@@ -255,6 +255,51 @@ def _percentiles(xs):
     return pick(0.5), pick(0.99)
 
 
+def bench_table1(args, dev, stream):
+    """The 2D configurations of the run-time table (64 channels, "n_tx / lines
+    per transmit" 64/1, 64/2, 128/1, 128/2; 45 mm; 0.0225 mm isotropic output):
+    per-node device time of the unfused chain (one launch per node, as the
+    paper times its nodes) and of the fused chain, single frames."""
+    import torch
+
+    import paper_1711_06127_b300 as supra
+    import phantom
+
+    out = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    for n_tx, k in ((64, 1), (64, 2), (128, 1), (128, 2)):
+        st = phantom.table1_setup(n_tx, k)
+        plan = supra.Plan(**st.params())
+        ch = phantom.synth_channels(st, phantom.make_phantom(st, 7000 + n_tx + k, 3000, n_points=5), 7000 + n_tx + k,
+                                    device=dev)
+        rf = plan.beamform(ch, stream=stream)
+        env = plan.envelope(rf, stream=stream)
+        bm = plan.logcompress(env, stream=stream)
+        img = plan.scanconvert(bm, stream=stream)
+        ws = torch.empty(max(1, supra.workspace_size([plan])), dtype=torch.uint8, device=dev)
+        nodes = {"beamformer": timed(lambda: plan.beamform(ch, rf, stream)),
+                 "envelope": timed(lambda: plan.envelope(rf, env, stream)),
+                 "log_compression": timed(lambda: plan.logcompress(env, bm, stream)),
+                 "scan_conversion": timed(lambda: plan.scanconvert(bm, img, stream))}
+        fused = timed(lambda: plan.bmode(ch, img, ws, stream))
+        out.append({"config": f"{n_tx}/{k}", "workload": st.name, "n_lines": st.n_lines, "n_samples": st.n_samples,
+                    "grid": "x".join(str(v) for v in plan.out_shape[::-1]),
+                    "node_ms": nodes, "unfused_total_ms": sum(nodes.values()), "fused_ms": fused,
+                    "fused_frames_per_s": 1e3 / fused})
+    return out
+
+
 def bench_apod(args, dev, stream):
     """Learned apodization on 128 elements x 256 lines x 2048 samples: train on
     seeded frames labelled by the exact MV beamformer, then report DAS, MV and
@@ -596,7 +641,8 @@ def run_ours(args):
     d2h = sum(o.numel() for o in outs)
     assert supra.device_status() == 0
 
-    # ---- learned apodization beside MV and DAS; the request loop
+    # ---- the run-time table's 2D shapes (multi-line); learned apodization beside MV and DAS; the request loop
+    table1 = bench_table1(args, dev, stream) if rank == 0 and not args.skip_table1 else None
     apod_res = serve_res = None
     if rank == 0 and not args.skip_apod:
         apod_res, trained = bench_apod(args, dev, stream)
@@ -632,6 +678,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "volume_3d": vol3d,
+            "table1_2d": table1,
             "learned_apodization": apod_res,
             "serving": serve_res,
             "gpu_launches": 2 * args.steps,
@@ -658,6 +705,7 @@ def main(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-3d", action="store_true")
     ap.add_argument("--skip-apod", action="store_true")
+    ap.add_argument("--skip-table1", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--apod-train-frames", type=int, default=200)
     ap.add_argument("--apod-eval-frames", type=int, default=20)

@@ -468,3 +468,19 @@ def apod_frame(setup: Setup, seed: int, device="cuda"):
     cysts = random_cysts(seed)
     ph = make_phantom(setup, seed, 10000, n_points=3, cysts=cysts)
     return synth_channels(setup, ph, seed, device=device), cysts
+
+
+def table1_setup(n_tx: int, lines_per_tx: int, seed_name: str = "") -> Setup:
+    """The 2D configurations of the run-time table (Table 1): a 64-channel
+    linear array (0.3 mm pitch, fc 5 MHz, fs 40 MHz), 45 mm depth, output on
+    a 0.0225 mm isotropic grid; "n_tx / k" = n_tx transmits with k receive
+    lines each (multi-line: n_tx * k - (k - 1) lines evenly over the array)."""
+    c, fs = 1540.0, 40e6
+    n_s = int(math.ceil(45e-3 * 2 / c * fs))
+    n_lines = n_tx * lines_per_tx - (lines_per_tx - 1)
+    span = 63 * 0.3e-3
+    zmax = (n_s - 1) * c / (2 * fs)
+    grid_n = (int(round(span / 0.0225e-3)) + 1, int(round(zmax / 0.0225e-3)) + 1)
+    return linear_setup(64, 0.3e-3, n_lines, n_s, fc=5e6, fs=fs, c=c, focus=30e-3, fnumber=1.5,
+                        lines_per_tx=lines_per_tx, grid_n=grid_n,
+                        name=f"2d-linear-64ch-{n_tx}tx-{lines_per_tx}lpt-45mm-grid0.0225mm")
