@@ -152,25 +152,36 @@ def fir_taps(n_taps: int, cutoff_hz: float, rate_hz: float) -> np.ndarray:
     return h / h.sum()
 
 
+def band_centres(p: dict) -> np.ndarray:
+    """Centre frequencies of the compounding bank (Sec. 2 item 3: envelope
+    detection by IQ demodulation with frequency compounding through a bank of
+    configurable bandpasses).  Reading: n_bands bands spaced band_step apart,
+    symmetric about fc; n_bands = 1 is plain IQ demodulation at fc."""
+    K = max(1, int(p.get("n_bands", 1) or 1))
+    return float(p["fc"]) + (np.arange(K) - (K - 1) / 2.0) * float(p.get("band_step", 0.0) or 0.0)
+
+
 def envelope(p: dict, rf: np.ndarray) -> np.ndarray:
     """IQ demodulation and envelope (Sec. 1 "envelope detection", Sec. 2
-    item 3).  Each line: baseband b(i) = rf(i) exp(-j 2 pi fc i / rate), low-pass
-    with fir_taps (zero padding at the ends, output aligned with the input),
-    envelope 2 |iq| so that a tone's envelope equals its amplitude.  No
-    decimation; one band (the compounding bank of Sec. 2 item 3 reduced to a
-    single band)."""
+    item 3).  For each band centre f_k and each line: baseband
+    b(i) = rf(i) exp(-j 2 pi f_k i / rate), low-pass with fir_taps (zero
+    padding at the ends, output aligned with the input), band envelope
+    2 |iq| so that a tone's envelope equals its amplitude; the compounded
+    envelope is the mean of the band envelopes.  No decimation."""
     rf = np.asarray(rf, dtype=np.float64)
     rate = depth_rate(p)
     n_d = rf.shape[-1]
     h = fir_taps(int(p["fir_taps"]), float(p["fir_cutoff"]), rate)
     H = (len(h) - 1) // 2
-    mix = np.exp(-2j * np.pi * float(p["fc"]) * np.arange(n_d) / rate)
     flat = rf.reshape(-1, n_d)
-    out = np.empty_like(flat)
-    for k in range(flat.shape[0]):
-        iq = np.convolve(flat[k] * mix, h, mode="full")[H:H + n_d]
-        out[k] = 2.0 * np.abs(iq)
-    return out.reshape(rf.shape)
+    out = np.zeros_like(flat)
+    centres = band_centres(p)
+    for f_k in centres:
+        mix = np.exp(-2j * np.pi * f_k * np.arange(n_d) / rate)
+        for k in range(flat.shape[0]):
+            iq = np.convolve(flat[k] * mix, h, mode="full")[H:H + n_d]
+            out[k] += 2.0 * np.abs(iq)
+    return (out / len(centres)).reshape(rf.shape)
 
 
 # ----------------------------------------------------------------------------- log compression

@@ -51,6 +51,8 @@ class Setup:
     t0: float = 0.0
     fir_taps: int = 63
     fir_cutoff: float = 0.0         # Hz; 0 -> fc / 2
+    n_bands: int = 1                # frequency-compounding bank size
+    band_step: float = 0.0          # Hz between band centres
     dyn_range_db: float = 60.0
     log_ref: float = 16000.0
     grid: Optional[dict] = None     # {"n": (nx, ny, nz), "origin": (3,), "spacing": (3,)}
@@ -80,7 +82,8 @@ class Setup:
             depth_step=self.depth_step, geometry=self.geometry, lines_x=self.lines_x, lines_y=self.lines_y,
             c=self.c, fs=self.fs, fc=self.fc, fnumber=self.fnumber, min_half_aperture=self.min_half_aperture,
             window=self.window, n_samples=self.n_samples, t0=self.t0, fir_taps=self.fir_taps,
-            fir_cutoff=self.cutoff, dyn_range_db=self.dyn_range_db, log_ref=self.log_ref, grid=self.grid)
+            fir_cutoff=self.cutoff, dyn_range_db=self.dyn_range_db, log_ref=self.log_ref, grid=self.grid,
+            n_bands=self.n_bands, band_step=self.band_step)
         return d
 
     def replace(self, **kw) -> "Setup":

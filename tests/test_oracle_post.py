@@ -182,3 +182,64 @@ def test_pyramid_constant_volume():
     assert np.all(vol[inside] == 9)
     assert set(np.unique(vol[~inside])) <= {0, 9}
     assert vol.sum() > 0
+
+
+# ----------------------------------------------------------------------------- frequency compounding
+
+def _bank(K, step, fc=5e6, fs=40e6, taps=63):
+    p = dict(c=1540.0, depth_step=1540.0 / (2 * fs), fc=fc, fir_taps=taps, fir_cutoff=fc / 2, n_bands=K,
+             band_step=step)
+    return p
+
+
+def _response(p, f):
+    # |H| of the low-pass at frequency offset f (direct DTFT of the taps)
+    rate = oracle.depth_rate(p)
+    h = oracle.fir_taps(int(p["fir_taps"]), float(p["fir_cutoff"]), rate)
+    n = np.arange(len(h))
+    return abs(np.sum(h * np.exp(-2j * np.pi * f / rate * n)))
+
+
+def test_one_band_is_plain_iq_demodulation():
+    p1 = _bank(1, 0.0)
+    rf = np.random.default_rng(3).normal(size=(2, 500))
+    a = oracle.envelope(p1, rf)
+    b = oracle.envelope(dict(p1, n_bands=None, band_step=None), rf)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_allclose(oracle.band_centres(_bank(3, 1e6)), [4e6, 5e6, 6e6])
+
+
+def test_bank_envelope_of_a_tone_is_the_mean_band_response():
+    # a tone A cos(2 pi f0 t) through band k: steady-state envelope A |H(f0 - f_k)|
+    # (the image at f0 + f_k lies far in the stop band); the bank averages them
+    p = _bank(3, 1.5e6)
+    rate = oracle.depth_rate(p)
+    A, f0 = 3.0, 5.4e6
+    n = np.arange(1200)
+    rf = A * np.cos(2 * np.pi * f0 * n / rate + 0.3)
+    env = oracle.envelope(p, rf[None])[0]
+    want = A * np.mean([_response(p, f0 - fk) for fk in oracle.band_centres(p)])
+    np.testing.assert_allclose(env[200:1000], want, rtol=2e-3)
+
+
+def test_symmetric_bank_is_symmetric_about_fc():
+    p = _bank(4, 1e6)
+    rate = oracle.depth_rate(p)
+    n = np.arange(900)
+    lo = oracle.envelope(p, np.cos(2 * np.pi * (p["fc"] - 0.7e6) * n / rate)[None])[0]
+    hi = oracle.envelope(p, np.cos(2 * np.pi * (p["fc"] + 0.7e6) * n / rate)[None])[0]
+    np.testing.assert_allclose(lo[200:700], hi[200:700], rtol=2e-3)
+
+
+def test_bank_widens_the_pass_band():
+    # a tone 3 MHz above fc sits in the single band's transition (|H(3 MHz)| ~ 0.2 for 63 Blackman
+    # taps at 40 MHz); a bank with 3 MHz steps centres its outer band on it: mean(|H|) ~ 0.4
+    rate = oracle.depth_rate(_bank(1, 0.0))
+    n = np.arange(900)
+    rf = np.cos(2 * np.pi * 8e6 * n / rate)[None]
+    one = oracle.envelope(_bank(1, 0.0), rf)[0, 200:700].mean()
+    p3 = _bank(3, 3e6)
+    bank = oracle.envelope(p3, rf)[0, 200:700].mean()
+    assert one == pytest.approx(_response(_bank(1, 0.0), 3e6), rel=2e-3)
+    assert bank == pytest.approx(np.mean([_response(p3, 8e6 - f) for f in oracle.band_centres(p3)]), rel=2e-3)
+    assert bank > 1.9 * one
