@@ -300,6 +300,44 @@ def bench_table1(args, dev, stream):
     return out
 
 
+def bench_compounding(args, dev, stream, s, ch):
+    """Frequency compounding (a bank of 3 IQ demodulators at fc, fc +- fc/4)
+    on one frame of the main workload: the envelope node with 1 and 3 bands,
+    and the whole chain per frame (fused for one band; beamform -> banked
+    envelope -> log compression -> scan conversion for three)."""
+    import dataclasses
+
+    import torch
+
+    import paper_1711_06127_b300 as supra
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    res = {}
+    for K in (1, 3):
+        st = dataclasses.replace(s, n_bands=K, band_step=s.fc / 4 if K > 1 else 0.0)
+        plan = supra.Plan(**st.params())
+        rf = plan.beamform(ch, stream=stream)
+        env = plan.envelope(rf, stream=stream)
+        img = torch.empty(plan.out_shape, dtype=torch.uint8, device=dev)
+        ws = torch.empty(max(1, supra.workspace_size([plan])), dtype=torch.uint8, device=dev)
+        res[f"bands_{K}"] = {"envelope_node_ms": timed(lambda: plan.envelope(rf, env, stream)),
+                             "chain_ms_per_frame": timed(lambda: plan.bmode(ch, img, ws, stream)),
+                             "chain": "fused" if K == 1 else "unfused (beamform, banked envelope, log, scan conversion)"}
+    res["workload"] = s.name
+    return res
+
+
 def bench_apod(args, dev, stream):
     """Learned apodization on 128 elements x 256 lines x 2048 samples: train on
     seeded frames labelled by the exact MV beamformer, then report DAS, MV and
@@ -643,6 +681,7 @@ def run_ours(args):
 
     # ---- the run-time table's 2D shapes (multi-line); learned apodization beside MV and DAS; the request loop
     table1 = bench_table1(args, dev, stream) if rank == 0 and not args.skip_table1 else None
+    compounding = bench_compounding(args, dev, stream, s, chs[0]) if rank == 0 and not args.skip_table1 else None
     apod_res = serve_res = None
     if rank == 0 and not args.skip_apod:
         apod_res, trained = bench_apod(args, dev, stream)
@@ -679,6 +718,7 @@ def run_ours(args):
                     "steps": e2e_steps},
             "volume_3d": vol3d,
             "table1_2d": table1,
+            "envelope_compounding": compounding,
             "learned_apodization": apod_res,
             "serving": serve_res,
             "gpu_launches": 2 * args.steps,

@@ -108,6 +108,11 @@ typedef struct supra_post {
     double fir_cutoff;          /* Hz (Blackman windowed sinc, unit DC gain)           */
     double dyn_range_db;        /* D: displayed dynamic range                          */
     double log_ref;             /* envelope value mapped to 0 dB (gray level 255)      */
+    int32_t n_bands;            /* frequency compounding (Sec. 2 item 3): 0 or 1 = one band at
+                                   fc; 2..4 = bands at fc + (k - (n_bands-1)/2) band_step, each
+                                   IQ-demodulated at its centre and low-passed, envelopes averaged.
+                                   Frames of plans with n_bands > 1 run the unfused chain.   */
+    double band_step;           /* Hz between band centres (each centre in (0, rate/2))       */
 } supra_post;
 
 /* Cartesian output grid of scan conversion: point (ix, iy, iz) lies at

@@ -60,7 +60,7 @@ class _Rx(ctypes.Structure):
 
 class _Post(ctypes.Structure):
     _fields_ = [("fir_taps", ctypes.c_int32), ("fir_cutoff", ctypes.c_double), ("dyn_range_db", ctypes.c_double),
-                ("log_ref", ctypes.c_double)]
+                ("log_ref", ctypes.c_double), ("n_bands", ctypes.c_int32), ("band_step", ctypes.c_double)]
 
 
 class _Grid(ctypes.Structure):
@@ -169,7 +169,7 @@ class Plan:
     def __init__(self, *, elem_pos, tx_origin, line_origin, line_dir, line_tx, n_depth, depth0, depth_step,
                  geometry="linear", lines_x=None, lines_y=1, c, fs, fc, fnumber, min_half_aperture, window="hann",
                  n_samples, t0=0.0, fir_taps=63, fir_cutoff=None, dyn_range_db=60.0, log_ref=16000.0, grid=None,
-                 **_ignored):
+                 n_bands=1, band_step=0.0, **_ignored):
         lib = load()
         self._keep = []
 
@@ -194,7 +194,7 @@ class Plan:
         self.rx = _Rx(float(c), float(fs), float(fc), float(fnumber), float(min_half_aperture),
                       WINDOWS[window] if isinstance(window, str) else int(window), int(n_samples), float(t0))
         self.post = _Post(int(fir_taps), float(fc / 2 if fir_cutoff is None else fir_cutoff), float(dyn_range_db),
-                          float(log_ref))
+                          float(log_ref), int(n_bands or 1), float(band_step or 0.0))
         self.grid = None
         gptr = None
         if grid is not None:

@@ -12,6 +12,7 @@ namespace supra {
 constexpr int kDepthTile = 256;     // depth samples per beamforming tile (one per consumer thread)
 constexpr int kMaxTaps = 63;       // IQ low-pass taps; shorter filters are zero-padded to 63, centred
 constexpr int kTapSlots = 64;      // 63 centred taps + one zero slot
+constexpr int kMaxBands = 4;       // frequency-compounding bank
 constexpr int kMaxGroup = 16;       // frames of one plan beamformed together
 
 // Per-line constants (fp32; built from fp64 host geometry).
@@ -51,6 +52,9 @@ struct DevPlan {
     // so every filter is applied as a 63-tap one: iq(i) = sum_k' g_k' rf(i + 31 - k').
     float taps_c[kTapSlots]; // h cos(w (k' - 31)): demodulation folded into the taps
     float taps_s[kTapSlots]; // h sin(w (k' - 31))
+    int n_bands;             // frequency-compounding bank (1 = the taps above only)
+    float bank_c[kMaxBands][kTapSlots];   // band k: h cos(w_k (k' - 31))
+    float bank_s[kMaxBands][kTapSlots];   // band k: h sin(w_k (k' - 31)); env = (2 / K) sum_k |iq_k|
     float log_a, log_b;      // code = log_a * log2(env) + log_b  (includes the +1/2 of rounding)
     float log_a2, log_b2;    // the same from |iq|^2: code = log_a2 * log2(|iq|^2) + log_b2
     // ---- scan conversion

@@ -12,17 +12,27 @@ constexpr float kInsideEps = 1e-3f;   // grid points this close (in index units)
 // IQ demodulation + low-pass + |.|: env(i) = 2 |sum_k' g_k' rf(i + 31 - k')| over the
 // plan's centred 63-slot taps, with the demodulation phase folded into the taps
 // (g_k' = h e^{j w (k' - 31)}; the remaining factor e^{-j w i} has unit modulus).
+// Frequency compounding (Sec. 2 item 3): one such sum per band of the plan's bank,
+// env = (2 / K) sum_k |iq_k|.
 __global__ void __launch_bounds__(kEnvTile) envelope_kernel(const DevPlan *__restrict__ P, const float *__restrict__ rf,
                                                             float *__restrict__ env) {
     __shared__ float x[kEnvTile + kTapSlots];
-    __shared__ float tc[kTapSlots], ts[kTapSlots];
+    __shared__ float tc[kMaxBands][kTapSlots], ts[kMaxBands][kTapSlots];
     const int line = blockIdx.y;
     const int nd = P->n_depth;
     const int i0 = blockIdx.x * kEnvTile;
+    const int nb = P->n_bands;
     const float *src = rf + (long long)line * nd;
     for (int k = threadIdx.x; k < kTapSlots; k += kEnvTile) {
-        tc[k] = P->taps_c[k];
-        ts[k] = P->taps_s[k];
+        if (nb == 1) {
+            tc[0][k] = P->taps_c[k];
+            ts[0][k] = P->taps_s[k];
+        } else {
+            for (int b = 0; b < nb; ++b) {
+                tc[b][k] = P->bank_c[b][k];
+                ts[b][k] = P->bank_s[b][k];
+            }
+        }
     }
     for (int k = threadIdx.x; k < kEnvTile + kTapSlots - 1; k += kEnvTile) {
         const int i = i0 - kTapSlots / 2 + k;   // x[k] = rf(i0 - 32 + k)
@@ -31,14 +41,18 @@ __global__ void __launch_bounds__(kEnvTile) envelope_kernel(const DevPlan *__res
     __syncthreads();
     const int i = i0 + threadIdx.x;
     if (i >= nd) return;
-    float re = 0.0f, im = 0.0f;
     const float *xp = x + threadIdx.x + kTapSlots - 1;   // rf(i + 31)
+    float mag = 0.0f;
+    for (int b = 0; b < nb; ++b) {
+        float re = 0.0f, im = 0.0f;
 #pragma unroll 8
-    for (int k = 0; k < kTapSlots; ++k) {
-        re = fmaf(tc[k], xp[-k], re);
-        im = fmaf(ts[k], xp[-k], im);
+        for (int k = 0; k < kTapSlots; ++k) {
+            re = fmaf(tc[b][k], xp[-k], re);
+            im = fmaf(ts[b][k], xp[-k], im);
+        }
+        mag += sqrtf(fmaf(re, re, im * im));
     }
-    env[(long long)line * nd + i] = 2.0f * sqrtf(fmaf(re, re, im * im));
+    env[(long long)line * nd + i] = nb == 1 ? 2.0f * mag : (2.0f / (float)nb) * mag;
 }
 
 __device__ __forceinline__ uint8_t log_code(const DevPlan *P, float env) {

@@ -409,7 +409,8 @@ bool valid_request(const supra_server *s, const supra_request &r, supra_plan_inf
         return false;
     // the request alone must fit the arena (with its share of a batch workspace)
     const size_t need = (r.ch_host ? align_up((size_t)info.channel_bytes) : 0) + align_up(out_bytes(info)) +
-                        align_up(scratch_bytes(r, info)) + (r.kind == SUPRA_KIND_DAS && info.has_grid ? align_up((size_t)info.bmode_bytes) : 0);
+                        align_up(scratch_bytes(r, info)) +
+                        (r.kind == SUPRA_KIND_DAS ? align_up(supra_bmode_workspace_size(1, &r.plan)) : 0);
     return need <= s->arena.size();
 }
 

@@ -292,6 +292,9 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     if (post->fir_taps < 1 || post->fir_taps > kMaxTaps || (post->fir_taps % 2) == 0) return SUPRA_EINVAL;
     if (!finite_pos(post->fir_cutoff) || !finite_pos(post->dyn_range_db) || !finite_pos(post->log_ref))
         return SUPRA_EINVAL;
+    const int n_bands = post->n_bands <= 1 ? 1 : post->n_bands;
+    if (n_bands > kMaxBands || (n_bands > 1 && !(std::isfinite(post->band_step) && post->band_step >= 0.0)))
+        return SUPRA_EINVAL;
     for (int e = 0; e < 3 * n_el; ++e)
         if (!std::isfinite(probe->elem_pos[e])) return SUPRA_EINVAL;
     for (int t = 0; t < 3 * n_tx; ++t)
@@ -537,6 +540,20 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
             H.taps_c[kp] = (float)(h[k] * std::cos(w * (k - Hh)));
             H.taps_s[kp] = (float)(h[k] * std::sin(w * (k - Hh)));
         }
+        // frequency-compounding bank: band centres fc + (k - (K-1)/2) step, each in (0, rate/2)
+        H.n_bands = n_bands;
+        for (int b = 0; b < kMaxBands; ++b)
+            for (int k = 0; k < kTapSlots; ++k) H.bank_c[b][k] = H.bank_s[b][k] = 0.0f;
+        for (int b = 0; b < n_bands; ++b) {
+            const double fk = rx->fc + (b - (n_bands - 1) / 2.0) * (n_bands > 1 ? post->band_step : 0.0);
+            if (!(fk > 0.0 && fk < depth_rate / 2)) return SUPRA_EINVAL;
+            const double wk = 2.0 * kPi * fk / depth_rate;
+            for (int k = 0; k < K; ++k) {
+                const int kp = k + (kMaxTaps - 1) / 2 - Hh;
+                H.bank_c[b][kp] = (float)(h[k] * std::cos(wk * (k - Hh)));
+                H.bank_s[b][kp] = (float)(h[k] * std::sin(wk * (k - Hh)));
+            }
+        }
         const double D = post->dyn_range_db;
         const double la = 255.0 / D * 20.0 * std::log10(2.0);
         const double lb = 255.0 / D * (D - 20.0 * std::log10(post->log_ref)) + 0.5;
@@ -659,11 +676,20 @@ int supra_scanconvert(const supra_plan *plan, const uint8_t *bm, uint8_t *img, v
     return launch_scan(S, static_cast<cudaStream_t>(stream));
 }
 
+// Workspace of one frame in the batched chain: its log-compressed lines when it is
+// scan-converted; frames of a compounding plan (n_bands > 1) run the unfused chain
+// and also hold their RF and envelope lines.
+static size_t frame_workspace(const supra_plan *p) {
+    size_t b = p->host.has_grid ? align_up((size_t)p->info.bmode_bytes, 256) : 0;
+    if (p->host.n_bands > 1) b += 2 * align_up((size_t)p->info.rf_bytes, 256);
+    return b;
+}
+
 size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *plans) {
     if (n < 1 || !plans) return 0;
     size_t total = 0;
     for (int k = 0; k < n; ++k)
-        if (plans[k] && plans[k]->host.has_grid) total += align_up((size_t)plans[k]->info.bmode_bytes, 256);
+        if (plans[k]) total += frame_workspace(plans[k]);
     return total;
 }
 
@@ -676,17 +702,28 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
     if (need > 0 && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)))
         return SUPRA_EWORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // log-compressed lines of scan-converted frames go to the workspace
+    // log-compressed lines of scan-converted frames go to the workspace; frames of
+    // compounding plans run beamform -> envelope (band bank) -> log compression there
     std::vector<uint8_t *> bm(n);
     {
         size_t off = 0;
         for (int k = 0; k < n; ++k) {
+            char *w = static_cast<char *>(workspace) + off;
             if (plans[k]->host.has_grid) {
-                bm[k] = static_cast<uint8_t *>(workspace) + off;
-                off += align_up((size_t)plans[k]->info.bmode_bytes, 256);
+                bm[k] = reinterpret_cast<uint8_t *>(w);
+                w += align_up((size_t)plans[k]->info.bmode_bytes, 256);
             } else {
                 bm[k] = out[k];
             }
+            if (plans[k]->host.n_bands > 1) {
+                float *rf = reinterpret_cast<float *>(w);
+                float *env = reinterpret_cast<float *>(w + align_up((size_t)plans[k]->info.rf_bytes, 256));
+                int rc = supra_beamform(plans[k], ch[k], rf, stream);
+                if (!rc) rc = supra_envelope(plans[k], rf, env, stream);
+                if (!rc) rc = supra_logcompress(plans[k], env, bm[k], stream);
+                if (rc) return rc;
+            }
+            off += frame_workspace(plans[k]);
         }
     }
     // Frames of one plan that are adjacent form groups of up to kMaxGroup; one launch
@@ -697,6 +734,10 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
     };
     std::vector<Grp> groups;
     for (int k = 0; k < n;) {
+        if (plans[k]->host.n_bands > 1) {   // done above by the unfused chain
+            ++k;
+            continue;
+        }
         Grp g{plans[k], k, 0};
         const int gmax = std::min(kMaxGroup, std::max(1, g.p->max_group.load(std::memory_order_relaxed)));
         while (k < n && plans[k] == g.p && g.n < gmax) {

@@ -54,6 +54,8 @@ def _params(**over):
     dict(n_depth=0), dict(n_samples=0), dict(window=7), dict(depth_step=0.0), dict(depth0=-1e-3),
     dict(line_tx=np.full(64, 64, np.int32)), dict(line_tx=np.full(64, -1, np.int32)),
     dict(line_dir=np.tile([0.0, 0.0, 2.0], (64, 1))), dict(fir_cutoff=25e6), dict(c=float("nan")),
+    dict(n_bands=5, band_step=1e6), dict(n_bands=3, band_step=20e6), dict(n_bands=2, band_step=float("nan")),
+    dict(n_bands=3, band_step=-1e6),
 ])
 def test_invalid_parameters_are_rejected(lib, over):
     with pytest.raises(supra.SupraError) as e:

@@ -327,3 +327,37 @@ def test_table1_multiline_frame_matches_oracle():
     ref = oracle.scanconvert(p, bm)[:, 0, :]
     assert img.shape == ref.shape
     assert_gray(img, ref, what="table-1 128/2 frame")
+
+
+def _compounding(s):
+    s.n_bands, s.band_step = 3, s.fc / 4
+    return s
+
+
+def test_compounded_envelope_node_matches_oracle():
+    # the band bank of Sec. 2 item 3 on identical fp32 RF input
+    s = _compounding(small_linear(24, 6, 700))
+    p = s.params()
+    plan = supra.Plan(**p)
+    rf = torch.as_tensor(np.random.default_rng(5).normal(0, 1000, plan.line_shape).astype(np.float32)).cuda()
+    env = plan.envelope(rf).cpu().numpy()
+    ref = oracle.envelope(p, rf.cpu().numpy().astype(np.float64))
+    assert max_norm_err(env, ref) <= ENV_TOL
+
+
+def test_compounded_chain_and_mixed_batch_match():
+    s = _compounding(phantom.linear_setup(48, 0.3e-3, 24, 900, fc=5e6, fs=40e6, grid_n=(96, 160)))
+    p = s.params()
+    ch = phantom.synth_channels(s, phantom.make_phantom(s, 91, 800, n_points=3), 91)
+    plan = supra.Plan(**p)
+    img = plan.bmode(ch.cuda()).cpu().numpy()
+    assert_gray(img, oracle.bmode(p, ch.numpy()), what="compounded chain")
+    # a batch mixing the compounding plan with a one-band plan: each frame as alone
+    s1 = phantom.linear_setup(32, 0.3e-3, 16, 600, fc=5e6, fs=40e6, grid_n=(64, 96))
+    plan1 = supra.Plan(**s1.params())
+    ch1 = phantom.synth_channels(s1, phantom.make_phantom(s1, 92, 500), 92).cuda()
+    outs = supra.bmode_batched([plan, plan1, plan], [ch.cuda(), ch1, ch.cuda()])
+    np.testing.assert_array_equal(outs[0].cpu().numpy(), img)
+    np.testing.assert_array_equal(outs[2].cpu().numpy(), img)
+    np.testing.assert_array_equal(outs[1].cpu().numpy(), plan1.bmode(ch1).cpu().numpy())
+    assert supra.device_status() == 0
