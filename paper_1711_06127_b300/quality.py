@@ -42,3 +42,38 @@ def cyst_stats(params: dict, env_lines, bm_lines, cyst, dyn_range_db: float = 60
     contrast = (bm[ring].mean() - bm[inside].mean()) * dyn_range_db / 255.0
     return {"contrast_db": float(contrast), "cnr": float(cnr), "n_inside": int(inside.sum()),
             "n_ring": int(ring.sum())}
+
+
+def fwhm(profile, spacing: float) -> float:
+    """Full width at half maximum (the -6 dB width of an envelope profile)
+    around the profile's peak, with linear interpolation of the two half-level
+    crossings; spacing is the sample distance."""
+    y = np.asarray(profile, np.float64)
+    k = int(np.argmax(y))
+    half = y[k] / 2.0
+    i = k
+    while i > 0 and y[i - 1] > half:
+        i -= 1
+    left = (i - 1) + (half - y[i - 1]) / (y[i] - y[i - 1]) if i > 0 else 0.0
+    j = k
+    while j < len(y) - 1 and y[j + 1] > half:
+        j += 1
+    right = j + (y[j] - half) / (y[j] - y[j + 1]) if j < len(y) - 1 else float(len(y) - 1)
+    return (right - left) * spacing
+
+
+def point_fwhm(params: dict, env_lines, line: int, depth: int, search: int = 20) -> dict:
+    """Lateral and axial -6 dB widths (metres) of a point target near (line,
+    depth) in envelope lines of a linear scan: the peak within +-search
+    samples, then its profile across lines and along depth."""
+    env = np.asarray(env_lines, np.float64)
+    L, N = env.shape
+    i0, i1 = max(0, depth - search), min(N, depth + search + 1)
+    l0, l1 = max(0, line - 3), min(L, line + 4)
+    sub = env[l0:l1, i0:i1]
+    pl, pi = np.unravel_index(int(np.argmax(sub)), sub.shape)
+    pl, pi = pl + l0, pi + i0
+    xs = np.asarray(params["line_origin"], np.float64)[:, 0]
+    dx = float(np.mean(np.diff(xs))) if len(xs) > 1 else 1.0
+    return {"lateral_m": fwhm(env[:, pi], dx), "axial_m": fwhm(env[pl, :], float(params["depth_step"])),
+            "line": int(pl), "depth": int(pi)}
