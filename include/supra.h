@@ -287,6 +287,31 @@ SUPRA_API int supra_apod_adam(float *params, float *m, float *v, const float *gr
 SUPRA_API int supra_apod_mlp(const supra_plan *plan, const float *params, const int16_t *ch, float *rf, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Headless volume rendering of a scan-converted volume (the paper shows
+ * rendered 3D output, Fig. 4b; no graphics API: the image is a device
+ * buffer).  Orthographic ray march: pixel (px, py) of a width x height image
+ * casts the ray from centre + (px - (width-1)/2) right + (py - (height-1)/2)
+ * down along the unit direction dir, sampled at t0 + k dt, k < n_steps
+ * (metres).  Samples are trilinear in the uint8 volume [nz][ny][nx] laid on
+ * `grid`, 0 outside.  SUPRA_RENDER_MIP: image = maximum sample (0..255).
+ * SUPRA_RENDER_EA: front-to-back emission-absorption, a = clamp((v - lo) /
+ * (hi - lo), 0, 1) alpha, c = v / 255, C = sum T a c, T *= 1 - a (0..1).
+ * vol, image: device pointers; image float [height][width].
+ * Errors: SUPRA_EINVAL (sizes, a zero ray direction, hi <= lo).
+ * ------------------------------------------------------------------------ */
+enum { SUPRA_RENDER_MIP = 0, SUPRA_RENDER_EA = 1 };
+
+typedef struct {
+    double centre[3], right[3], down[3], dir[3];
+    double t0, dt;
+    int32_t n_steps, width, height, mode;
+    double lo, hi, alpha;
+} supra_camera;
+
+SUPRA_API int supra_render(const supra_grid *grid, const uint8_t *vol, const supra_camera *cam, float *image,
+                           void *stream);
+
+/* ------------------------------------------------------------------------
  * Tuning.  Frames of one plan that are adjacent in a batch share a DAS tile
  * (frames x 256 depths x 1 line) of up to max_group frames: larger tiles
  * share the delay and weight arithmetic across frames, smaller ones expose

@@ -27,7 +27,7 @@ EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "su
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
            "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_apod_features", "supra_apod_forward",
            "supra_apod_workspace_size", "supra_apod_grad", "supra_apod_adam", "supra_apod_mlp",
-           "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode", "supra_server_create",
+           "supra_render", "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode", "supra_server_create",
            "supra_server_submit", "supra_server_submit_trace", "supra_server_poll", "supra_server_wait",
            "supra_server_release", "supra_server_get_stats", "supra_server_now", "supra_server_destroy",
            "supra_device_status", "supra_strerror", "supra_version")
@@ -66,6 +66,13 @@ class _Post(ctypes.Structure):
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double * 3)]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("centre", ctypes.c_double * 3), ("right", ctypes.c_double * 3), ("down", ctypes.c_double * 3),
+                ("dir", ctypes.c_double * 3), ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+                ("n_steps", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("lo", ctypes.c_double), ("hi", ctypes.c_double), ("alpha", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -113,6 +120,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_apod_grad.argtypes = [P, I64, I64, P, P, P, P, P, P, P, ctypes.c_size_t, P]
     lib.supra_apod_adam.argtypes = [P, P, P, P, ctypes.c_int32, F, F, F, F, P]
     lib.supra_apod_mlp.argtypes = [P, P, P, P, P]
+    lib.supra_render.argtypes = [ctypes.POINTER(_Grid), P, ctypes.POINTER(_Camera), P, P]
     lib.supra_plan_set_max_group.argtypes = [P, ctypes.c_int32]
     lib.supra_plan_get_max_group.argtypes = [P]
     lib.supra_autotune_bmode.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.c_size_t,
@@ -384,6 +392,28 @@ def bmode_batched(plans: Sequence[Plan], chs, outs=None, workspace=None, stream=
     oa = P(*[_dev_tensor(o, torch.uint8, p.out_shape, "out") for p, o in zip(plans, outs)])
     _check(load().supra_bmode_batched(n, pa, ca, oa, wptr, wbytes, _stream_ptr(stream)), "supra_bmode_batched")
     return outs
+
+
+def render(vol, grid: dict, camera: dict, width: int, height: int, mode: str = "mip", lo: float = 0.0,
+           hi: float = 255.0, alpha: float = 1.0, image=None, stream=None):
+    """Headless volume rendering (supra_render) of a uint8 volume [nz][ny][nx]
+    on `grid` ({"n", "origin", "spacing"}); camera: centre, right, down, dir
+    (3-vectors, metres), t0, dt, n_steps.  Returns float [height, width]."""
+    import torch
+
+    n = grid["n"]
+    g = _Grid(int(n[0]), int(n[1]), int(n[2]), (ctypes.c_double * 3)(*grid["origin"]),
+              (ctypes.c_double * 3)(*grid["spacing"]))
+    v3 = lambda k: (ctypes.c_double * 3)(*[float(x) for x in camera[k]])
+    cam = _Camera(v3("centre"), v3("right"), v3("down"), v3("dir"), float(camera["t0"]), float(camera["dt"]),
+                  int(camera["n_steps"]), int(width), int(height), {"mip": 0, "ea": 1}[mode], float(lo), float(hi),
+                  float(alpha))
+    if image is None:
+        image = torch.empty((height, width), dtype=torch.float32, device=vol.device)
+    _check(load().supra_render(ctypes.byref(g), _dev_tensor(vol, torch.uint8, (int(n[2]), int(n[1]), int(n[0])), "vol"),
+                               ctypes.byref(cam), _dev_tensor(image, torch.float32, (height, width), "image"),
+                               _stream_ptr(stream)), "supra_render")
+    return image
 
 
 def device_status(clear: bool = True) -> int:

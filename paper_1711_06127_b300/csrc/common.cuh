@@ -52,9 +52,6 @@ struct DevPlan {
     // so every filter is applied as a 63-tap one: iq(i) = sum_k' g_k' rf(i + 31 - k').
     float taps_c[kTapSlots]; // h cos(w (k' - 31)): demodulation folded into the taps
     float taps_s[kTapSlots]; // h sin(w (k' - 31))
-    int n_bands;             // frequency-compounding bank (1 = the taps above only)
-    float bank_c[kMaxBands][kTapSlots];   // band k: h cos(w_k (k' - 31))
-    float bank_s[kMaxBands][kTapSlots];   // band k: h sin(w_k (k' - 31)); env = (2 / K) sum_k |iq_k|
     float log_a, log_b;      // code = log_a * log2(env) + log_b  (includes the +1/2 of rounding)
     float log_a2, log_b2;    // the same from |iq|^2: code = log_a2 * log2(|iq|^2) + log_b2
     // ---- scan conversion
@@ -65,6 +62,11 @@ struct DevPlan {
     float u0, du_inv;        // x-axis line coordinate: u = (t - u0) * du_inv (t = x, angle or tan-angle)
     float w0, dw_inv;        // y-axis line coordinate (pyramid)
     float v0, dv_inv;        // depth coordinate: v = (r - v0) * dv_inv
+    // frequency-compounding bank (1 = the taps above only); kept last so the
+    // fields the beamforming kernel reads keep their place
+    int n_bands;
+    float bank_c[kMaxBands][kTapSlots];   // band k: h cos(w_k (k' - 31))
+    float bank_s[kMaxBands][kTapSlots];   // band k: h sin(w_k (k' - 31)); env = (2 / K) sum_k |iq_k|
 };
 
 // A group of up to kMaxGroup frames beamformed together under one plan.

@@ -15,6 +15,7 @@
 #include "post_kernels.cuh"
 #include "mv_kernel.cuh"
 #include "apod_kernel.cuh"
+#include "render_kernel.cuh"
 
 using namespace supra;
 
@@ -833,6 +834,47 @@ int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const i
         const dim3 grid((plan->host.n_depth + w - 1) / w, plan->host.n_lines);
         mv_kernel<double><<<grid, w * 32, 0, st>>>(plan->dev, ch, rf, subaperture, loading);
     }
+    return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- volume rendering
+
+int supra_render(const supra_grid *grid, const uint8_t *vol, const supra_camera *cam, float *image, void *stream) {
+    if (!grid || !vol || !cam || !image) return SUPRA_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || cam->width < 1 || cam->height < 1 || cam->n_steps < 0 ||
+        (cam->mode != SUPRA_RENDER_MIP && cam->mode != SUPRA_RENDER_EA))
+        return SUPRA_EINVAL;
+    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 40) || (long long)grid->nx * grid->ny > 0x7fffffffLL)
+        return SUPRA_EINVAL;
+    for (int k = 0; k < 3; ++k)
+        if (!finite_pos(grid->spacing[k]) || !std::isfinite(grid->origin[k])) return SUPRA_EINVAL;
+    const double dn = std::sqrt(cam->dir[0] * cam->dir[0] + cam->dir[1] * cam->dir[1] + cam->dir[2] * cam->dir[2]);
+    if (!(dn > 0.0) || !std::isfinite(dn) || !std::isfinite(cam->t0) || !std::isfinite(cam->dt)) return SUPRA_EINVAL;
+    if (cam->mode == SUPRA_RENDER_EA && !(cam->hi > cam->lo && std::isfinite(cam->alpha))) return SUPRA_EINVAL;
+    RenderArgs a{};
+    a.vol = vol;
+    a.nx = grid->nx, a.ny = grid->ny, a.nz = grid->nz;
+    double base[3], R[3], D[3], S[3];
+    for (int k = 0; k < 3; ++k) {
+        const double d = cam->dir[k] / dn;
+        base[k] = (cam->centre[k] - 0.5 * (cam->width - 1) * cam->right[k] - 0.5 * (cam->height - 1) * cam->down[k] +
+                   cam->t0 * d - grid->origin[k]) / grid->spacing[k];
+        R[k] = cam->right[k] / grid->spacing[k];
+        D[k] = cam->down[k] / grid->spacing[k];
+        S[k] = cam->dt * d / grid->spacing[k];
+        if (!std::isfinite(base[k]) || !std::isfinite(R[k]) || !std::isfinite(D[k])) return SUPRA_EINVAL;
+    }
+    a.bx = (float)base[0], a.by = (float)base[1], a.bz = (float)base[2];
+    a.rx = (float)R[0], a.ry = (float)R[1], a.rz = (float)R[2];
+    a.dx = (float)D[0], a.dy = (float)D[1], a.dz = (float)D[2];
+    a.sx = (float)S[0], a.sy = (float)S[1], a.sz = (float)S[2];
+    a.n_steps = cam->n_steps, a.W = cam->width, a.H = cam->height, a.mode = cam->mode;
+    a.lo = (float)cam->lo;
+    a.inv_range = cam->mode == SUPRA_RENDER_EA ? (float)(1.0 / (cam->hi - cam->lo)) : 0.0f;
+    a.alpha = (float)cam->alpha;
+    a.image = image;
+    const dim3 grd((cam->width + kRenderTile - 1) / kRenderTile, (cam->height + kRenderTile - 1) / kRenderTile);
+    render_kernel<<<grd, dim3(kRenderTile, kRenderTile), 0, static_cast<cudaStream_t>(stream)>>>(a);
     return check_cuda(cudaGetLastError());
 }
 
