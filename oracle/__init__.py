@@ -45,6 +45,7 @@ class _Geom(ctypes.Structure):
         ("c", ctypes.c_double), ("fs", ctypes.c_double), ("t0", ctypes.c_double),
         ("fnumber", ctypes.c_double), ("min_half_aperture", ctypes.c_double),
         ("window", ctypes.c_int32), ("n_s", ctypes.c_int32),
+        ("tx_dir", ctypes.POINTER(ctypes.c_double)), ("compound", ctypes.c_int32),
     ]
 
 
@@ -73,12 +74,15 @@ class Geometry:
         self.lo = np.ascontiguousarray(p["line_origin"], dtype=np.float64)
         self.ld = np.ascontiguousarray(p["line_dir"], dtype=np.float64)
         self.lt = np.ascontiguousarray(p["line_tx"], dtype=np.int32)
+        td = p.get("tx_dir")
+        self.td = None if td is None else np.ascontiguousarray(td, dtype=np.float64).reshape(-1, 3)
         dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.g = _Geom(self.elem.shape[0], dp(self.elem), self.tx.shape[0], dp(self.tx), self.lo.shape[0],
                        dp(self.lo), dp(self.ld), self.lt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                        int(p["n_depth"]), float(p["depth0"]), float(p["depth_step"]), float(p["c"]),
                        float(p["fs"]), float(p.get("t0", 0.0)), float(p["fnumber"]),
-                       float(p["min_half_aperture"]), WINDOWS[p["window"]], int(p["n_samples"]))
+                       float(p["min_half_aperture"]), WINDOWS[p["window"]], int(p["n_samples"]),
+                       dp(self.td) if self.td is not None else None, int(p.get("compound", 0) or 0))
 
     @property
     def ref(self):

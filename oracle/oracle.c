@@ -30,6 +30,14 @@
  * transmit origin, normalisation by the weight sum, linear interpolation, a
  * separable square aperture, zero padding outside the record.
  *
+ * Plane-wave transmits (planned in the paper's outlook, Sec. 2, citing
+ * ultrafast plane-wave imaging): a transmit t with a nonzero direction n_t
+ * is a plane wave that passes its origin o_t at time 0, so it reaches p after
+ * n_t.(p - o_t) / c (n_t normalised) instead of |p - o_t| / c.  Coherent
+ * compounding: each line is reconstructed from every transmit event of the
+ * frame and the per-transmit delay-and-sum values are averaged,
+ *     RF_comp(l, i) = (1 / n_tx) sum_t RF_t(l, i).
+ *
  * The minimum-variance (Capon) beamformer below is not in the paper; it is the
  * textbook spatially smoothed MV estimator with diagonal loading.
  */
@@ -57,6 +65,8 @@ typedef struct {
     double fnumber, min_half_aperture;
     int32_t window;            /* OR_WINDOW_*                                 */
     int32_t n_s;               /* samples per channel                         */
+    const double *tx_dir;      /* NULL or [n_tx][3]: nonzero = plane wave     */
+    int32_t compound;          /* 1: every line averages all transmits        */
 } or_geom;
 
 static double dist3(const double *a, const double *b)
@@ -112,15 +122,28 @@ static void point_and_aperture(const or_geom *g, const double ext[4], int32_t li
     *a = a_f > g->min_half_aperture ? a_f : g->min_half_aperture;
 }
 
-/* delay-and-sum value at (line, depth index i); ch_tx = records of the line's
- * transmit event, [n_el][n_s] */
-static double das_point(const or_geom *g, const double ext[4], const int16_t *ch_tx,
-                        int32_t line, int32_t i)
+/* Transmit path of event t to point p: |p - o_t| (spherical), or
+ * n_t . (p - o_t) for a plane wave of direction n_t. */
+static double tx_path_to(const or_geom *g, int32_t t, const double p[3])
+{
+    const double *o_t = g->tx_origin + 3 * t;
+    if (g->tx_dir) {
+        const double *n = g->tx_dir + 3 * t;
+        double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (len > 0.0)
+            return (n[0] * (p[0] - o_t[0]) + n[1] * (p[1] - o_t[1]) + n[2] * (p[2] - o_t[2])) / len;
+    }
+    return dist3(p, o_t);
+}
+
+/* delay-and-sum value at (line, depth index i) from transmit event t; ch_tx =
+ * records of that transmit event, [n_el][n_s] */
+static double das_point_tx(const or_geom *g, const double ext[4], const int16_t *ch_tx, int32_t t,
+                           int32_t line, int32_t i)
 {
     double p[3], q[2], a;
     point_and_aperture(g, ext, line, i, p, q, &a);
-    const double *o_t = g->tx_origin + 3 * g->line_tx[line];
-    double tx_path = dist3(p, o_t);
+    double tx_path = tx_path_to(g, t, p);
     double num = 0.0, den = 0.0;
     for (int e = 0; e < g->n_el; ++e) {
         const double *x = g->elem + 3 * e;
@@ -139,7 +162,14 @@ static double das_point(const or_geom *g, const double ext[4], const int16_t *ch
     return den > 0.0 ? num / den : 0.0;
 }
 
-/* Whole frame: ch [n_tx][n_el][n_s] -> rf [n_lines][n_depth]. */
+/* delay-and-sum value at (line, i) from the line's own transmit event */
+static double das_point(const or_geom *g, const double ext[4], const int16_t *ch_tx, int32_t line, int32_t i)
+{
+    return das_point_tx(g, ext, ch_tx, g->line_tx[line], line, i);
+}
+
+/* Whole frame: ch [n_tx][n_el][n_s] -> rf [n_lines][n_depth]; with compounding
+ * every line averages the delay-and-sum values of all transmit events. */
 void oracle_das(const or_geom *g, const int16_t *ch, double *rf)
 {
     double ext[4];
@@ -147,15 +177,24 @@ void oracle_das(const or_geom *g, const int16_t *ch, double *rf)
     long rec_tx = (long)g->n_el * g->n_s;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t l = 0; l < g->n_lines; ++l) {
-        const int16_t *ch_tx = ch + rec_tx * g->line_tx[l];
-        for (int32_t i = 0; i < g->n_depth; ++i)
-            rf[(long)l * g->n_depth + i] = das_point(g, ext, ch_tx, l, i);
+        for (int32_t i = 0; i < g->n_depth; ++i) {
+            double v;
+            if (g->compound) {
+                v = 0.0;
+                for (int32_t t = 0; t < g->n_tx; ++t) v += das_point_tx(g, ext, ch + rec_tx * t, t, l, i);
+                v /= (double)g->n_tx;
+            } else {
+                v = das_point(g, ext, ch + rec_tx * g->line_tx[l], l, i);
+            }
+            rf[(long)l * g->n_depth + i] = v;
+        }
     }
 }
 
 /* Selected points only: point k is (lines[k], depths[k]); its transmit
  * event's records are at ch_tx[k] ([n_el][n_s]).  Used for sampled checks of
- * frames too large for a full CPU pass. */
+ * frames too large for a full CPU pass (one transmit per line: no
+ * compounding). */
 void oracle_das_points(const or_geom *g, int32_t n_pts, const int32_t *lines, const int32_t *depths,
                        const int16_t *const *ch_tx, double *out)
 {
@@ -195,8 +234,7 @@ int32_t oracle_delayed_samples(const or_geom *g, const int16_t *ch_tx, int32_t l
     double ext[4], p[3], q[2], a;
     array_extent(g, ext);
     point_and_aperture(g, ext, line, i, p, q, &a);
-    const double *o_t = g->tx_origin + 3 * g->line_tx[line];
-    double tx_path = dist3(p, o_t);
+    double tx_path = tx_path_to(g, g->line_tx[line], p);
     int32_t m = 0;
     for (int e = 0; e < g->n_el; ++e) {
         const double *xe = g->elem + 3 * e;

@@ -138,3 +138,60 @@ def test_sampled_points_match_full_frame():
     depths = rng.integers(0, s.n_depth, 40)
     got = oracle.das_points(p, lines, depths, [ch[s.line_tx[l]] for l in lines])
     np.testing.assert_array_equal(got, rf[lines, depths])
+
+
+# ----------------------------------------------------------------------------- plane waves and compounding
+
+def _plane_setup(n_el=16, n_lines=6, n_s=400, angles=(0.0,)):
+    s = phantom.linear_setup(n_el, 0.3e-3, n_lines, n_s, fc=5e6, fs=40e6)
+    p = s.params()
+    th = np.deg2rad(np.asarray(angles, np.float64))
+    p["tx_dir"] = np.stack([np.sin(th), np.zeros_like(th), np.cos(th)], 1)
+    # each plane wave passes the array's first (steering toward +x) or last element at time 0
+    x0, x1 = p["elem_pos"][0, 0], p["elem_pos"][-1, 0]
+    p["tx_origin"] = np.stack([np.where(th >= 0, x0, x1), np.zeros_like(th), np.zeros_like(th)], 1)
+    p["line_tx"] = np.zeros(n_lines, np.int32)
+    return s, p
+
+
+def test_zero_degree_plane_wave_equals_the_line_origin_transmit():
+    # straight-down lines from z = 0: the 0-degree plane wave arrives at depth r after r / c,
+    # exactly as a spherical transmit from the line's own origin
+    s, p = _plane_setup()
+    ch = phantom.random_channels(s, 3).numpy()
+    plane = oracle.das(p, ch[:1])
+    q = dict(s.params(), tx_origin=np.asarray(s.line_origin), line_tx=np.arange(s.n_lines, dtype=np.int32))
+    sph = oracle.das(q, np.repeat(ch[:1], s.n_lines, axis=0))
+    np.testing.assert_allclose(plane, sph, rtol=1e-12, atol=1e-9)
+
+
+def test_steered_plane_wave_pythagorean_arrival():
+    # element and line at the origin, plane wave n = (3/5, 0, 4/5) through the origin: a point at
+    # depth 5 mm is reached after 4 mm and heard after 5 mm more; fs / c = 10 samples per mm puts
+    # the echo exactly on sample 90 (a spherical transmit from the origin would give sample 100)
+    c, fs = 1540.0, 15.4e6
+    p = dict(elem_pos=np.zeros((1, 3)), tx_origin=np.zeros((1, 3)), tx_dir=np.array([[0.6, 0.0, 0.8]]),
+             line_origin=np.zeros((1, 3)), line_dir=np.array([[0.0, 0.0, 1.0]]), line_tx=np.zeros(1, np.int32),
+             n_depth=201, depth0=0.0, depth_step=0.05e-3, c=c, fs=fs, t0=0.0, fnumber=1.0,
+             min_half_aperture=1e-3, window="rect", n_samples=300)
+    ch = np.zeros((1, 1, 300), np.int16)
+    ch[0, 0, 90] = 1000
+    rf = oracle.das(p, ch)[0]
+    assert rf[100] == pytest.approx(1000.0, rel=1e-9)
+    # a spherical transmit from the origin puts the same echo at 2 r = 9 mm: depth 4.5 mm (i = 90)
+    spherical = oracle.das(dict(p, tx_dir=None), ch)[0]
+    assert spherical[100] == 0.0 and spherical[90] == pytest.approx(1000.0, rel=1e-9)
+
+
+def test_compounding_averages_the_transmits():
+    s, p = _plane_setup(angles=(-6.0, 0.0, 6.0))
+    ch = phantom.random_channels(s, 4).numpy()[:1]
+    one = {a: oracle.das(dict(p, tx_dir=p["tx_dir"][a:a + 1], tx_origin=p["tx_origin"][a:a + 1]), ch)
+           for a in range(3)}
+    # identical transmits compound to the single-transmit image
+    pc = dict(p, compound=1, tx_dir=np.repeat(p["tx_dir"][1:2], 3, 0), tx_origin=np.repeat(p["tx_origin"][1:2], 3, 0))
+    np.testing.assert_allclose(oracle.das(pc, np.repeat(ch, 3, 0)), one[1], rtol=1e-12, atol=1e-9)
+    # with the other transmits' records zero, the compound is that transmit's image / 3
+    rec = np.zeros((3,) + ch.shape[1:], np.int16)
+    rec[2] = ch[0]
+    np.testing.assert_allclose(oracle.das(dict(p, compound=1), rec), one[2] / 3.0, rtol=1e-12, atol=1e-9)
