@@ -88,6 +88,16 @@ typedef struct supra_scan {
     double depth0, depth_step;
     int32_t geometry;           /* SUPRA_GEOM_* (used by scan conversion)             */
     int32_t lines_x, lines_y;   /* line layout; lines_y = 1 for 2D                    */
+    const double *tx_dir;       /* NULL, or [n_tx][3]: a nonzero row makes transmit t a plane
+                                   wave of that direction passing tx_origin[t] at time 0
+                                   (arrival n.(p - o_t) / c); a zero row keeps the spherical
+                                   wave from tx_origin[t] (arrival |p - o_t| / c)            */
+    int32_t compound;           /* 0: line l is formed from transmit line_tx[l]; 1: coherent
+                                   compounding -- every line is formed from every transmit of
+                                   the frame and the per-transmit images are averaged (e.g.
+                                   plane waves at several angles).  Compounding plans serve
+                                   delay-and-sum and the fused chain, not supra_mv or the
+                                   learned apodization (SUPRA_EINVAL there).               */
 } supra_scan;
 
 /* Receive parameters (Sec. 2 item 2; dynamic aperture by F-number). */

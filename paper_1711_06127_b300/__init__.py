@@ -49,7 +49,8 @@ class _Scan(ctypes.Structure):
                 ("n_lines", ctypes.c_int32), ("line_origin", ctypes.POINTER(ctypes.c_double)),
                 ("line_dir", ctypes.POINTER(ctypes.c_double)), ("line_tx", ctypes.POINTER(ctypes.c_int32)),
                 ("n_depth", ctypes.c_int32), ("depth0", ctypes.c_double), ("depth_step", ctypes.c_double),
-                ("geometry", ctypes.c_int32), ("lines_x", ctypes.c_int32), ("lines_y", ctypes.c_int32)]
+                ("geometry", ctypes.c_int32), ("lines_x", ctypes.c_int32), ("lines_y", ctypes.c_int32),
+                ("tx_dir", ctypes.POINTER(ctypes.c_double)), ("compound", ctypes.c_int32)]
 
 
 class _Rx(ctypes.Structure):
@@ -177,7 +178,7 @@ class Plan:
     def __init__(self, *, elem_pos, tx_origin, line_origin, line_dir, line_tx, n_depth, depth0, depth_step,
                  geometry="linear", lines_x=None, lines_y=1, c, fs, fc, fnumber, min_half_aperture, window="hann",
                  n_samples, t0=0.0, fir_taps=63, fir_cutoff=None, dyn_range_db=60.0, log_ref=16000.0, grid=None,
-                 n_bands=1, band_step=0.0, **_ignored):
+                 n_bands=1, band_step=0.0, tx_dir=None, compound=0, **_ignored):
         lib = load()
         self._keep = []
 
@@ -196,9 +197,15 @@ class Plan:
         self.n_el, self.n_tx, self.n_lines = ep.shape[0], tx.shape[0], n_lines
         self.n_depth, self.n_samples = int(n_depth), int(n_samples)
         self.probe = _Probe(ep.shape[0], ep_p)
+        td_p = None
+        if tx_dir is not None:
+            td, td_p = dp(np.asarray(tx_dir, np.float64).reshape(-1, 3))
+            if td.shape[0] != tx.shape[0]:
+                raise ValueError("tx_dir must have one row per transmit")
+        self.compound = int(compound or 0)
         self.scan = _Scan(tx.shape[0], tx_p, n_lines, lo_p, ld_p, lt_p, int(n_depth), float(depth0),
                           float(depth_step), GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry),
-                          int(n_lines if lines_x is None else lines_x), int(lines_y))
+                          int(n_lines if lines_x is None else lines_x), int(lines_y), td_p, self.compound)
         self.rx = _Rx(float(c), float(fs), float(fc), float(fnumber), float(min_half_aperture),
                       WINDOWS[window] if isinstance(window, str) else int(window), int(n_samples), float(t0))
         self.post = _Post(int(fir_taps), float(fc / 2 if fir_cutoff is None else fir_cutoff), float(dyn_range_db),

@@ -16,12 +16,23 @@ constexpr int kMaxBands = 4;       // frequency-compounding bank
 constexpr int kMaxGroup = 16;       // frames of one plan beamformed together
 
 // Per-line constants (fp32; built from fp64 host geometry).
+// Transmit path of one (line, transmit) pair as the excess over r of the path
+// to p = o_l + r d: spherical wave from o_t: |p - o_t| - r with b = d.(o_l - o_t),
+// g = |o_l - o_t|^2; plane wave of direction n through o_t: n.(p - o_t) - r =
+// b + g r with b = n.(o_l - o_t), g = n.d - 1.
+struct TxTerm {
+    float b, g;
+    int tx;             // transmit event (record index)
+    int plane;          // 1: plane wave
+};
+
 struct LineGeo {
     float ox, oy, oz;   // line origin
     float dx, dy, dz;   // unit direction
-    float bt, gt;       // transmit path: bt = d.(o_l - o_t), gt = |o_l - o_t|^2
+    float bt, gt;       // transmit path of the line's own transmit (TxTerm b, g)
     int tx;             // transmit event
-    int pad[3];
+    int plane;          // 1: that transmit is a plane wave
+    int pad[2];
 };
 
 // Resident plan record (lives in device global memory; kernels read it through a pointer).
@@ -67,6 +78,10 @@ struct DevPlan {
     int n_bands;
     float bank_c[kMaxBands][kTapSlots];   // band k: h cos(w_k (k' - 31))
     float bank_s[kMaxBands][kTapSlots];   // band k: h sin(w_k (k' - 31)); env = (2 / K) sum_k |iq_k|
+    // coherent compounding: n_comp transmits per line (1 = the line's own transmit);
+    // txterms [n_lines][n_comp] when n_comp > 1
+    int n_comp;
+    const TxTerm *txterms;
 };
 
 // A group of up to kMaxGroup frames beamformed together under one plan.

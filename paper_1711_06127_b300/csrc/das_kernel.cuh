@@ -58,11 +58,14 @@ struct ElemMeta {
     float beta2, gamma, ex, ey;  // 2 d.(o_l - x_e), |o_l - x_e|^2, x_e, y_e
     int ws;                      // absolute sample index of the row's first staged sample
     int ia, ib;                  // depths (absolute indices) this staged window serves
-    int flags;                   // bit 0 valid, bits 1-2 width class, bit 3 (slot 0): last stage of the tile
+    int flags;                   // bit 0 valid, bits 1-2 width class, bit 3 (slot 0): last stage of the tile,
+                                 // bits 4-15: compounded transmit of the stage
 };
 __device__ __forceinline__ int meta_valid(const ElemMeta &m) { return m.flags & 1; }
 __device__ __forceinline__ int meta_widx(const ElemMeta &m) { return (m.flags >> 1) & 3; }
 __device__ __forceinline__ int meta_last(const ElemMeta &m) { return (m.flags >> 3) & 1; }
+// compounding: index of the stage's transmit among the line's transmits (a stage never mixes them)
+__device__ __forceinline__ int meta_comp(const ElemMeta &m) { return (m.flags >> 4) & 0xFFF; }
 
 // Staged window widths (samples; multiples of 16) and their frame-row strides in shared memory.
 constexpr int kNumWidths = 4;
@@ -123,6 +126,11 @@ __device__ __forceinline__ float path_excess(float r, float beta, float gamma) {
     const float r2 = fmaxf(fmaf(r, r + 2.0f * beta, gamma), 1e-30f);
     const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);
     return __fdividef(fmaf(2.0f * r, beta, gamma), den);
+}
+
+// Transmit path excess over r (see TxTerm): spherical or plane wave.
+__device__ __forceinline__ float tx_excess(float r, float b, float g, int plane) {
+    return plane ? fmaf(g, r, b) : path_excess(r, b, g);
 }
 
 // named barrier among the 256 consumer threads (the producer warp never joins)
@@ -268,8 +276,8 @@ __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo 
 
 // Record window of depths [ia, ib] for element e: start ws (a multiple of 8) and
 // the width class that covers every sample those depths interpolate.
-__device__ __forceinline__ void element_window(const ProdConst &C, const LineGeo &lg, int tile, int ia, int ib,
-                                               float4 xe, ElemMeta &m) {
+__device__ __forceinline__ void element_window(const ProdConst &C, const LineGeo &lg, const TxTerm &tt, int ci,
+                                               int tile, int ia, int ib, float4 xe, ElemMeta &m) {
     const float mx = lg.ox - xe.x, my = lg.oy - xe.y, mz = lg.oz - xe.z;
     const float beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
     const float gamma = mx * mx + my * my + mz * mz;
@@ -278,15 +286,22 @@ __device__ __forceinline__ void element_window(const ProdConst &C, const LineGeo
     const float r1 = C.depth0 + (float)ib * C.depth_step;
     const int kt = __ldg(&C.tile_k[tile]);
     const float ft = __ldg(&C.tile_f[tile]);
-    const float s0 = ft + C.a1 * (float)(ia - i0) + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * C.fsc;
-    const float s1 = ft + C.a1 * (float)(ib - i0) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * C.fsc;
+    const float s0 = ft + C.a1 * (float)(ia - i0) + (tx_excess(r0, tt.b, tt.g, tt.plane) + path_excess(r0, beta, gamma)) * C.fsc;
+    const float s1 = ft + C.a1 * (float)(ib - i0) + (tx_excess(r1, tt.b, tt.g, tt.plane) + path_excess(r1, beta, gamma)) * C.fsc;
     float lo = fminf(s0, s1), hi = fmaxf(s0, s1);
-    // The two-way path is convex in r: its maximum is at an end, its minimum may be
-    // inside; bound that minimum by the sum of the two paths' minima.
-    if ((-beta > r0 && -beta < r1) || (-lg.bt > r0 && -lg.bt < r1)) {
-        const float re = fminf(fmaxf(-beta, r0), r1), rt = fminf(fmaxf(-lg.bt, r0), r1);
+    // The two-way path is convex in r (a plane wave's path is linear): its maximum is at
+    // an end, its minimum may be inside; bound that minimum by the sum of the two paths' minima.
+    const bool tx_min_inside = !tt.plane && -tt.b > r0 && -tt.b < r1;
+    if ((-beta > r0 && -beta < r1) || tx_min_inside) {
+        const float re = fminf(fmaxf(-beta, r0), r1);
         const float de = sqrtf(fmaxf(fmaf(re, re + 2.0f * beta, gamma), 0.0f));
-        const float dtp = sqrtf(fmaxf(fmaf(rt, rt + 2.0f * lg.bt, lg.gt), 0.0f));
+        float dtp;
+        if (tt.plane) {
+            dtp = fminf(fmaf(1.0f + tt.g, r0, tt.b), fmaf(1.0f + tt.g, r1, tt.b));
+        } else {
+            const float rt = fminf(fmaxf(-tt.b, r0), r1);
+            dtp = sqrtf(fmaxf(fmaf(rt, rt + 2.0f * tt.b, tt.g), 0.0f));
+        }
         lo = fminf(lo, (de + dtp) * C.fsc - C.t0fs - (float)kt);
     }
     const int lo_i = kt + (int)floorf(lo) - 1;
@@ -304,22 +319,22 @@ __device__ __forceinline__ void element_window(const ProdConst &C, const LineGeo
     m.ws = ws;
     m.ia = ia;
     m.ib = ib;
-    m.flags = 1 | (widx << 1);
+    m.flags = 1 | (widx << 1) | (ci << 4);
 }
 
 // Stages the element's window of all frames into slot `slot` of a stage (frame
 // rows of width_of(widx) samples, packed).  Returns the bytes that will land.
 template <int G>
-__device__ __forceinline__ uint32_t stage_element(const ProdConst &C, const FrameGroup &fg, int nf, const LineGeo &lg,
+__device__ __forceinline__ uint32_t stage_element(const ProdConst &C, const FrameGroup &fg, int nf, int tx,
                                                   int e, const ElemMeta &m, int16_t *slot_base, uint64_t *full) {
     const int wsamp = width_of(meta_widx(m));
     if (fg.tma) {
-        tma_load_4d(slot_base, &fg.tmap[meta_widx(m)], m.ws >> 1, e, lg.tx, 0, full);
+        tma_load_4d(slot_base, &fg.tmap[meta_widx(m)], m.ws >> 1, e, tx, 0, full);
         return (uint32_t)(G * wsamp * 2);
     }
     const int ws = m.ws, n_s = C.n_s;
     const int c0 = max(ws, 0), c1 = min(ws + wsamp, n_s);
-    const long long rec = ((long long)lg.tx * C.n_el + e) * (long long)n_s;
+    const long long rec = ((long long)tx * C.n_el + e) * (long long)n_s;
     uint32_t total = 0;
     for (int f = 0; f < nf; ++f) {
         int16_t *row = slot_base + f * wsamp;
@@ -580,7 +595,7 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // -------------------------------------------------------------------------------------------------
 // MODE 0: write RF (float [n_lines][n_depth] per frame).
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
-template <int G, int MODE>
+template <int G, int MODE, bool COMP>
 __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_constant__ LaunchGroups L) {
     constexpr int E = kRows / G;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -649,7 +664,14 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
             slot = 0;
             ++n;
         };
-        for (int tile = 0; tile < NT && ok; ++tile) {
+        // With compounding, each tile is staged once per transmit of the line (same
+        // aperture, that transmit's records and delays), as consecutive (tile, transmit)
+        // passes; stages never mix transmits and only the tile's final pass marks its
+        // last stage.  Without compounding there is one pass per tile.
+        const int n_comp = COMP ? P->n_comp : 1;   // compile-time 1 for plans that do not compound
+        for (int vt = 0; vt < NT * n_comp && ok; ++vt) {
+            const int tile = vt / n_comp, ci = vt - tile * n_comp;
+            const bool final_ci = ci == n_comp - 1;
             const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
             const int nbox = (b.y - b.x + 1) * (b.w - b.z + 1) * (halves ? 2 : 1);
             // pass 1: how many elements can be active in this tile
@@ -667,8 +689,14 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 int e, ia, ib;
                 float4 xe;
                 const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                TxTerm tt;
+                if constexpr (COMP) {
+                    tt = P->txterms[line * n_comp + ci];
+                } else {
+                    tt.b = lg.bt, tt.g = lg.gt, tt.tx = lg.tx, tt.plane = lg.plane;
+                }
                 ElemMeta m;
-                if (a) element_window(C, lg, tile, ia, ib, xe, m);
+                if (a) element_window(C, lg, tt, ci, tile, ia, ib, xe, m);
                 uint32_t mask = __ballot_sync(0xffffffffu, a);
                 while (mask) {
                     if (slot == 0 && !acquire()) {
@@ -682,22 +710,25 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                         const int sb = n % kStages;
                         ElemMeta *meta = metas + sb * kRows;
                         meta[slot + rank] = m;
-                        bytes += stage_element<G>(C, fg, nf, lg, e, m,
+                        bytes += stage_element<G>(C, fg, nf, tt.tx, e, m,
                                                   stages + sb * stage_elems + (slot + rank) * G * kSlotSamples,
                                                   &full[sb]);
                     }
                     // drop the `take` lowest lanes of the mask
                     for (int t = 0; t < take; ++t) mask &= mask - 1u;
                     slot += take;
-                    if (slot == E) finalize(++emitted == nst);
+                    if (slot == E) {
+                        ++emitted;
+                        finalize(final_ci && emitted == nst);
+                    }
                 }
             }
-            if (ok && (slot > 0 || emitted == 0)) {
+            if (ok && (slot > 0 || (emitted == 0 && final_ci))) {
                 if (slot == 0 && !acquire()) {
                     ok = false;
                 } else {
                     ++emitted;
-                    finalize(true);
+                    finalize(final_ci);
                 }
             }
         }
@@ -732,7 +763,8 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
             const float qx = fminf(fmaxf(px, P->xmin), P->xmax);
             const float qy = fminf(fmaxf(py, P->ymin), P->ymax);
             const float inv_a = 1.0f / fmaxf(pz * P->inv2f, P->amin);
-            const float base = P->tile_f[tile] + P->a1 * (float)m + path_excess(r, lg.bt, lg.gt) * fsc;
+            float base = P->tile_f[tile] + P->a1 * (float)m + tx_excess(r, lg.bt, lg.gt, lg.plane) * fsc;
+            int cur = 0;   // compounding: transmit whose delay term `base` holds
             const int kt = P->tile_k[tile];
             for (;;) {
                 bool ok = !aborted && mbar_try_wait_sleep(&full[sb], parity);
@@ -747,6 +779,15 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 if (aborted) break;
                 const ElemMeta *meta = metas + sb * kRows;
                 const int last = meta_last(meta[0]);
+                if constexpr (COMP) {
+                    const int ci = meta_comp(meta[0]);
+                    if (ci != cur) {
+                        const int nc = P->n_comp;
+                        const TxTerm tt = P->txterms[line * nc + ci];
+                        base = P->tile_f[tile] + P->a1 * (float)m + tx_excess(r, tt.b, tt.g, tt.plane) * fsc;
+                        cur = ci;
+                    }
+                }
                 consume_stage<G>(stages + sb * stage_elems, meta, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc,
                                  acc2, acc1, wsum);
                 __syncwarp();

@@ -27,7 +27,7 @@ __device__ __forceinline__ PixelGeo pixel_geo(const DevPlan *__restrict__ P, con
     g.qx = fminf(fmaxf(px, P->xmin), P->xmax);
     g.qy = fminf(fmaxf(py, P->ymin), P->ymax);
     g.inv_a = 1.0f / fmaxf(pz * P->inv2f, P->amin);
-    g.base = P->tile_f[tile] + P->a1 * (float)(i - tile * kTD) + path_excess(g.r, g.lg.bt, g.lg.gt) * P->fsc;
+    g.base = P->tile_f[tile] + P->a1 * (float)(i - tile * kTD) + tx_excess(g.r, g.lg.bt, g.lg.gt, g.lg.plane) * P->fsc;
     g.kt = P->tile_k[tile];
     g.rec0 = ch + (long long)g.lg.tx * P->n_el * P->n_s;
     return g;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(mv_warps<T>() * 32) mv_kernel(const DevPlan *_
     const float px = fmaf(r, lg.dx, lg.ox), py = fmaf(r, lg.dy, lg.oy), pz = fmaf(r, lg.dz, lg.oz);
     const float qx = fminf(fmaxf(px, P->xmin), P->xmax), qy = fminf(fmaxf(py, P->ymin), P->ymax);
     const float inv_a = 1.0f / fmaxf(pz * P->inv2f, P->amin);
-    const float base = P->tile_f[tile] + P->a1 * (float)(i - tile * kTD) + path_excess(r, lg.bt, lg.gt) * P->fsc;
+    const float base = P->tile_f[tile] + P->a1 * (float)(i - tile * kTD) + tx_excess(r, lg.bt, lg.gt, lg.plane) * P->fsc;
     const int kt = P->tile_k[tile];
     const int16_t *rec0 = ch + (long long)lg.tx * n_el * n_s;
     // delayed samples of the active elements, compacted in element order

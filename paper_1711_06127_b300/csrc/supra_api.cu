@@ -155,7 +155,7 @@ bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, 
 // kernel choice for a frame group size
 int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
 
-template <int G, int MODE>
+template <int G, int MODE, bool COMP>
 int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -163,23 +163,30 @@ int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const SmemLayout lay(G, MODE, kSlotSamples);
     if (lay.total > max_optin) return SUPRA_EINVAL;
-    auto kern = das_kernel<G, MODE>;
+    auto kern = das_kernel<G, MODE, COMP>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess)
         return SUPRA_ECUDA;
     kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L);
     return check_cuda(cudaGetLastError());
 }
 
-int launch_das(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
-    if (L.total_lines == 0) return SUPRA_OK;
-    if (G == 1) return mode == 0 ? launch_das_t<1, 0>(L, st) : launch_das_t<1, 1>(L, st);
+template <bool COMP>
+int launch_das_c(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
+    if (G == 1) return mode == 0 ? launch_das_t<1, 0, COMP>(L, st) : launch_das_t<1, 1, COMP>(L, st);
     if (mode == 0) return SUPRA_EINVAL;
     switch (G) {
-        case 2: return launch_das_t<2, 1>(L, st);
-        case 4: return launch_das_t<4, 1>(L, st);
-        case 8: return launch_das_t<8, 1>(L, st);
-        default: return launch_das_t<16, 1>(L, st);
+        case 2: return launch_das_t<2, 1, COMP>(L, st);
+        case 4: return launch_das_t<4, 1, COMP>(L, st);
+        case 8: return launch_das_t<8, 1, COMP>(L, st);
+        default: return launch_das_t<16, 1, COMP>(L, st);
     }
+}
+
+// comp: the groups' plans compound several transmits per line (a separate kernel
+// instantiation, so plans that do not compound run the kernel without that code)
+int launch_das(int G, int mode, bool comp, const LaunchGroups &L, cudaStream_t st) {
+    if (L.total_lines == 0) return SUPRA_OK;
+    return comp ? launch_das_c<true>(G, mode, L, st) : launch_das_c<false>(G, mode, L, st);
 }
 
 // Frames of one scan-conversion launch and their host-side plan records (grid sizing).
@@ -299,7 +306,10 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     for (int e = 0; e < 3 * n_el; ++e)
         if (!std::isfinite(probe->elem_pos[e])) return SUPRA_EINVAL;
     for (int t = 0; t < 3 * n_tx; ++t)
-        if (!std::isfinite(scan->tx_origin[t])) return SUPRA_EINVAL;
+        if (!std::isfinite(scan->tx_origin[t]) || (scan->tx_dir && !std::isfinite(scan->tx_dir[t])))
+            return SUPRA_EINVAL;
+    if (scan->compound != 0 && scan->compound != 1) return SUPRA_EINVAL;
+    if (scan->compound && n_tx > 4096) return SUPRA_EINVAL;   // transmit index in the stage metadata
     for (int l = 0; l < n_lines; ++l) {
         const double *d = scan->line_dir + 3 * l;
         const double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -446,11 +456,33 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     for (int e = 0; e < n_el; ++e)
         elem[e] = make_float4((float)probe->elem_pos[3 * e], (float)probe->elem_pos[3 * e + 1],
                               (float)probe->elem_pos[3 * e + 2], 0.f);
+    // transmit terms of a (line, transmit) pair: spherical (b = d.(o_l - o_t), g = |o_l - o_t|^2)
+    // or plane wave (b = n.(o_l - o_t), g = n.d - 1)
+    auto tx_term = [&](int l, int t) {
+        const double *o = scan->line_origin + 3 * l, *d = scan->line_dir + 3 * l;
+        const double *ot = scan->tx_origin + 3 * t;
+        const double m0 = o[0] - ot[0], m1 = o[1] - ot[1], m2 = o[2] - ot[2];
+        TxTerm tt{};
+        tt.tx = t;
+        const double *n = scan->tx_dir ? scan->tx_dir + 3 * t : nullptr;
+        const double nl = n ? std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]) : 0.0;
+        if (nl > 0.0) {
+            const double n0 = n[0] / nl, n1 = n[1] / nl, n2 = n[2] / nl;
+            tt.plane = 1;
+            tt.b = (float)(n0 * m0 + n1 * m1 + n2 * m2);
+            tt.g = (float)(n0 * d[0] + n1 * d[1] + n2 * d[2] - 1.0);
+        } else {
+            tt.b = (float)(d[0] * m0 + d[1] * m1 + d[2] * m2);
+            tt.g = (float)(m0 * m0 + m1 * m1 + m2 * m2);
+        }
+        return tt;
+    };
+    const int n_comp = scan->compound ? n_tx : 1;
+    H.n_comp = n_comp;
     std::vector<LineGeo> lines(n_lines);
+    std::vector<TxTerm> txterms(n_comp > 1 ? (size_t)n_lines * n_comp : 0);
     for (int l = 0; l < n_lines; ++l) {
         const double *o = scan->line_origin + 3 * l, *d = scan->line_dir + 3 * l;
-        const double *ot = scan->tx_origin + 3 * scan->line_tx[l];
-        const double m0 = o[0] - ot[0], m1 = o[1] - ot[1], m2 = o[2] - ot[2];
         LineGeo g{};
         g.ox = (float)o[0];
         g.oy = (float)o[1];
@@ -458,10 +490,13 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
         g.dx = (float)d[0];
         g.dy = (float)d[1];
         g.dz = (float)d[2];
-        g.bt = (float)(d[0] * m0 + d[1] * m1 + d[2] * m2);
-        g.gt = (float)(m0 * m0 + m1 * m1 + m2 * m2);
-        g.tx = scan->line_tx[l];
+        const TxTerm own = tx_term(l, n_comp > 1 ? 0 : scan->line_tx[l]);
+        g.bt = own.b;
+        g.gt = own.g;
+        g.tx = own.tx;
+        g.plane = own.plane;
         lines[l] = g;
+        for (int t = 0; t < (n_comp > 1 ? n_comp : 0); ++t) txterms[(size_t)l * n_comp + t] = tx_term(l, t);
     }
     const int NT = H.n_tiles;
     std::vector<int> tile_k(NT);
@@ -579,6 +614,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     const size_t o_tf = take(sizeof(float) * NT);
     const size_t o_box = take(sizeof(short4) * box.size());
     const size_t o_ord = take(sizeof(int) * n_lines);
+    const size_t o_txt = take(sizeof(TxTerm) * std::max<size_t>(txterms.size(), 1));
     auto *plan = new (std::nothrow) supra_plan();
     if (!plan) return SUPRA_ENOMEM;
     cudaGetDevice(&plan->device);
@@ -594,6 +630,7 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.tile_f = reinterpret_cast<const float *>(b + o_tf);
     H.ap_box = reinterpret_cast<const short4 *>(b + o_box);
     H.line_order = reinterpret_cast<const int *>(b + o_ord);
+    H.txterms = reinterpret_cast<const TxTerm *>(b + o_txt);
     plan->dev = reinterpret_cast<DevPlan *>(b + o_plan);
     plan->host = H;
     cudaError_t err = cudaSuccess;
@@ -604,6 +641,8 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     err = err ? err : cudaMemcpy(b + o_tf, tile_f.data(), sizeof(float) * NT, cudaMemcpyHostToDevice);
     err = err ? err : cudaMemcpy(b + o_box, box.data(), sizeof(short4) * box.size(), cudaMemcpyHostToDevice);
     err = err ? err : cudaMemcpy(b + o_ord, line_order.data(), sizeof(int) * n_lines, cudaMemcpyHostToDevice);
+    if (!txterms.empty())
+        err = err ? err : cudaMemcpy(b + o_txt, txterms.data(), sizeof(TxTerm) * txterms.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
         cudaFree(plan->blob);
         delete plan;
@@ -616,8 +655,9 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     I.n_lines = n_lines;
     I.n_depth = n_d;
     I.channel_bytes = 2LL * n_tx * n_el * n_s;
-    I.aperture_element_samples = ap_count;
-    I.aperture_bytes = 2 * ap_count;
+    // with compounding every line reads its aperture from every transmit's records
+    I.aperture_element_samples = ap_count * n_comp;
+    I.aperture_bytes = 2 * ap_count * n_comp;
     I.rf_bytes = 4LL * n_lines * n_d;
     I.bmode_bytes = (long long)n_lines * n_d;
     I.image_bytes = grid ? (long long)grid->nx * grid->ny * grid->nz : I.bmode_bytes;
@@ -652,7 +692,7 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
     L.uniform = 1;
-    return launch_das(1, 0, L, static_cast<cudaStream_t>(stream));
+    return launch_das(1, 0, plan->host.n_comp > 1, L, static_cast<cudaStream_t>(stream));
 }
 
 int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream) {
@@ -748,18 +788,18 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
         groups.push_back(g);
     }
     for (int Gc : {16, 8, 4, 2, 1}) {
-        {
+        for (int comp = 0; comp < 2; ++comp) {
             LaunchGroups L{};
             L.uniform = 1;
             auto flush = [&]() -> int {
                 if (L.n_groups == 0) return SUPRA_OK;
-                const int rc = launch_das(Gc, 1, L, st);
+                const int rc = launch_das(Gc, 1, comp == 1, L, st);
                 L = LaunchGroups{};
                 L.uniform = 1;
                 return rc;
             };
             for (const Grp &gr : groups) {
-                if (group_template(gr.n) != Gc) continue;
+                if (group_template(gr.n) != Gc || (gr.p->host.n_comp > 1) != (comp == 1)) continue;
                 FrameGroup &g = L.g[L.n_groups];
                 g.plan = gr.p->dev;
                 g.line0 = L.total_lines;
@@ -823,7 +863,7 @@ int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *w
 int supra_mv(const supra_plan *plan, int32_t subaperture, float loading, const int16_t *ch, float *rf, void *stream) {
     if (!plan || !ch || !rf) return SUPRA_EINVAL;
     if (subaperture < 1 || subaperture > kMvMaxL || !(loading > 0.0f) || !std::isfinite(loading)) return SUPRA_EINVAL;
-    if (plan->max_active > kMvMaxM) return SUPRA_EINVAL;
+    if (plan->max_active > kMvMaxM || plan->host.n_comp > 1) return SUPRA_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((double)subaperture / loading <= 1e4) {
         constexpr int w = mv_warps<float>();
@@ -941,7 +981,8 @@ size_t supra_apod_workspace_size(void) {
 int supra_apod_features(const supra_plan *plan, const int16_t *ch, uint16_t *feat, uint32_t *mask, float *norm,
                         void *stream) {
     if (!plan || !ch || !feat || !mask || !norm) return SUPRA_EINVAL;
-    if (plan->host.n_el > apod::kIn || !aligned16(feat) || !aligned16(mask)) return SUPRA_EINVAL;
+    if (plan->host.n_el > apod::kIn || plan->host.n_comp > 1 || !aligned16(feat) || !aligned16(mask))
+        return SUPRA_EINVAL;
     const dim3 grid((plan->host.n_depth + 127) / 128, plan->host.n_lines);
     apod::features_kernel<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(plan->dev, ch, feat, mask, norm);
     return check_cuda(cudaGetLastError());
@@ -991,7 +1032,7 @@ int supra_apod_adam(float *params, float *m, float *v, const float *grad, int32_
 
 int supra_apod_mlp(const supra_plan *plan, const float *params, const int16_t *ch, float *rf, void *stream) {
     if (!plan || !params || !ch || !rf) return SUPRA_EINVAL;
-    if (plan->host.n_el > apod::kIn) return SUPRA_EINVAL;
+    if (plan->host.n_el > apod::kIn || plan->host.n_comp > 1) return SUPRA_EINVAL;
     apod::Args a{};
     a.params = params, a.plan = plan->dev, a.ch = ch, a.rf = rf;
     const long long tiles = (long long)plan->host.n_lines * ((plan->host.n_depth + apod::kTile - 1) / apod::kTile);

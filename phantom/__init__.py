@@ -57,6 +57,8 @@ class Setup:
     log_ref: float = 16000.0
     grid: Optional[dict] = None     # {"n": (nx, ny, nz), "origin": (3,), "spacing": (3,)}
     name: str = ""
+    tx_dir: Optional[np.ndarray] = None   # [n_tx, 3]: nonzero rows are plane-wave transmits
+    compound: int = 0                     # 1: every line averages all transmits
 
     @property
     def n_el(self) -> int:
@@ -83,7 +85,7 @@ class Setup:
             c=self.c, fs=self.fs, fc=self.fc, fnumber=self.fnumber, min_half_aperture=self.min_half_aperture,
             window=self.window, n_samples=self.n_samples, t0=self.t0, fir_taps=self.fir_taps,
             fir_cutoff=self.cutoff, dyn_range_db=self.dyn_range_db, log_ref=self.log_ref, grid=self.grid,
-            n_bands=self.n_bands, band_step=self.band_step)
+            n_bands=self.n_bands, band_step=self.band_step, tx_dir=self.tx_dir, compound=self.compound)
         return d
 
     def replace(self, **kw) -> "Setup":
@@ -318,6 +320,15 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
     zf = torch.linalg.norm(axis, dim=1).clamp_min(1e-9)
     axis = axis / zf[:, None]
     Ftx = zf / width
+    # plane-wave transmits: arrival n.(p - o_t), the whole field insonified (no focal beam)
+    if setup.tx_dir is not None:
+        ND = torch.as_tensor(np.asarray(setup.tx_dir, np.float64).reshape(-1, 3), dtype=f64, device=dev)
+        nlen = torch.linalg.norm(ND, dim=1)
+        plane = nlen > 0
+        ND = torch.where(plane[:, None], ND / nlen.clamp_min(1e-30)[:, None], ND)
+    else:
+        ND = torch.zeros_like(O)
+        plane = torch.zeros(n_tx, dtype=torch.bool, device=dev)
     gpu_lists = []   # (transmit, pair) lists for the GPU accumulation
     # transmit beam weight for every (transmit, scatterer), kept where significant
     tx_rows = max(1, (1 << 24) // max(1, P.shape[0]))
@@ -328,6 +339,7 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
         dperp2 = (rel * rel).sum(-1) - z * z
         sb = lam * Ftx[t0:t1, None] * (1 + (z - zf[t0:t1, None]).abs() / zf[t0:t1, None])
         b = torch.exp(-dperp2.clamp_min(0) / (2 * sb * sb))
+        b = torch.where(plane[t0:t1, None], torch.ones_like(b), b)
         tt, ss = torch.nonzero(b > beam_floor, as_tuple=True)
         if tt.numel() == 0:
             continue
@@ -336,7 +348,7 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
         if dev.type == "cuda":
             gpu_lists.append((tt, torch.cat([P[ss].float(), amp.float()[:, None]], dim=1)))
             continue
-        dtx = torch.linalg.norm(P[ss] - O[tt], dim=1)
+        dtx = torch.where(plane[tt], ((P[ss] - O[tt]) * ND[tt]).sum(-1), torch.linalg.norm(P[ss] - O[tt], dim=1))
         npair = tt.numel()
         pair_rows = max(1, chunk // (n_el * J))
         for p0 in range(0, npair, pair_rows):
@@ -353,7 +365,7 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
             buf.index_add_(0, idx[ok], val[ok].to(torch.float32))
 
     if dev.type == "cuda" and gpu_lists:
-        _gpu_echoes(setup, gpu_lists, sig, half, J, buf)
+        _gpu_echoes(setup, gpu_lists, sig, half, J, buf, ND.float())
 
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed) * 7919 + 17)
@@ -371,7 +383,7 @@ def synth_channels(setup: Setup, phantom: Phantom, seed: int, device="cpu", snr_
 _synth_lib = None
 
 
-def _gpu_echoes(setup, lists, sig, half, J, buf):
+def _gpu_echoes(setup, lists, sig, half, J, buf, tx_dir):
     """Accumulates the echoes of (transmit, scatterer) pairs on the GPU
     (synth_cuda.cu) into buf, float [n_tx * n_el * n_s]."""
     import ctypes
@@ -383,7 +395,7 @@ def _gpu_echoes(setup, lists, sig, half, J, buf):
         from . import build
 
         _synth_lib = ctypes.CDLL(build.build())
-        _synth_lib.phantom_echoes.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 4 + [ctypes.c_float] * 5 + \
+        _synth_lib.phantom_echoes.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 5 + [ctypes.c_float] * 5 + \
             [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     dev = buf.device
     tt = torch.cat([l[0] for l in lists])
@@ -395,9 +407,10 @@ def _gpu_echoes(setup, lists, sig, half, J, buf):
     start[1:] = torch.cumsum(counts, 0).to(torch.int32)
     elem = torch.as_tensor(setup.elem_pos, dtype=torch.float32, device=dev).contiguous()
     txo = torch.as_tensor(setup.tx_origin, dtype=torch.float32, device=dev).contiguous()
+    txd = tx_dir.to(dev).contiguous()
     rc = _synth_lib.phantom_echoes(setup.n_tx, setup.n_el, setup.n_samples, elem.data_ptr(), txo.data_ptr(),
-                                   start.data_ptr(), pairs.data_ptr(), setup.c, setup.fs, setup.fc, sig, half, J,
-                                   buf.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
+                                   txd.data_ptr(), start.data_ptr(), pairs.data_ptr(), setup.c, setup.fs, setup.fc,
+                                   sig, half, J, buf.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
     if rc != 0:
         raise RuntimeError(f"phantom_echoes failed with CUDA error {rc}")
 
@@ -487,3 +500,22 @@ def table1_setup(n_tx: int, lines_per_tx: int, seed_name: str = "") -> Setup:
     return linear_setup(64, 0.3e-3, n_lines, n_s, fc=5e6, fs=fs, c=c, focus=30e-3, fnumber=1.5,
                         lines_per_tx=lines_per_tx, grid_n=grid_n,
                         name=f"2d-linear-64ch-{n_tx}tx-{lines_per_tx}lpt-45mm-grid0.0225mm")
+
+
+
+def planewave_setup(n_el=128, pitch=0.3e-3, n_lines=128, n_samples=2048, angles_deg=(-10, -5, 0, 5, 10), fc=5e6,
+                    fs=40e6, c=1540.0, fnumber=1.5, window="hann", grid_n=None, name="planewave") -> Setup:
+    """Plane-wave imaging with coherent compounding: one plane wave per angle
+    (direction (sin a, 0, cos a)), passing the array's first element (a >= 0)
+    or last element (a < 0) at time 0 so every element fires at t >= 0; lines
+    straight down, evenly over the array; every line averages all angles."""
+    s = linear_setup(n_el, pitch, n_lines, n_samples, fc=fc, fs=fs, c=c, fnumber=fnumber, window=window,
+                     grid_n=grid_n, name=name)
+    th = np.deg2rad(np.asarray(angles_deg, np.float64))
+    x0, x1 = s.elem_pos[0, 0], s.elem_pos[-1, 0]
+    s.tx_origin = np.stack([np.where(th >= 0, x0, x1), np.zeros_like(th), np.zeros_like(th)], 1)
+    s.tx_dir = np.stack([np.sin(th), np.zeros_like(th), np.cos(th)], 1)
+    s.tx_focus = s.tx_origin + 30e-3 * s.tx_dir   # unused for plane waves
+    s.line_tx = np.zeros(n_lines, np.int32)
+    s.compound = 1
+    return s

@@ -6,7 +6,7 @@
 // For transmit t and element e the noise-free record is
 //   sum over (scatterer p, transmit t) pairs of
 //     a_p * exp(-(k/fs - T)^2 / (2 s^2)) * cos(2 pi fc (k/fs - T)),  |k/fs - T| <= half,
-//   T = (|p - o_t| + |p - x_e|) / c,
+//   T = (|p - o_t| + |p - x_e|) / c  (a plane-wave transmit of direction n: n.(p - o_t) + |p - x_e|),
 // with a_p already including the transmit-beam weight.  One CTA accumulates 8
 // elements of one transmit in shared memory.
 #include <cuda_runtime.h>
@@ -17,7 +17,8 @@ namespace {
 constexpr int kElems = 8;
 
 __global__ void __launch_bounds__(256) echo_kernel(int n_el, int n_s, const float *__restrict__ elem,
-                                                   const float *__restrict__ tx_origin, const int *__restrict__ start,
+                                                   const float *__restrict__ tx_origin,
+                                                   const float *__restrict__ tx_dir, const int *__restrict__ start,
                                                    const float4 *__restrict__ pairs, float c, float fs, float fc,
                                                    float sig, float half, int J, float *__restrict__ out) {
     extern __shared__ float acc[];   // [kElems][n_s]
@@ -25,11 +26,15 @@ __global__ void __launch_bounds__(256) echo_kernel(int n_el, int n_s, const floa
     for (int k = threadIdx.x; k < kElems * n_s; k += blockDim.x) acc[k] = 0.0f;
     __syncthreads();
     const float ox = tx_origin[3 * t], oy = tx_origin[3 * t + 1], oz = tx_origin[3 * t + 2];
+    // plane-wave transmit (unit direction, zero for a spherical wave from the origin)
+    const float nx = tx_dir[3 * t], ny = tx_dir[3 * t + 1], nz = tx_dir[3 * t + 2];
+    const bool plane = nx != 0.0f || ny != 0.0f || nz != 0.0f;
     const float inv2s2 = 1.0f / (2.0f * sig * sig), w = 6.283185307179586f * fc;
     const int p0 = start[t], p1 = start[t + 1];
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const float4 q = pairs[p];
-        const float dtx = sqrtf((q.x - ox) * (q.x - ox) + (q.y - oy) * (q.y - oy) + (q.z - oz) * (q.z - oz));
+        const float dtx = plane ? nx * (q.x - ox) + ny * (q.y - oy) + nz * (q.z - oz)
+                                : sqrtf((q.x - ox) * (q.x - ox) + (q.y - oy) * (q.y - oy) + (q.z - oz) * (q.z - oz));
         for (int j = 0; j < kElems && e0 + j < n_el; ++j) {
             const float *x = elem + 3 * (e0 + j);
             const float drx = sqrtf((q.x - x[0]) * (q.x - x[0]) + (q.y - x[1]) * (q.y - x[1]) + (q.z - x[2]) * (q.z - x[2]));
@@ -57,7 +62,8 @@ __global__ void __launch_bounds__(256) echo_kernel(int n_el, int n_s, const floa
 // pairs: float4 (x, y, z, amplitude) grouped by transmit, start[t]..start[t+1].
 // Returns 0 or a CUDA error code.
 extern "C" __attribute__((visibility("default"))) int phantom_echoes(int n_tx, int n_el, int n_s, const float *elem,
-                                                                     const float *tx_origin, const int *start,
+                                                                     const float *tx_origin, const float *tx_dir,
+                                                                     const int *start,
                                                                      const float *pairs, float c, float fs, float fc,
                                                                      float sig, float half, int J, float *out,
                                                                      void *stream) {
@@ -66,6 +72,6 @@ extern "C" __attribute__((visibility("default"))) int phantom_echoes(int n_tx, i
     cudaFuncSetAttribute(echo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(n_tx, (n_el + kElems - 1) / kElems);
     echo_kernel<<<grid, 256, smem, static_cast<cudaStream_t>(stream)>>>(
-        n_el, n_s, elem, tx_origin, start, reinterpret_cast<const float4 *>(pairs), c, fs, fc, sig, half, J, out);
+        n_el, n_s, elem, tx_origin, tx_dir, start, reinterpret_cast<const float4 *>(pairs), c, fs, fc, sig, half, J, out);
     return (int)cudaGetLastError();
 }

@@ -361,3 +361,44 @@ def test_compounded_chain_and_mixed_batch_match():
     np.testing.assert_array_equal(outs[2].cpu().numpy(), img)
     np.testing.assert_array_equal(outs[1].cpu().numpy(), plan1.bmode(ch1).cpu().numpy())
     assert supra.device_status() == 0
+
+
+def test_plane_wave_compounding_matches_oracle():
+    # five plane waves at -8..8 degrees, every line averages all of them (coherent compounding)
+    s = phantom.planewave_setup(32, 0.3e-3, 24, 700, angles_deg=(-8, -4, 0, 4, 8), fc=5e6, fs=40e6,
+                                grid_n=(96, 160))
+    p = s.params()
+    ch = phantom.synth_channels(s, phantom.make_phantom(s, 31, 1500, n_points=3), 31)
+    plan = supra.Plan(**p)
+    rf = plan.beamform(ch.cuda()).cpu().numpy()
+    ref = oracle.das(p, ch.numpy())
+    assert max_norm_err(rf, ref) <= RF_TOL
+    img = plan.bmode(ch.cuda()).cpu().numpy()
+    assert_gray(img, oracle.bmode(p, ch.numpy()), what="plane-wave compounding")
+    # in a batch with a plan that does not compound: each frame as alone
+    s1 = small_linear(24, 10, 500, grid_n=(64, 96))
+    plan1 = supra.Plan(**s1.params())
+    ch1 = phantom.random_channels(s1, 32).cuda()
+    outs = supra.bmode_batched([plan1, plan, plan, plan1], [ch1, ch.cuda(), ch.cuda(), ch1])
+    np.testing.assert_array_equal(outs[1].cpu().numpy(), img)
+    np.testing.assert_array_equal(outs[2].cpu().numpy(), img)
+    np.testing.assert_array_equal(outs[0].cpu().numpy(), plan1.bmode(ch1).cpu().numpy())
+    with pytest.raises(supra.SupraError):   # MV is defined per transmit, not on compounded lines
+        plan.mv(ch.cuda(), 8)
+    assert supra.device_status() == 0
+
+
+def test_single_steered_plane_wave_lines_match_oracle():
+    # one 6-degree plane wave, every line formed from it (no compounding): DAS and MV
+    s = phantom.planewave_setup(32, 0.3e-3, 16, 600, angles_deg=(6,), fc=5e6, fs=40e6)
+    s.compound = 0
+    p = s.params()
+    ch = phantom.random_channels(s, 33)
+    plan = supra.Plan(**p)
+    rf = plan.beamform(ch.cuda()).cpu().numpy()
+    assert max_norm_err(rf, oracle.das(p, ch.numpy())) <= RF_TOL
+    mv = plan.mv(ch.cuda(), 8).cpu().numpy()
+    lines, depths = list(range(16)), list(range(0, 600, 13))
+    ref = oracle.mv(p, ch.numpy(), 8, lines=lines, depths=depths)
+    keep = np.array([[np.min(np.abs(oracle.aperture(p, l, i)[2])) > 1e-9 for i in depths] for l in lines])
+    assert np.max(np.abs(mv[np.ix_(lines, depths)] - ref)[keep]) <= 1e-3 * np.max(np.abs(ref))
