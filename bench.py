@@ -300,6 +300,47 @@ def bench_table1(args, dev, stream):
     return out
 
 
+def bench_planewave(args, dev, stream):
+    """Plane-wave imaging with coherent compounding: 11 plane waves at -10..10
+    degrees per frame, 128 elements, 256 lines, 2048 samples, 512 x 512 output;
+    64 frames per fused batched call (370 MB of records, larger than L2)."""
+    import numpy as np
+    import torch
+
+    import paper_1711_06127_b300 as supra
+    import phantom
+
+    st = phantom.planewave_setup(128, 0.3e-3, 256, 2048, angles_deg=tuple(np.linspace(-10, 10, 11)), fc=7e6,
+                                 fs=40e6, grid_n=(512, 512), name="planewave-128el-11angles-256lines-2048s-sc512")
+    plan = supra.Plan(**st.params())
+    nb = 64
+    batch = torch.empty((nb, *plan.ch_shape), dtype=torch.int16, device=dev)
+    for k in range(nb):
+        batch[k].copy_(phantom.synth_channels(st, phantom.make_phantom(st, 8000 + k, 4000, n_points=3), 8000 + k,
+                                              device=dev))
+    chs = list(batch)
+    outs = [torch.empty(plan.out_shape, dtype=torch.uint8, device=dev) for _ in range(nb)]
+    ws = torch.empty(max(1, supra.workspace_size([plan] * nb)), dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        supra.bmode_batched([plan] * nb, chs, outs, ws, stream)
+    reps = 10
+    ev[0].record(stream)
+    for _ in range(reps):
+        supra.bmode_batched([plan] * nb, chs, outs, ws, stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    info = plan.info
+    alg = nb * (info["aperture_bytes"] + info["image_bytes"])
+    return {"workload": st.name, "angles": st.n_tx, "frames_per_call": nb, "ms_per_call": ms,
+            "frames_per_s": nb / (ms * 1e-3),
+            "samples_channels_per_s": nb * info["n_tx"] * info["n_el"] * info["n_samples"] / (ms * 1e-3),
+            "aperture_gb_per_s": alg / (ms * 1e-3) / 1e9,
+            "note": "each line reads its aperture from all 11 transmits' records (L2-resident per frame); "
+                    "aperture bytes count every (transmit, element, depth) sample"}
+
+
 def bench_compounding(args, dev, stream, s, ch):
     """Frequency compounding (a bank of 3 IQ demodulators at fc, fc +- fc/4)
     on one frame of the main workload: the envelope node with 1 and 3 bands,
@@ -397,7 +438,14 @@ def bench_apod(args, dev, stream):
 
     kinds = ("das", "mv", "apod")
     lat = {k: [] for k in kinds}
-    q = {k: {"psnr_vs_mv": [], "contrast_db": [], "cnr": []} for k in kinds}
+    q = {k: {"psnr_vs_mv": [], "contrast_db": [], "cnr": [], "fwhm_lat_mm": [], "fwhm_ax_mm": []} for k in kinds}
+    # the three point targets of each frame: on the central axis at 0.25, 0.575, 0.9 of the imaged depth
+    import numpy as np
+
+    xs = np.asarray(p["line_origin"])[:, 0]
+    zmax = p["depth0"] + (p["n_depth"] - 1) * p["depth_step"]
+    targets = [(int(np.argmin(np.abs(xs))), int(round((f * zmax - p["depth0"]) / p["depth_step"])))
+               for f in np.linspace(0.25, 0.9, 3)]
     out = torch.empty(plan.line_shape, dtype=torch.uint8, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for f in range(n_eval):
@@ -421,6 +469,10 @@ def bench_apod(args, dev, stream):
                 st = quality.cyst_stats(p, envs[k], bms[k], cy, float(p.get("dyn_range_db", 60.0)))
                 q[k]["contrast_db"].append(st["contrast_db"])
                 q[k]["cnr"].append(st["cnr"])
+            for tl, ti in targets:
+                w = quality.point_fwhm(p, envs[k], tl, ti)
+                q[k]["fwhm_lat_mm"].append(1e3 * w["lateral_m"])
+                q[k]["fwhm_ax_mm"].append(1e3 * w["axial_m"])
     res = {"workload": s.name + "-mv-labels", "subaperture": L, "loading": 0.01,
            "train": {"frames": n_train, "pixels": P * n_train, "epochs": args.apod_epochs,
                      "minibatch_pixels": P * n_train // n_batches, "lr": args.apod_lr, "loss_first_epoch": losses[0],
@@ -435,9 +487,12 @@ def bench_apod(args, dev, stream):
         res[name] = {"frames_per_s": 1e3 / mean_ms, "latency_ms": {"p50": p50, "p99": p99},
                      "psnr_vs_mv_db": (sum(psnr) / len(psnr)) if psnr else None,
                      "cyst_contrast_db": sum(q[k]["contrast_db"]) / len(q[k]["contrast_db"]),
-                     "cyst_cnr": sum(q[k]["cnr"]) / len(q[k]["cnr"])}
+                     "cyst_cnr": sum(q[k]["cnr"]) / len(q[k]["cnr"]),
+                     "point_fwhm_mm": {"lateral": float(np.median(q[k]["fwhm_lat_mm"])),
+                                       "axial": float(np.median(q[k]["fwhm_ax_mm"]))}}
     res["note"] = ("single-frame launches, B-mode lines out (beamformer + envelope + log compression); "
-                   "PSNR of 8-bit B-mode lines against MV's; cysts of each held-out frame")
+                   "PSNR of 8-bit B-mode lines against MV's; cysts of each held-out frame; -6 dB widths of the "
+                   "three axial point targets (median over frames and targets)")
     return res, tr.params
 
 
@@ -712,6 +767,7 @@ def run_ours(args):
     # ---- the run-time table's 2D shapes (multi-line); learned apodization beside MV and DAS; the request loop
     table1 = bench_table1(args, dev, stream) if rank == 0 and not args.skip_table1 else None
     compounding = bench_compounding(args, dev, stream, s, chs[0]) if rank == 0 and not args.skip_table1 else None
+    planewave = bench_planewave(args, dev, stream) if rank == 0 and not args.skip_table1 else None
     apod_res = serve_res = None
     if rank == 0 and not args.skip_apod:
         apod_res, trained = bench_apod(args, dev, stream)
@@ -749,6 +805,7 @@ def run_ours(args):
             "volume_3d": vol3d,
             "table1_2d": table1,
             "envelope_compounding": compounding,
+            "planewave_compounding": planewave,
             "learned_apodization": apod_res,
             "serving": serve_res,
             "gpu_launches": 2 * args.steps,

@@ -322,6 +322,47 @@ __device__ __forceinline__ void element_window(const ProdConst &C, const LineGeo
     m.flags = 1 | (widx << 1) | (ci << 4);
 }
 
+// The same for the line's own spherical transmit (the kernel without extended
+// transmit models; kept separate so that kernel compiles to the spherical-only code).
+__device__ __forceinline__ void element_window_line(const ProdConst &C, const LineGeo &lg, int tile, int ia, int ib,
+                                               float4 xe, ElemMeta &m) {
+    const float mx = lg.ox - xe.x, my = lg.oy - xe.y, mz = lg.oz - xe.z;
+    const float beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
+    const float gamma = mx * mx + my * my + mz * mz;
+    const int i0 = tile * kTD;   // the tile's delay base is at its first depth
+    const float r0 = C.depth0 + (float)ia * C.depth_step;
+    const float r1 = C.depth0 + (float)ib * C.depth_step;
+    const int kt = __ldg(&C.tile_k[tile]);
+    const float ft = __ldg(&C.tile_f[tile]);
+    const float s0 = ft + C.a1 * (float)(ia - i0) + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * C.fsc;
+    const float s1 = ft + C.a1 * (float)(ib - i0) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * C.fsc;
+    float lo = fminf(s0, s1), hi = fmaxf(s0, s1);
+    // The two-way path is convex in r: its maximum is at an end, its minimum may be
+    // inside; bound that minimum by the sum of the two paths' minima.
+    if ((-beta > r0 && -beta < r1) || (-lg.bt > r0 && -lg.bt < r1)) {
+        const float re = fminf(fmaxf(-beta, r0), r1), rt = fminf(fmaxf(-lg.bt, r0), r1);
+        const float de = sqrtf(fmaxf(fmaf(re, re + 2.0f * beta, gamma), 0.0f));
+        const float dtp = sqrtf(fmaxf(fmaf(rt, rt + 2.0f * lg.bt, lg.gt), 0.0f));
+        lo = fminf(lo, (de + dtp) * C.fsc - C.t0fs - (float)kt);
+    }
+    const int lo_i = kt + (int)floorf(lo) - 1;
+    const int ws = (lo_i >> 3) << 3;                              // 16-byte aligned window start
+    const int need = kt + (int)floorf(hi) + 2 - ws;               // samples up to x1 of the last depth
+    int widx = need <= width_of(0) ? 0 : (need - width_of(0) + 63) / 64;   // smallest width >= need
+    if (widx >= kNumWidths) {
+        set_status(SUPRA_EINTERNAL);
+        widx = kNumWidths - 1;
+    }
+    m.beta2 = beta + beta;
+    m.gamma = gamma;
+    m.ex = xe.x;
+    m.ey = xe.y;
+    m.ws = ws;
+    m.ia = ia;
+    m.ib = ib;
+    m.flags = 1 | (widx << 1);
+}
+
 // Stages the element's window of all frames into slot `slot` of a stage (frame
 // rows of width_of(widx) samples, packed).  Returns the bytes that will land.
 template <int G>
@@ -595,7 +636,7 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // -------------------------------------------------------------------------------------------------
 // MODE 0: write RF (float [n_lines][n_depth] per frame).
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
-template <int G, int MODE, bool COMP>
+template <int G, int MODE, bool EXT>
 __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_constant__ LaunchGroups L) {
     constexpr int E = kRows / G;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -668,7 +709,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
         // aperture, that transmit's records and delays), as consecutive (tile, transmit)
         // passes; stages never mix transmits and only the tile's final pass marks its
         // last stage.  Without compounding there is one pass per tile.
-        const int n_comp = COMP ? P->n_comp : 1;   // compile-time 1 for plans that do not compound
+        const int n_comp = EXT ? P->n_comp : 1;   // compile-time 1 for plans with a plain transmit model
         for (int vt = 0; vt < NT * n_comp && ok; ++vt) {
             const int tile = vt / n_comp, ci = vt - tile * n_comp;
             const bool final_ci = ci == n_comp - 1;
@@ -689,14 +730,21 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 int e, ia, ib;
                 float4 xe;
                 const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
-                TxTerm tt;
-                if constexpr (COMP) {
-                    tt = P->txterms[line * n_comp + ci];
-                } else {
-                    tt.b = lg.bt, tt.g = lg.gt, tt.tx = lg.tx, tt.plane = lg.plane;
-                }
                 ElemMeta m;
-                if (a) element_window(C, lg, tt, ci, tile, ia, ib, xe, m);
+                int tx;
+                if constexpr (EXT) {
+                    TxTerm tt;
+                    if (n_comp > 1) {
+                        tt = P->txterms[line * n_comp + ci];
+                    } else {
+                        tt.b = lg.bt, tt.g = lg.gt, tt.tx = lg.tx, tt.plane = lg.plane;
+                    }
+                    tx = tt.tx;
+                    if (a) element_window(C, lg, tt, ci, tile, ia, ib, xe, m);
+                } else {
+                    tx = lg.tx;
+                    if (a) element_window_line(C, lg, tile, ia, ib, xe, m);
+                }
                 uint32_t mask = __ballot_sync(0xffffffffu, a);
                 while (mask) {
                     if (slot == 0 && !acquire()) {
@@ -710,7 +758,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                         const int sb = n % kStages;
                         ElemMeta *meta = metas + sb * kRows;
                         meta[slot + rank] = m;
-                        bytes += stage_element<G>(C, fg, nf, tt.tx, e, m,
+                        bytes += stage_element<G>(C, fg, nf, tx, e, m,
                                                   stages + sb * stage_elems + (slot + rank) * G * kSlotSamples,
                                                   &full[sb]);
                     }
@@ -763,7 +811,8 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
             const float qx = fminf(fmaxf(px, P->xmin), P->xmax);
             const float qy = fminf(fmaxf(py, P->ymin), P->ymax);
             const float inv_a = 1.0f / fmaxf(pz * P->inv2f, P->amin);
-            float base = P->tile_f[tile] + P->a1 * (float)m + tx_excess(r, lg.bt, lg.gt, lg.plane) * fsc;
+            float base = P->tile_f[tile] + P->a1 * (float)m +
+                         (EXT ? tx_excess(r, lg.bt, lg.gt, lg.plane) : path_excess(r, lg.bt, lg.gt)) * fsc;
             int cur = 0;   // compounding: transmit whose delay term `base` holds
             const int kt = P->tile_k[tile];
             for (;;) {
@@ -779,7 +828,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 if (aborted) break;
                 const ElemMeta *meta = metas + sb * kRows;
                 const int last = meta_last(meta[0]);
-                if constexpr (COMP) {
+                if constexpr (EXT) {
                     const int ci = meta_comp(meta[0]);
                     if (ci != cur) {
                         const int nc = P->n_comp;

@@ -27,6 +27,7 @@ struct supra_plan {
     int device = 0;
     int max_active = 0;     // upper bound on the elements inside one pixel's aperture
     std::atomic<int> max_group{kMaxGroup};   // frames per DAS tile (autotuned)
+    bool ext = false;   // extended transmit model (a plane-wave line or compounding): its own kernels
 };
 
 namespace {
@@ -155,38 +156,45 @@ bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, 
 // kernel choice for a frame group size
 int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
 
-template <int G, int MODE, bool COMP>
+template <int G, int MODE, bool EXT>
 int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int max_optin = 0;
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // the shared-memory opt-in is set once per device (it outlives the call)
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> ready[kMaxDev];
     const SmemLayout lay(G, MODE, kSlotSamples);
-    if (lay.total > max_optin) return SUPRA_EINVAL;
-    auto kern = das_kernel<G, MODE, COMP>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess)
-        return SUPRA_ECUDA;
+    auto kern = das_kernel<G, MODE, EXT>;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SUPRA_ECUDA;
+    if (dev >= kMaxDev || ready[dev].load(std::memory_order_acquire) == 0) {
+        int max_optin = 0;
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (lay.total > max_optin) return SUPRA_EINVAL;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess)
+            return SUPRA_ECUDA;
+        if (dev < kMaxDev) ready[dev].store(1, std::memory_order_release);
+    }
     kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L);
     return check_cuda(cudaGetLastError());
 }
 
-template <bool COMP>
+template <bool EXT>
 int launch_das_c(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
-    if (G == 1) return mode == 0 ? launch_das_t<1, 0, COMP>(L, st) : launch_das_t<1, 1, COMP>(L, st);
+    if (G == 1) return mode == 0 ? launch_das_t<1, 0, EXT>(L, st) : launch_das_t<1, 1, EXT>(L, st);
     if (mode == 0) return SUPRA_EINVAL;
     switch (G) {
-        case 2: return launch_das_t<2, 1, COMP>(L, st);
-        case 4: return launch_das_t<4, 1, COMP>(L, st);
-        case 8: return launch_das_t<8, 1, COMP>(L, st);
-        default: return launch_das_t<16, 1, COMP>(L, st);
+        case 2: return launch_das_t<2, 1, EXT>(L, st);
+        case 4: return launch_das_t<4, 1, EXT>(L, st);
+        case 8: return launch_das_t<8, 1, EXT>(L, st);
+        default: return launch_das_t<16, 1, EXT>(L, st);
     }
 }
 
-// comp: the groups' plans compound several transmits per line (a separate kernel
-// instantiation, so plans that do not compound run the kernel without that code)
-int launch_das(int G, int mode, bool comp, const LaunchGroups &L, cudaStream_t st) {
+// ext: the groups' plans use an extended transmit model (plane waves and/or
+// compounding several transmits per line).  They run their own kernel
+// instantiation, so plans with spherical single transmits keep the plain code.
+int launch_das(int G, int mode, bool ext, const LaunchGroups &L, cudaStream_t st) {
     if (L.total_lines == 0) return SUPRA_OK;
-    return comp ? launch_das_c<true>(G, mode, L, st) : launch_das_c<false>(G, mode, L, st);
+    return ext ? launch_das_c<true>(G, mode, L, st) : launch_das_c<false>(G, mode, L, st);
 }
 
 // Frames of one scan-conversion launch and their host-side plan records (grid sizing).
@@ -633,6 +641,8 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     H.txterms = reinterpret_cast<const TxTerm *>(b + o_txt);
     plan->dev = reinterpret_cast<DevPlan *>(b + o_plan);
     plan->host = H;
+    plan->ext = n_comp > 1;
+    for (int l = 0; l < n_lines && !plan->ext; ++l) plan->ext = lines[l].plane != 0;
     cudaError_t err = cudaSuccess;
     err = err ? err : cudaMemcpy(b + o_plan, &H, sizeof(DevPlan), cudaMemcpyHostToDevice);
     err = err ? err : cudaMemcpy(b + o_elem, elem.data(), sizeof(float4) * n_el, cudaMemcpyHostToDevice);
@@ -692,7 +702,7 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
     L.uniform = 1;
-    return launch_das(1, 0, plan->host.n_comp > 1, L, static_cast<cudaStream_t>(stream));
+    return launch_das(1, 0, plan->ext, L, static_cast<cudaStream_t>(stream));
 }
 
 int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream) {
@@ -787,8 +797,12 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
         }
         groups.push_back(g);
     }
+    bool present[5][2] = {};   // (group-size class, compounding) pairs that have groups
+    auto class_of = [](int Gc) { return Gc == 16 ? 0 : Gc == 8 ? 1 : Gc == 4 ? 2 : Gc == 2 ? 3 : 4; };
+    for (const Grp &gr : groups) present[class_of(group_template(gr.n))][gr.p->ext ? 1 : 0] = true;
     for (int Gc : {16, 8, 4, 2, 1}) {
         for (int comp = 0; comp < 2; ++comp) {
+            if (!present[class_of(Gc)][comp]) continue;
             LaunchGroups L{};
             L.uniform = 1;
             auto flush = [&]() -> int {
@@ -799,7 +813,7 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
                 return rc;
             };
             for (const Grp &gr : groups) {
-                if (group_template(gr.n) != Gc || (gr.p->host.n_comp > 1) != (comp == 1)) continue;
+                if (group_template(gr.n) != Gc || gr.p->ext != (comp == 1)) continue;
                 FrameGroup &g = L.g[L.n_groups];
                 g.plan = gr.p->dev;
                 g.line0 = L.total_lines;
