@@ -117,25 +117,25 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo
 }
 
 template <int MODE>
-__device__ __forceinline__ void stage_weights(const float *__restrict__ prm, unsigned char *sm, int t) {
+__device__ __forceinline__ void stage_weights(const float *__restrict__ prm, unsigned char *sm, int t, int nt) {
     using S = Smem<MODE>;
-    for (int k = t; k < kH1 * kIn; k += kTile) {
+    for (int k = t; k < kH1 * kIn; k += nt) {
         const int n = k >> 7, i = k & 127;
         *reinterpret_cast<__nv_bfloat16 *>(sm + S::W1 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
             __float2bfloat16_rn(prm[kOffW1 + k]);
     }
-    for (int k = t; k < kH2 * kH1; k += kTile) {
+    for (int k = t; k < kH2 * kH1; k += nt) {
         const int n = k >> 6, i = k & 63;
         *reinterpret_cast<__nv_bfloat16 *>(sm + S::W2 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
             __float2bfloat16_rn(prm[kOffW2 + k]);
     }
-    for (int k = t; k < kIn * kH2; k += kTile) {
+    for (int k = t; k < kIn * kH2; k += nt) {
         const int n = k >> 6, i = k & 63;
         *reinterpret_cast<__nv_bfloat16 *>(sm + S::W3 + (i >> 3) * 2048 + n * 16 + (i & 7) * 2) =
             __float2bfloat16_rn(prm[kOffW3 + k]);
     }
     float *bias = reinterpret_cast<float *>(sm + S::BIAS);
-    for (int k = t; k < 256; k += kTile)
+    for (int k = t; k < 256; k += nt)
         bias[k] = k < 64 ? prm[kOffB1 + k] : k < 128 ? prm[kOffB2 + k - 64] : prm[kOffB3 + k - 128];
 }
 
@@ -147,38 +147,50 @@ __device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t &phase) {
     return ok;
 }
 
+// Threads per CTA: training splits every pixel row over two warpgroups (warps w
+// and w + 4 share TMEM lanes 32 (w % 4).., each takes half of every row's
+// columns), so two warps per scheduler hide each other's TMEM, shared-memory
+// and MMA waits; the two-CTA-per-SM modes keep one warpgroup.
 template <int MODE>
-__global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(const Args a) {
+__host__ __device__ constexpr int apod_threads() { return MODE == kTrain ? 256 : 128; }
+
+template <int MODE>
+__global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) apod_kernel(const Args a) {
     using S = Smem<MODE>;
+    constexpr int NT = apod_threads<MODE>(), H = NT / kTile;   // H halves per row
     constexpr uint32_t kCols = MODE == kTrain ? 512 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
-    __shared__ float red[2][4];
+    __shared__ float red[2][NT / 32];
+    __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
     const int t = threadIdx.x, warp = t >> 5;
+    const int row = t & (kTile - 1), half = t / kTile;
     if (t == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
-    stage_weights<MODE>(a.params, sm, t);
-    if (MODE == kTrain) {
+    stage_weights<MODE>(a.params, sm, t, NT);
+    if (MODE == kTrain && half == 0) {
         const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
-        chunk(sm, S::X, 16, t) = ones;
-        chunk(sm, S::X, 17, t) = ones;
-        chunk(sm, S::H1, 8, t) = ones;
-        chunk(sm, S::H1, 9, t) = ones;
-        chunk(sm, S::H2, 8, t) = ones;
-        chunk(sm, S::H2, 9, t) = ones;
+        chunk(sm, S::X, 16, row) = ones;
+        chunk(sm, S::X, 17, row) = ones;
+        chunk(sm, S::H1, 8, row) = ones;
+        chunk(sm, S::H1, 9, row) = ones;
+        chunk(sm, S::H2, 8, row) = ones;
+        chunk(sm, S::H2, 9, row) = ones;
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tm = tmem_base, lane = (uint32_t)(32 * warp) << 16;
+    const uint32_t tm = tmem_base, lane = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t sb = tc::smem_u32(sm);
     const float *b1 = reinterpret_cast<const float *>(sm + S::BIAS), *b2 = b1 + 64, *b3 = b1 + 128;
     constexpr uint32_t kI64 = tc::idesc_bf16(128, 64, false, false), kI128 = tc::idesc_bf16(128, 128, false, false);
+    // this thread's column blocks of 32: 64-wide layers q in [q2, q2 + 2/H), the 128 outputs q in [q4, q4 + 4/H)
+    const int q2 = half * (2 / H), q4 = half * (4 / H);
 
     long long n_tiles;
     int nblk = 1, nd = 0;
@@ -194,7 +206,7 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
     float loss_acc = 0.0f, cnt_acc = 0.0f;
 
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // ---- inputs: one row of X per thread
+        // ---- inputs: one row of X per pixel (each half writes its chunks)
         uint32_t mk[4] = {0u, 0u, 0u, 0u};
         float nrm = 0.0f, tgt = 0.0f;
         bool row_ok;
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
         int line = 0, i = 0;
         if (MODE == kInfer) {
             line = (int)(tile / nblk);
-            i = (int)(tile % nblk) * kTile + t;
+            i = (int)(tile % nblk) * kTile + row;
             row_ok = i < nd;
             float n2v[2] = {0.0f, 0.0f};
             const int n_el = a.plan->n_el;
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
 #pragma unroll 1
             for (int c = 0; c < 16; ++c) {
                 if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
-                    chunk(sm, S::X, c, t) = make_uint4(0u, 0u, 0u, 0u);
+                    chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
                     continue;
                 }
                 float v[8];
@@ -225,24 +237,25 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
                     n2v[j & 1] = fmaf(v[j], v[j], n2v[j & 1]);
                     if (act) mk[e >> 5] |= 1u << (e & 31);
                 }
-                chunk(sm, S::X, c, t) = pack8(v);
+                chunk(sm, S::X, c, row) = pack8(v);
             }
             nrm = sqrtf(n2v[0] + n2v[1]);
         } else {
-            p = tile * kTile + t;
+            p = tile * kTile + row;
             row_ok = p < a.n;
-            const long long row = p * a.stride;
+            const long long rw = p * a.stride;
             if (row_ok) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + row * kIn);
+                const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + rw * kIn);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) chunk(sm, S::X, c, t) = __ldg(src + c);
-                const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + row);
+                for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) chunk(sm, S::X, c, row) = __ldg(src + c);
+                const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + rw);
                 mk[0] = m4.x, mk[1] = m4.y, mk[2] = m4.z, mk[3] = m4.w;
-                nrm = __ldg(a.norm + row);
-                if (MODE == kTrain) tgt = nrm > 0.0f ? __ldg(a.label + row) / nrm : 0.0f;
+                nrm = __ldg(a.norm + rw);
+                if (MODE == kTrain) tgt = nrm > 0.0f ? __ldg(a.label + rw) / nrm : 0.0f;
             } else {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) chunk(sm, S::X, c, t) = make_uint4(0u, 0u, 0u, 0u);
+                for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c)
+                    chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
             }
         }
         const bool valid = row_ok && nrm > 0.0f;
@@ -260,13 +273,13 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
         ok = mma_wait(&bar, phase) && ok;
         const float scale = (MODE == kInfer) ? (nrm > 0.0f ? 1.0f / nrm : 0.0f) : 1.0f;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = q2; q < q2 + 2 / H; ++q) {
             float v[32];
             tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = fmaxf(fmaf(v[j], scale, b1[32 * q + j]), 0.0f);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::H1, 4 * q + c, t) = pack8(v + 8 * c);
+            for (int c = 0; c < 4; ++c) chunk(sm, S::H1, 4 * q + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -281,13 +294,13 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = q2; q < q2 + 2 / H; ++q) {
             float v[32];
             tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + b2[32 * q + j], 0.0f);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::H2, 4 * q + c, t) = pack8(v + 8 * c);
+            for (int c = 0; c < 4; ++c) chunk(sm, S::H2, 4 * q + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -301,24 +314,29 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
             tc::mma_commit(&bar);
         }
         ok = mma_wait(&bar, phase) && ok;
-        // reductions over the 128 outputs in 4 independent partials (latency, not order, matters)
+        // reductions over this thread's outputs in 4 independent partials (latency, not order, matters)
         float zm4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = q4; q < q4 + 4 / H; ++q) {
             float v[32];
             tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j)
                 if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], v[j] + b3[32 * q + j]);
         }
-        const float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
+        float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
+        if constexpr (H > 1) {   // the row's maximum over both halves
+            xrow[0][half][row] = zmax;
+            __syncthreads();
+            zmax = fmaxf(xrow[0][0][row], xrow[0][1][row]);
+        }
         float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = q4; q < q4 + 4 / H; ++q) {
             float v[32], x[32];
             tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, t), x + 8 * c);
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, row), x + 8 * c);
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
@@ -326,31 +344,40 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
                 sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
             }
         }
-        const float se = (se4[0] + se4[1]) + (se4[2] + se4[3]);
-        const float sx = (sx4[0] + sx4[1]) + (sx4[2] + sx4[3]);
+        float se = (se4[0] + se4[1]) + (se4[2] + se4[3]);
+        float sx = (sx4[0] + sx4[1]) + (sx4[2] + sx4[3]);
+        if constexpr (H > 1) {   // the row's sums over both halves
+            xrow[1][half][row] = se;
+            xrow[2][half][row] = sx;
+            __syncthreads();
+            se = xrow[1][0][row] + xrow[1][1][row];
+            sx = xrow[2][0][row] + xrow[2][1][row];
+        }
         const float yh = se > 0.0f ? sx / se : 0.0f;
         if (MODE == kForward) {
-            if (row_ok) a.y[p * a.stride] = yh * nrm;
+            if (row_ok && half == 0) a.y[p * a.stride] = yh * nrm;
         } else if (MODE == kInfer) {
-            if (row_ok) a.rf[(long long)line * nd + i] = yh;
+            if (row_ok && half == 0) a.rf[(long long)line * nd + i] = yh;
         } else {
             const float r = valid ? yh - tgt : 0.0f;
-            loss_acc = fmaf(r, r, loss_acc);
-            cnt_acc += valid ? 1.0f : 0.0f;
+            if (half == 0) {
+                loss_acc = fmaf(r, r, loss_acc);
+                cnt_acc += valid ? 1.0f : 0.0f;
+            }
             const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = q4; q < q4 + 4 / H; ++q) {
                 float v[32], x[32];
                 tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, t), x + 8 * c);
+                for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, row), x + 8 * c);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float pe = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
                     v[j] = pe * (x[j] - yh) * g;
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, t) = pack8(v + 8 * c);
+                for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = pack8(v + 8 * c);
             }
         }
         tc::fence_async_smem();
@@ -370,15 +397,15 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = q2; q < q2 + 2 / H; ++q) {
             float v[32], h[32];
             tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H2, 4 * q + c, t), h + 8 * c);
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H2, 4 * q + c, row), h + 8 * c);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ2, 4 * q + c, t) = pack8(v + 8 * c);
+            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ2, 4 * q + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -396,15 +423,15 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = q2; q < q2 + 2 / H; ++q) {
             float v[32], h[32];
             tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H1, 4 * q + c, t), h + 8 * c);
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H1, 4 * q + c, row), h + 8 * c);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ1, 4 * q + c, t) = pack8(v + 8 * c);
+            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ1, 4 * q + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -426,37 +453,40 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
 
     if (MODE == kTrain) {
         float *part = a.partial + (long long)blockIdx.x * kPartStride;
-        // weight and bias gradients (unnormalised sums over this CTA's pixels)
+        // weight and bias gradients (unnormalised sums over this CTA's pixels); lane = row,
+        // each half takes half of every accumulator's weight columns
         float v[32], w[16];
+        const bool low = (warp & 3) < 2;   // rows 0..63: the 64-row accumulators dW2, dW1
         if (ok && !first) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = q2; q < q2 + 2 / H; ++q) {
                 tc::tmem_ld32(tm + lane + kDW3 + 32 * q, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) part[kOffW3 + t * 64 + 32 * q + j] = v[j];
+                for (int j = 0; j < 32; ++j) part[kOffW3 + row * 64 + 32 * q + j] = v[j];
             }
-            tc::tmem_ld16(tm + lane + kDW3 + 64, w);
-            part[kOffB3 + t] = w[0];
-            if (warp < 2) {
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
+            if (half == 0) {
+                tc::tmem_ld16(tm + lane + kDW3 + 64, w);
+                part[kOffB3 + row] = w[0];
+            }
+            if (low) {
+                for (int q = q2; q < q2 + 2 / H; ++q) {
                     tc::tmem_ld32(tm + lane + kDW2 + 32 * q, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) part[kOffW2 + t * 64 + 32 * q + j] = v[j];
+                    for (int j = 0; j < 32; ++j) part[kOffW2 + row * 64 + 32 * q + j] = v[j];
                 }
-                tc::tmem_ld16(tm + lane + kDW2 + 64, w);
-                part[kOffB2 + t] = w[0];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = q4; q < q4 + 4 / H; ++q) {
                     tc::tmem_ld32(tm + lane + kDW1 + 32 * q, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) part[kOffW1 + t * 128 + 32 * q + j] = v[j];
+                    for (int j = 0; j < 32; ++j) part[kOffW1 + row * 128 + 32 * q + j] = v[j];
                 }
-                tc::tmem_ld16(tm + lane + kDW1 + 128, w);
-                part[kOffB1 + t] = w[0];
+                if (half == 0) {
+                    tc::tmem_ld16(tm + lane + kDW2 + 64, w);
+                    part[kOffB2 + row] = w[0];
+                    tc::tmem_ld16(tm + lane + kDW1 + 128, w);
+                    part[kOffB1 + row] = w[0];
+                }
             }
         } else {
-            for (int k = t; k < kParams; k += kTile) part[k] = 0.0f;
+            for (int k = t; k < kParams; k += NT) part[k] = 0.0f;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -466,8 +496,10 @@ __global__ void __launch_bounds__(kTile, MODE == kTrain ? 1 : 2) apod_kernel(con
         if ((t & 31) == 0) red[0][warp] = loss_acc, red[1][warp] = cnt_acc;
         __syncthreads();
         if (t == 0) {
-            part[kParams] = red[0][0] + red[0][1] + red[0][2] + red[0][3];
-            part[kParams + 1] = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+            float ls = 0.0f, cs = 0.0f;
+            for (int k = 0; k < NT / 32; ++k) ls += red[0][k], cs += red[1][k];
+            part[kParams] = ls;
+            part[kParams + 1] = cs;
         }
     }
     tc::fence_before_sync();

@@ -267,7 +267,7 @@ static int launch_apod(const apod::Args &a, long long n_tiles, int per_sm, cudaS
     const int smem = apod::Smem<MODE>::TOTAL;
     if (cudaFuncSetAttribute(apod::apod_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return SUPRA_ECUDA;
-    apod::apod_kernel<MODE><<<grid, apod::kTile, smem, st>>>(a);
+    apod::apod_kernel<MODE><<<grid, apod::apod_threads<MODE>(), smem, st>>>(a);
     return check_cuda(cudaGetLastError());
 }
 
