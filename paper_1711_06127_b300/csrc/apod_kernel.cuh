@@ -147,12 +147,14 @@ __device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t &phase) {
     return ok;
 }
 
-// Threads per CTA: training splits every pixel row over two warpgroups (warps w
-// and w + 4 share TMEM lanes 32 (w % 4).., each takes half of every row's
-// columns), so two warps per scheduler hide each other's TMEM, shared-memory
-// and MMA waits; the two-CTA-per-SM modes keep one warpgroup.
+// Threads per CTA: training and the fused beamformer split every pixel row over
+// two warpgroups (warps w and w + 4 share TMEM lanes 32 (w % 4).., each takes
+// half of every row's columns; in the beamformer each half gathers the elements
+// whose weights it computes), so two warps per scheduler hide each other's
+// gather, TMEM, shared-memory and MMA waits; the forward pass on stored rows
+// keeps one warpgroup.
 template <int MODE>
-__host__ __device__ constexpr int apod_threads() { return MODE == kTrain ? 256 : 128; }
+__host__ __device__ constexpr int apod_threads() { return MODE == kForward ? 128 : 256; }
 
 template <int MODE>
 __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) apod_kernel(const Args a) {
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             PixelGeo g;
             if (row_ok) g = pixel_geo(a.plan, a.ch, line, i);
 #pragma unroll 1
-            for (int c = 0; c < 16; ++c) {
+            for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) {
                 if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
                     chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
                     continue;
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 }
                 chunk(sm, S::X, c, row) = pack8(v);
             }
-            nrm = sqrtf(n2v[0] + n2v[1]);
+            nrm = n2v[0] + n2v[1];   // this half's share of ||x||^2 (square root below)
         } else {
             p = tile * kTile + row;
             row_ok = p < a.n;
@@ -258,12 +260,14 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                     chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
             }
         }
-        const bool valid = row_ok && nrm > 0.0f;
+        if constexpr (MODE == kInfer && H > 1) xrow[0][half][row] = nrm;
         tc::fence_async_smem();
         tc::fence_before_sync();
         ok = __syncthreads_and(ok);
         if (!ok) break;
         tc::fence_after_sync();
+        if constexpr (MODE == kInfer) nrm = sqrtf(H > 1 ? xrow[0][0][row] + xrow[0][1][row] : nrm);
+        const bool valid = row_ok && nrm > 0.0f;
 
         // ---- Z1 = X W1^T
         if (t == 0) {
