@@ -44,6 +44,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over the ranks (the job's time is its slowest
+    rank's); x itself with one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (replicas: each rank does the same work)."""
+    return units_per_rank * world / seconds
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -646,15 +665,10 @@ def run_ours(args):
     barrier()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     per_frame = s.n_tx * s.n_el * s.n_samples
     frames = BATCH * args.steps * world
-    value = per_frame * frames / (total_ms * 1e-3)
+    value = job_rate(per_frame * BATCH * args.steps, world, total_ms * 1e-3)
 
     # ---- the dominant kernel alone: beamforming + envelope + log compression, same launch shape
     for _ in range(3):
@@ -776,13 +790,8 @@ def run_ours(args):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = per_frame * BATCH * e2e_steps * world / e2e_s if e2e_steps else None
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e_value = job_rate(per_frame * BATCH * e2e_steps, world, e2e_s) if e2e_steps else None
     h2d = sum(c.numel() * c.element_size() for c in chs)
     d2h = sum(o.numel() for o in outs)
     assert supra.device_status() == 0
