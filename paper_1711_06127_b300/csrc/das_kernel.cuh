@@ -40,16 +40,26 @@
 //
 // After the last chunk of a tile (MODE 1) the RF of the tile goes to a
 // per-frame ring that keeps the previous tile's last 2H samples, the complex
-// demodulating FIR runs register-blocked over it, and the log-compressed
-// codes are written out.
+// demodulating FIR runs over it, and the log-compressed codes are written out.
+// With G = 16 the FIR runs on the tensor cores (tcgen05): within a tile it is
+// a product of one fixed banded Toeplitz matrix of taps with the ring, so the
+// taps sit in tensor memory for the whole CTA, the ring is the FP16 B operand
+// in shared memory and the accumulators come back from tensor memory; other
+// group sizes run it register-blocked on the FP32 cores.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace supra {
 
 constexpr int kTD = 256;             // depth samples per tile = consumer threads
 constexpr int kConsumers = 256;
 constexpr int kCtaThreads = 288;     // + one producer warp
+// the G = 16 envelope kernel has a tenth warp that issues the tensor-core FIR
+template <int G, int MODE>
+__host__ __device__ constexpr int das_threads() { return (MODE == 1 && G == 16) ? kCtaThreads + 32 : kCtaThreads; }
 constexpr int kRows = 32;            // rows staged per stage = producer lanes
 constexpr int kStages = 4;
 constexpr float kMagic = 8421376.0f; // 2^23 + 2^15
@@ -185,16 +195,31 @@ constexpr int kLag = 32;
 constexpr int kRingLen = kTD + kHalo;
 __device__ __forceinline__ int ring_addr(int p) { return p + (p >> 3); }
 
+// G = 16 FIR on the tensor cores.  The ring holds the RF [kRingLen][16 frames]
+// split as x = hi + lo (hi = x rounded to FP16, lo = the rest rounded to FP16),
+// as one MN-major B operand of N = 32 columns (hi of frames 0..15, then lo) in
+// the canonical no-swizzle layout: the core matrix (8 ring positions x 8
+// columns, 128 B) of positions 8a.. and columns 8c.. sits at byte 512 a + 128 c,
+// so core matrices adjacent in K (positions) are 512 B apart and adjacent in N
+// 128 B apart.
+constexpr int kRing16Bytes = kRingLen * 32 * 2;
+// tensor memory: taps hi (columns 0-63) and lo (64-127), 128 x 128 FP16 each;
+// accumulators D (128-255, 4 blocks x 32 columns: the hi and lo halves of 16 frames)
+constexpr uint32_t kFirTmemCols = 256;
+constexpr uint32_t kFirColLo = 64, kFirColD = 128;
+
 // Shared-memory layout, identical on host and device.
 struct SmemLayout {
     int bars, meta, taps, ring, stage, total, ring_stride;
     __host__ __device__ SmemLayout(int G, int mode, int W) {
-        bars = 0;                                             // full[kStages], empty[kStages], abort flag
+        bars = 0;                                             // full[kStages], empty[kStages], abort flag,
+                                                              // FIR done (72), tensor-memory base (80),
+                                                              // FIR ring ready (88)
         meta = 128;                                           // [kStages][kRows] ElemMeta
         taps = meta + kStages * kRows * (int)sizeof(ElemMeta); // [kTapSlots] float4 (c, c, s, s)
         ring = taps + (mode == 1 ? kTapSlots * 16 : 0);
         ring_stride = ((kRingLen - 1) + ((kRingLen - 1) >> 3) + 1 + 3) & ~3;
-        stage = ring + (mode == 1 ? G * ring_stride * 4 : 0);
+        stage = ring + (mode == 1 ? (G == 16 ? kRing16Bytes : G * ring_stride * 4) : 0);
         stage = (stage + 127) & ~127;
         total = stage + kStages * kRows * W * 2;
     }
@@ -525,58 +550,127 @@ __device__ __forceinline__ void store_codes8(uint8_t *row, int o, int nd, const 
     }
 }
 
-// G == 16: thread -> frame pair q = tid / 32, outputs t = 8 bq + j (bq = tid % 32, j < 8).
-// Taps go in 8 blocks of 8; the sliding window of 15 ring values is kept in
-// registers and shifted by 8 positions per block (8 new loads per block), and
-// every shared address is the thread's base plus a compile-time offset:
-// for block b and d = j - kk, u = 8 (bq - b) + 63 + d, so
-// ring_addr(u) = 9 bq - 9 b + 63 + d + ((63 + d) >> 3).
-__device__ __forceinline__ void fir_log_tile16(const float *ring, int RS, const float4 *taps4, uint8_t *outA,
-                                               uint8_t *outB, long long row_off, int i0, int nd, float a2, float b2,
-                                               bool wa, bool wb) {
-    const int tid = threadIdx.x;
-    const int q = tid >> 5, bq = tid & 31;
-    const float *ra = ring + (2 * q) * RS + 9 * bq;
-    const float *rb = ring + (2 * q + 1) * RS + 9 * bq;
-    u64 re[8], im[8], win[15];
+// ---- G = 16: the FIR on the tensor cores.  Per 64-output block b of the tile,
+// D_b [128 x 32] = A [128 x 128] * ring [positions 64 b .. 64 b + 127][hi, lo of 16 frames].
+// Row r of A (lane r of tensor memory): quadrant qd = r / 32, j = r % 32, part
+// j / 16 (0: cos taps -> I, 1: sin taps -> Q) of the block's output t = 16 qd +
+// j % 16; column u (ring position 64 b + u) holds tap k' = 63 + t - u when
+// 0 <= k' < 64, else 0.  A is the same for every block and every tile.  With A
+// and the ring each split into FP16 hi + lo parts, two MMAs per K step (A hi and
+// A lo, each against the ring's hi and lo columns; FP32 accumulation) leave an
+// error of order 2^-22 of each product, as FP32 arithmetic would.  The taps are scaled by kFirTapScale
+// (a power of two) so that their lo parts stay normal FP16 numbers; the log
+// stage removes the scale exactly.
+constexpr float kFirTapScale = 4096.0f;
+constexpr float kFirLog2Scale2 = 24.0f;   // log2(kFirTapScale^2)
+
+__device__ __forceinline__ uint32_t half2_bits(__half2 h) { return *reinterpret_cast<const uint32_t *>(&h); }
+
+// (a, b) -> FP16 pairs hi = (a, b) rounded and lo = the remainders rounded.
+__device__ __forceinline__ void split_half2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    hi = half2_bits(h);
+    lo = half2_bits(__floats2half2_rn(a - hf.x, b - hf.y));
+}
+
+// Warps 0..3 write lanes 32 w .. 32 w + 31 of A hi and A lo (64 columns of FP16 pairs each).
+__device__ __forceinline__ void fir_tc_fill_taps(const DevPlan *__restrict__ P, uint32_t tbase, int warp, int lane) {
+    const int t = 16 * warp + (lane & 15);
+    const float *taps = lane < 16 ? P->taps_c : P->taps_s;
+    const uint32_t row = tbase + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        uint32_t rh[16], rl[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) re[j] = im[j] = 0ull;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        // window slot d + 7 (d = -7..7); slots d = 1..7 carry over from the previous block
-#pragma unroll
-        for (int d = 7; d >= -7; --d) {
-            if (b > 0 && d >= 1) {
-                win[d + 7] = win[d - 1];   // value of d - 8 in the previous block
-            } else {
-                const int off = -9 * b + 63 + d + ((63 + d) >> 3);
-                win[d + 7] = pack2(ra[off], rb[off]);
-            }
+        for (int c = 0; c < 16; ++c) {
+            const int k0 = 63 + t - 2 * (c0 + c), k1 = k0 - 1;   // columns u = 2 (c0 + c) and u + 1
+            const float a = (k0 >= 0 && k0 < kTapSlots) ? kFirTapScale * taps[k0] : 0.f;
+            const float b = (k1 >= 0 && k1 < kTapSlots) ? kFirTapScale * taps[k1] : 0.f;
+            split_half2(a, b, rh[c], rl[c]);
         }
+        tc::tmem_st16(row + (uint32_t)c0, rh);
+        tc::tmem_st16(row + kFirColLo + (uint32_t)c0, rl);
+    }
+    tc::tmem_st_wait();
+}
+
+// This thread's 16 frames of ring position u, as FP16 hi (columns 0..15) and lo (16..31).
+__device__ __forceinline__ void ring16_put(unsigned char *ring16, int u, const float (&v)[16]) {
+    uint32_t h[8], l[8];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const float4 t4 = taps4[8 * b + kk];
-            const u64 C = pack2(t4.x, t4.y), S = pack2(t4.z, t4.w);
+    for (int k = 0; k < 8; ++k) split_half2(v[2 * k], v[2 * k + 1], h[k], l[k]);
+    unsigned char *row = ring16 + (u >> 3) * 512 + (u & 7) * 16;
+    *reinterpret_cast<uint4 *>(row) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(row + 128) = make_uint4(h[4], h[5], h[6], h[7]);
+    *reinterpret_cast<uint4 *>(row + 256) = make_uint4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<uint4 *>(row + 384) = make_uint4(l[4], l[5], l[6], l[7]);
+}
+
+// One thread: 8 K steps of 16 positions x the 4 blocks x (A hi, A lo), then a commit to `bar`.
+__device__ __forceinline__ void fir_tc_issue(uint32_t tbase, uint32_t ring_saddr, uint64_t *bar) {
+    constexpr uint32_t idesc = tc::idesc_f16(128, 32, false, true);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const u64 v = win[j - kk + 7];
-                re[j] = fma2(C, v, re[j]);
-                im[j] = fma2(S, v, im[j]);
-            }
+    for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t d = tbase + kFirColD + 32u * b;
+            const uint64_t bd = tc::smem_desc(ring_saddr + 4096u * b + 1024u * kk, 512, 128);
+            tc::mma_f16_ta(d, tbase + 8u * kk, bd, idesc, kk > 0);
+            tc::mma_f16_ta(d, tbase + kFirColLo + 8u * kk, bd, idesc, true);
         }
     }
-    uint32_t ca[8], cb[8];
+    tc::mma_commit(bar);
+}
+
+// Warp w reads lanes 32 (w % 4) .. of blocks 2 (w / 4) and 2 (w / 4) + 1: lane j
+// holds part j / 16 of output t = 64 blk + 16 (w % 4) + j % 16 for the 16 frames
+// (the sum of a block's hi and lo columns).
+// Lanes j and j ^ 16 swap half of their values, so lane j < 16 finishes |iq|^2
+// of frames 0..7 and lane j >= 16 of frames 8..15, and writes their codes.
+__device__ __forceinline__ void fir_tc_epilogue(uint32_t tbase, const FrameGroup &fg, int nf, long long row_off,
+                                                int i0, int nd, float a2, float b2s) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qd = warp & 3, h = warp >> 2;
+    float v[32];
+    {
+        const uint32_t ta = tbase + ((uint32_t)(32 * qd) << 16) + kFirColD + 64u * h;
+        float d[32];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const u64 qq = fma2(re[j], re[j], mul2(im[j], im[j]));
-        float qa, qb;
-        unpack2(qq, qa, qb);
-        ca[j] = code_of(qa, a2, b2);
-        cb[j] = code_of(qb, a2, b2);
+        for (int bi = 0; bi < 2; ++bi) {
+            tc::tmem_ld32(ta + 32u * bi, d);
+#pragma unroll
+            for (int f = 0; f < 16; ++f) v[16 * bi + f] = d[f] + d[16 + f];
+        }
     }
-    const int o = i0 - kLag + 8 * bq;
-    if (wa) store_codes8(outA + row_off, o, nd, ca);
-    if (wb) store_codes8(outB + row_off, o, nd, cb);
+    const bool hi = lane >= 16;
+    const int f0 = hi ? 8 : 0;
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi) {
+        const int o = i0 - kLag + 64 * (2 * h + bi) + 16 * qd + (lane & 15);
+        const bool in = o >= 0 && o < nd;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float a = v[16 * bi + k], b = v[16 * bi + 8 + k];
+            const float other = __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+            const float keep = hi ? b : a;
+            const float q = fmaf(keep, keep, other * other);
+            if (in && f0 + k < nf) static_cast<uint8_t *>(fg.out[f0 + k])[row_off + o] = (uint8_t)code_of(q, a2, b2s);
+        }
+    }
+}
+
+// Wait (bounded) for the products of tile `tile` (phase tile of the FIR
+// mbarrier); true for the whole warp when they are complete.  A timeout flags the
+// CTA and sets the device status.
+__device__ __forceinline__ bool fir_tc_wait(uint64_t *bar, int tile, volatile int *abort_flag, bool &aborted) {
+    const bool ok = __all_sync(0xffffffffu, wait_phase(bar, (uint32_t)(tile & 1), abort_flag));
+    if (!ok) {
+        aborted = true;
+        *abort_flag = 1;
+        set_status(SUPRA_ETIMEOUT);
+    }
+    return ok;
 }
 
 // Other group sizes: frame pairs with BO = G / 2 outputs per thread (G >= 2), or one
@@ -637,7 +731,7 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // MODE 0: write RF (float [n_lines][n_depth] per frame).
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
 template <int G, int MODE, bool EXT>
-__global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_constant__ LaunchGroups L) {
+__global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __grid_constant__ LaunchGroups L) {
     constexpr int E = kRows / G;
     extern __shared__ __align__(128) unsigned char smem[];
     int gi, line;
@@ -651,6 +745,10 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
     uint64_t *empty = full + kStages;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kStages);
+    constexpr bool kTcFir = (MODE == 1 && G == 16);
+    uint64_t *fir_bar = reinterpret_cast<uint64_t *>(smem + lay.bars + 72);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.bars + 80);
+    uint64_t *ring_bar = reinterpret_cast<uint64_t *>(smem + lay.bars + 88);
     ElemMeta *metas = reinterpret_cast<ElemMeta *>(smem + lay.meta);
     float4 *taps4 = reinterpret_cast<float4 *>(smem + lay.taps);
     float *ring = reinterpret_cast<float *>(smem + lay.ring);
@@ -664,18 +762,37 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumers / 32);
         }
+        if (kTcFir) {
+            mbar_init(fir_bar, 1);
+            mbar_init(ring_bar, 1);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (MODE == 1) {
-        for (int k = tid; k < kTapSlots; k += kCtaThreads) {
+    if constexpr (kTcFir) {
+        if (warp == 0) {
+            tc::tmem_alloc(tmem_slot, kFirTmemCols);
+            tc::fence_before_sync();
+        }
+        for (int k = tid; k < kRing16Bytes / 4; k += (int)blockDim.x) reinterpret_cast<uint32_t *>(ring)[k] = 0u;
+    } else if (MODE == 1) {
+        for (int k = tid; k < kTapSlots; k += (int)blockDim.x) {
             const float c = P->taps_c[k], s = P->taps_s[k];
             taps4[k] = make_float4(c, c, s, s);
         }
-        for (int k = tid; k < G * lay.ring_stride; k += kCtaThreads) ring[k] = 0.f;
+        for (int k = tid; k < G * lay.ring_stride; k += (int)blockDim.x) ring[k] = 0.f;
     }
     const LineGeo lg = P->lines[line];
     __syncthreads();
+    uint32_t tbase = 0;   // tensor memory of the FIR (kTcFir)
+    if constexpr (kTcFir) {
+        tc::fence_after_sync();
+        tbase = *tmem_slot;
+        if (warp < 4) {
+            fir_tc_fill_taps(P, tbase, warp, tid & 31);
+            tc::fence_before_sync();
+        }
+    }
 
     if (warp == kConsumers / 32) {
         // ------------------------------------------------------------------ producer warp
@@ -790,6 +907,22 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
         return;
     }
 
+    if constexpr (kTcFir) {
+        if (warp == kConsumers / 32 + 1) {
+            // ------------------------------------------------------------ FIR issuer (one lane)
+            // tile n's products once the consumers have written its ring (ring_bar phase n)
+            if ((tid & 31) == 0) {
+                const uint32_t ring_saddr = tc::smem_u32(ring);
+                for (int t = 0; t <= NT; ++t) {
+                    if (!wait_phase(ring_bar, (uint32_t)(t & 1), abort_flag)) break;
+                    tc::fence_after_sync();
+                    fir_tc_issue(tbase, ring_saddr, fir_bar);
+                }
+            }
+            return;
+        }
+    }
+
     // ---------------------------------------------------------------------- consumer warps
     const int m = tid;
     const bool use_y = P->el_ny > 1 || P->ymax > P->ymin;
@@ -848,7 +981,17 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 if (last) break;
             }
         }
-        if (consumer_sync_or(aborted ? 1 : 0)) return;
+        if (consumer_sync_or(aborted ? 1 : 0)) {
+            if constexpr (kTcFir) {
+                if (warp == 0) {
+                    // the previous tile's products may still be in flight
+                    if (tile > 0) mbar_wait_bounded(fir_bar, (uint32_t)((tile - 1) & 1), 1LL << 27);
+                    tc::fence_after_sync();
+                    tc::tmem_free(tbase, kFirTmemCols);
+                }
+            }
+            return;
+        }
         const bool act = (tile < NT) && (i < nd);
         const float inv = wsum > 0.f ? 1.0f / wsum : 0.f;
         float v[G];
@@ -869,20 +1012,36 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 for (int g = 0; g < G; ++g)
                     if (g < nf) static_cast<float *>(fg.out[g])[(long long)line * nd + i] = v[g];
             }
+        } else if constexpr (kTcFir) {
+            // The FIR of tile n runs on the tensor cores while the consumers beamform tile n + 1;
+            // its codes are written after that (one accumulator set suffices: they are read out
+            // before the next products are issued).
+            unsigned char *ring16 = reinterpret_cast<unsigned char *>(ring);
+            bool prev = false;
+            if (tile > 0) {
+                prev = fir_tc_wait(fir_bar, tile - 1, abort_flag, aborted);
+                // keep the last kHalo positions (bytes 512 kTD / 8 ..) as the next tile's leading
+                // halo: 4096 B, 16 B per thread
+                const uint4 x = *reinterpret_cast<const uint4 *>(ring16 + (kTD / 8) * 512 + 16 * m);
+                consumer_sync();   // every thread has read the previous tile's ring
+                *reinterpret_cast<uint4 *>(ring16 + 16 * m) = x;
+            }
+            ring16_put(ring16, kHalo + m, v);
+            tc::fence_async_smem();
+            if (prev) {
+                tc::fence_after_sync();
+                fir_tc_epilogue(tbase, fg, nf, (long long)line * nd, i0 - kTD, nd, P->log_a2,
+                                P->log_b2 - kFirLog2Scale2 * P->log_a2);
+            }
+            tc::fence_before_sync();
+            consumer_sync();   // ring written, accumulators read out
+            if (tid == 0) mbar_arrive(ring_bar);
         } else {
             const int a = ring_addr(kHalo + m);
 #pragma unroll
             for (int g = 0; g < G; ++g) ring[g * lay.ring_stride + a] = v[g];
             consumer_sync();
-            const float a2 = P->log_a2, b2 = P->log_b2;
-            if constexpr (G == 16) {
-                const int q = m >> 5;
-                fir_log_tile16(ring, lay.ring_stride, taps4, static_cast<uint8_t *>(fg.out[2 * q]),
-                               static_cast<uint8_t *>(fg.out[2 * q + 1]), (long long)line * nd, i0, nd, a2, b2,
-                               2 * q < nf, 2 * q + 1 < nf);
-            } else {
-                fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, a2, b2);
-            }
+            fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, P->log_a2, P->log_b2);
             consumer_sync();
             // keep the last kHalo RF samples as the next tile's leading halo
             for (int k = m; k < G * kHalo; k += kConsumers) {
@@ -890,6 +1049,20 @@ __global__ void __launch_bounds__(kCtaThreads, 2) das_kernel(const __grid_consta
                 ring[g * lay.ring_stride + ring_addr(j)] = ring[g * lay.ring_stride + ring_addr(kTD + j)];
             }
             consumer_sync();
+        }
+    }
+    if constexpr (kTcFir) {
+        // the last tile's FIR
+        if (fir_tc_wait(fir_bar, NT, abort_flag, aborted)) {
+            tc::fence_after_sync();
+            fir_tc_epilogue(tbase, fg, nf, (long long)line * nd, NT * kTD, nd, P->log_a2,
+                            P->log_b2 - kFirLog2Scale2 * P->log_a2);
+        }
+        tc::fence_before_sync();
+        consumer_sync();
+        if (warp == 0) {
+            tc::fence_after_sync();
+            tc::tmem_free(tbase, kFirTmemCols);
         }
     }
 }

@@ -173,7 +173,7 @@ int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
             return SUPRA_ECUDA;
         if (dev < kMaxDev) ready[dev].store(1, std::memory_order_release);
     }
-    kern<<<L.total_lines, kCtaThreads, lay.total, st>>>(L);
+    kern<<<L.total_lines, das_threads<G, MODE>(), lay.total, st>>>(L);
     return check_cuda(cudaGetLastError());
 }
 
