@@ -574,20 +574,41 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t &hi, uint
     lo = half2_bits(__floats2half2_rn(a - hf.x, b - hf.y));
 }
 
-// Warps 0..3 write lanes 32 w .. 32 w + 31 of A hi and A lo (64 columns of FP16 pairs each).
-__device__ __forceinline__ void fir_tc_fill_taps(const DevPlan *__restrict__ P, uint32_t tbase, int warp, int lane) {
+// Tap pairs for the fill: entry j of table (part, plane) holds the FP16 (hi or lo)
+// pair of the scaled taps k = j - 64 and k - 1 (0 outside 0..63), j < 192; the
+// four tables (cos hi, cos lo, sin hi, sin lo) are kFirPairStride words apart
+// (200: the sin tables fall 16 banks away from the cos tables).
+constexpr int kFirPairStride = 200;
+constexpr int kFirPairBytes = 4 * kFirPairStride * 4;
+static_assert(kFirPairBytes <= (kRingLen - kTD) / 8 * 512, "tap-pair tables exceed the last ring positions");
+
+__device__ __forceinline__ void fir_tc_build_pairs(const DevPlan *__restrict__ P, uint32_t *tab) {
+    for (int e = threadIdx.x; e < 2 * 192; e += blockDim.x) {
+        const int part = e / 192, j = e % 192, k = j - 64;
+        const float *taps = part ? P->taps_s : P->taps_c;
+        const float a = (k >= 0 && k < kTapSlots) ? kFirTapScale * taps[k] : 0.f;
+        const float b = (k >= 1 && k - 1 < kTapSlots) ? kFirTapScale * taps[k - 1] : 0.f;
+        uint32_t hi, lo;
+        split_half2(a, b, hi, lo);
+        tab[(2 * part) * kFirPairStride + j] = hi;
+        tab[(2 * part + 1) * kFirPairStride + j] = lo;
+    }
+}
+
+// Warps 0..3 write lanes 32 w .. 32 w + 31 of A hi and A lo (64 columns of FP16
+// pairs each): column c of row (part, t) is the pair of taps k' = 63 + t - 2 c, k' - 1.
+__device__ __forceinline__ void fir_tc_fill_taps(const uint32_t *tab, uint32_t tbase, int warp, int lane) {
     const int t = 16 * warp + (lane & 15);
-    const float *taps = lane < 16 ? P->taps_c : P->taps_s;
+    const uint32_t *th = tab + (lane >> 4) * 2 * kFirPairStride + 127 + t;   // j = 63 + t + 64 at c = 0
+    const uint32_t *tl = th + kFirPairStride;
     const uint32_t row = tbase + ((uint32_t)(32 * warp) << 16);
 #pragma unroll 1
     for (int c0 = 0; c0 < 64; c0 += 16) {
         uint32_t rh[16], rl[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const int k0 = 63 + t - 2 * (c0 + c), k1 = k0 - 1;   // columns u = 2 (c0 + c) and u + 1
-            const float a = (k0 >= 0 && k0 < kTapSlots) ? kFirTapScale * taps[k0] : 0.f;
-            const float b = (k1 >= 0 && k1 < kTapSlots) ? kFirTapScale * taps[k1] : 0.f;
-            split_half2(a, b, rh[c], rl[c]);
+            rh[c] = th[-2 * (c0 + c)];
+            rl[c] = tl[-2 * (c0 + c)];
         }
         tc::tmem_st16(row + (uint32_t)c0, rh);
         tc::tmem_st16(row + kFirColLo + (uint32_t)c0, rl);
@@ -774,7 +795,10 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
             tc::tmem_alloc(tmem_slot, kFirTmemCols);
             tc::fence_before_sync();
         }
-        for (int k = tid; k < kRing16Bytes / 4; k += (int)blockDim.x) reinterpret_cast<uint32_t *>(ring)[k] = 0u;
+        // zero the halo and the first tile's positions; the tap-pair tables for the fill sit in the
+        // last positions' bytes until the first tile's RF overwrites them
+        for (int k = tid; k < (kTD / 8) * 512 / 4; k += (int)blockDim.x) reinterpret_cast<uint32_t *>(ring)[k] = 0u;
+        fir_tc_build_pairs(P, reinterpret_cast<uint32_t *>(ring) + (kTD / 8) * 512 / 4);
     } else if (MODE == 1) {
         for (int k = tid; k < kTapSlots; k += (int)blockDim.x) {
             const float c = P->taps_c[k], s = P->taps_s[k];
@@ -789,7 +813,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
         tc::fence_after_sync();
         tbase = *tmem_slot;
         if (warp < 4) {
-            fir_tc_fill_taps(P, tbase, warp, tid & 31);
+            fir_tc_fill_taps(reinterpret_cast<const uint32_t *>(ring) + (kTD / 8) * 512 / 4, tbase, warp, tid & 31);
             tc::fence_before_sync();
         }
     }
