@@ -444,9 +444,10 @@ __device__ __forceinline__ Geo element_geo(const ElemMeta &md, int i, float r, f
     }
     g.go = __any_sync(0xffffffffu, in) && meta_valid(md);
     w = in ? w : 0.0f;
-    const float r2 = fmaxf(fmaf(r, r + md.beta2, md.gamma), 1e-30f);   // |p - x_e|^2
+    const float num = fmaf(r, md.beta2, md.gamma);                       // |p - x_e|^2 - r^2
+    const float r2 = fmaxf(fmaf(r, r, num), 1e-30f);                      // |p - x_e|^2
     const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);            // |p - x_e| + r
-    const float s = fmaf(__fdividef(fmaf(r, md.beta2, md.gamma), den), fsc, base);
+    const float s = fmaf(__fdividef(num, den), fsc, base);
     const float fl = floorf(s);
     g.w = w;
     g.w1 = w * (s - fl);
