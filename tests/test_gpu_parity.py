@@ -229,16 +229,19 @@ def test_config2_batch_of_64_matches_oracle_on_first_and_last_frame():
     assert max_norm_err(rf, oracle.das(p, chs[7].cpu().numpy())) <= RF_TOL
 
 
-@pytest.mark.parametrize("kind", ["one_tile", "whole_tile", "plane_waves"])
+@pytest.mark.parametrize("kind", ["one_tile", "whole_tile", "pyramid", "plane_waves"])
 def test_sixteen_frame_groups_match_single_frames(kind):
     # groups of 9-16 frames run the demodulating FIR on the tensor cores (split FP16 operands,
     # FP32 accumulation); single frames run it on the FP32 cores.  Records of one depth tile (the
-    # FIR's halo and lag tile), of exactly one tile, and compounded plane-wave lines (the
-    # extended transmit model) must agree with the single-frame path and with the oracle.
+    # FIR's halo and lag tile), of exactly one tile, a matrix-array pyramid (square 3D aperture)
+    # and compounded plane-wave lines (the extended transmit model) must agree with the
+    # single-frame path and with the oracle.
     if kind == "one_tile":
         s = phantom.linear_setup(24, 0.3e-3, 20, 200, fc=5e6, fs=40e6, grid_n=(40, 60))
     elif kind == "whole_tile":
         s = phantom.linear_setup(24, 0.3e-3, 20, 256, fc=5e6, fs=40e6, grid_n=(40, 60))
+    elif kind == "pyramid":
+        s = phantom.pyramid_setup(8, 8, 0.3e-3, 10, 9, 30.0, 400, fc=3.5e6, fs=20e6, grid_n=(40, 36, 50))
     else:
         s = phantom.planewave_setup(32, 0.3e-3, 24, 700, angles_deg=(-8, 0, 8), fc=5e6, fs=40e6,
                                     grid_n=(96, 160))
@@ -247,7 +250,7 @@ def test_sixteen_frame_groups_match_single_frames(kind):
     n = 13
     chs = [phantom.random_channels(s, 500 + k).cuda() for k in range(n)]
     outs = supra.bmode_batched([plan] * n, chs)
-    # images of 2400-15360 pixels: identical codes on >= 99.9 % (a handful of pixels may sit on a
+    # images of 2400-72000 pixels: identical codes on >= 99.9 % (a handful of pixels may sit on a
     # code boundary, where the two FIR forms' summation orders differ), never more than one level
     for k in (0, 6, n - 1):
         single = plan.bmode(chs[k])
