@@ -74,9 +74,13 @@ struct ScanFrame {
 };
 
 constexpr int kMaxScanFrames = 256;
+constexpr int kScanGroup = 4;   // frames of one plan per CTA of the linear kernel
 struct ScanLaunch {
     int n;
     ScanFrame f[kMaxScanFrames];
+    // linear kernel: blockIdx.y = group of gn[g] <= kScanGroup consecutive frames from g0[g], one plan
+    int n_groups;
+    short g0[kMaxScanFrames], gn[kMaxScanFrames];
 };
 
 // Fractional line / depth coordinates of point (x, y, z) and the inside test.
@@ -291,19 +295,23 @@ __global__ void __launch_bounds__(256) scanconvert_kernel(const __grid_constant_
 }
 
 // Linear layouts: the inverse map is separable (u from x, v from z).  A CTA
-// covers 32 columns x 64 rows.  Each warp takes 4 columns; its lanes walk 32
-// consecutive rows of one column at a time, so both lines it interpolates are
-// read within one or two cache lines per load; the tile goes through shared
-// memory so that rows are written out coalesced.  Same arithmetic as
-// scan_coords / lerp_lines.
+// covers 32 columns x 64 rows of up to kScanGroup frames of one plan: the
+// coordinates are computed once and the frames' loads issue together.  Each
+// warp takes 4 columns; its lanes walk 32 consecutive rows of one column at a
+// time, so both lines it interpolates are read within one or two cache lines per
+// load; the tiles go through shared memory so that rows are written out
+// coalesced.  Same arithmetic as scan_coords / lerp_lines.
 __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_constant__ ScanLaunch L) {
-    __shared__ uint8_t tile[64][33];
-    const ScanFrame &F = L.f[blockIdx.y];
-    const DevPlan *P = F.plan;
+    __shared__ uint8_t tile[kScanGroup][64][33];
+    const int f0 = L.g0[blockIdx.y], nf = L.gn[blockIdx.y];
+    const DevPlan *P = L.f[f0].plan;
     const int nx = P->gnx, nz = P->gnz, nlx = P->lines_x, nd = P->n_depth;
     const int cols = (nx + 31) >> 5;
     const int xb = (blockIdx.x % cols) * 32, zb = (blockIdx.x / cols) * 64;
     if (zb >= nz) return;
+    const uint8_t *bm[kScanGroup];
+#pragma unroll
+    for (int f = 0; f < kScanGroup; ++f) bm[f] = L.f[f0 + (f < nf ? f : 0)].bm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c = 0; c < 4; ++c) {
         const int xl = warp * 4 + c, x = xb + xl;
@@ -313,41 +321,47 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
         float fx;
         lerp_axis(u, nlx, ix, fx);
         const int dx = ix + 1 < nlx ? nd : 0;
-        const uint8_t *line = F.bm + (long long)ix * nd;
+        const long long lo = (long long)ix * nd;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int zl = h * 32 + lane, z = zb + zl;
             const float rz = fmaf((float)z, P->gsz, P->goz) - P->apz;
             const float v = (rz - P->v0) * P->dv_inv;
-            uint8_t out = 0;
-            if (in_u && z < nz && v >= -kInsideEps && v <= (float)(nd - 1) + kInsideEps) {
-                int iv;
-                float fv;
-                lerp_axis(v, nd, iv, fv);
-                const int dv = iv + 1 < nd ? 1 : 0;
-                const uint8_t *b = line + iv;
-                const float c0 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
-                const float c1 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
-                out = (uint8_t)fminf(fmaxf(floorf(fmaf(fx, c1 - c0, c0) + 0.5f), 0.0f), 255.0f);
+            const bool in = in_u && z < nz && v >= -kInsideEps && v <= (float)(nd - 1) + kInsideEps;
+            int iv;
+            float fv;
+            lerp_axis(v, nd, iv, fv);
+            const int dv = iv + 1 < nd ? 1 : 0;
+#pragma unroll
+            for (int f = 0; f < kScanGroup; ++f) {
+                uint8_t out = 0;
+                if (in && f < nf) {
+                    const uint8_t *b = bm[f] + lo + iv;
+                    const float c0 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
+                    const float c1 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
+                    out = (uint8_t)fminf(fmaxf(floorf(fmaf(fx, c1 - c0, c0) + 0.5f), 0.0f), 255.0f);
+                }
+                tile[f][zl][xl] = out;
             }
-            tile[zl][xl] = out;
         }
     }
     __syncthreads();
-    // 64 rows x 32 bytes: thread -> (row, 8-byte chunk)
+    // per frame, 64 rows x 32 bytes: thread -> (row, 8-byte chunk)
     const int row = threadIdx.x >> 2, ch = (threadIdx.x & 3) * 8, z = zb + row;
     if (z < nz) {
-        uint8_t *dst = F.img + (long long)z * nx + xb + ch;
-        if (xb + ch + 8 <= nx && (reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
-            uint2 w;
-            w.x = (uint32_t)tile[row][ch] | ((uint32_t)tile[row][ch + 1] << 8) | ((uint32_t)tile[row][ch + 2] << 16) |
-                  ((uint32_t)tile[row][ch + 3] << 24);
-            w.y = (uint32_t)tile[row][ch + 4] | ((uint32_t)tile[row][ch + 5] << 8) |
-                  ((uint32_t)tile[row][ch + 6] << 16) | ((uint32_t)tile[row][ch + 7] << 24);
-            *reinterpret_cast<uint2 *>(dst) = w;
-        } else {
-            for (int k = 0; k < 8; ++k)
-                if (xb + ch + k < nx) dst[k] = tile[row][ch + k];
+        for (int f = 0; f < nf; ++f) {
+            uint8_t *dst = L.f[f0 + f].img + (long long)z * nx + xb + ch;
+            if (xb + ch + 8 <= nx && (reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+                uint2 w;
+                w.x = (uint32_t)tile[f][row][ch] | ((uint32_t)tile[f][row][ch + 1] << 8) |
+                      ((uint32_t)tile[f][row][ch + 2] << 16) | ((uint32_t)tile[f][row][ch + 3] << 24);
+                w.y = (uint32_t)tile[f][row][ch + 4] | ((uint32_t)tile[f][row][ch + 5] << 8) |
+                      ((uint32_t)tile[f][row][ch + 6] << 16) | ((uint32_t)tile[f][row][ch + 7] << 24);
+                *reinterpret_cast<uint2 *>(dst) = w;
+            } else {
+                for (int k = 0; k < 8; ++k)
+                    if (xb + ch + k < nx) dst[k] = tile[f][row][ch + k];
+            }
         }
     }
 }

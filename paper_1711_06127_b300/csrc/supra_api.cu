@@ -215,6 +215,14 @@ int launch_scan(const ScanBatch &S, cudaStream_t st) {
     for (int k = 0; k < S.launch.n; ++k) {
         const DevPlan &H = *S.host[k];
         if (H.geometry == SUPRA_GEOM_LINEAR) {
+            // consecutive frames of one plan share a CTA (up to kScanGroup)
+            const int g = lin.n_groups - 1;
+            if (g >= 0 && lin.gn[g] < kScanGroup && lin.f[lin.n - 1].plan == S.launch.f[k].plan) {
+                ++lin.gn[g];
+            } else {
+                lin.g0[lin.n_groups] = (short)lin.n;
+                lin.gn[lin.n_groups++] = 1;
+            }
             lin.f[lin.n++] = S.launch.f[k];
             lin_blocks = std::max(lin_blocks, (long long)((H.gnx + 31) / 32) * ((H.gnz + 63) / 64));
         } else {
@@ -228,7 +236,7 @@ int launch_scan(const ScanBatch &S, cudaStream_t st) {
     if (lin.n) {
         // every CTA of the largest frame; smaller frames' extra CTAs return at once
         if (lin_blocks > 0x7fffffffLL) return SUPRA_EINVAL;
-        scanconvert_linear_kernel<<<dim3((unsigned)lin_blocks, lin.n), 256, 0, st>>>(lin);
+        scanconvert_linear_kernel<<<dim3((unsigned)lin_blocks, lin.n_groups), 256, 0, st>>>(lin);
         const int rc = check_cuda(cudaGetLastError());
         if (rc) return rc;
     }
