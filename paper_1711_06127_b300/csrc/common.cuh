@@ -102,6 +102,7 @@ struct LaunchGroups {
     int n_groups;
     int total_lines;
     int uniform;                         // every group uses the same plan
+    int n_seg;                           // depth segments per line (0 or 1: whole lines); CTA = (item, segment)
     FrameGroup g[kMaxGroupsPerLaunch];
 };
 static_assert(sizeof(LaunchGroups) <= 32000, "kernel parameter space is 32 KB");

@@ -755,19 +755,34 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 template <int G, int MODE, bool EXT>
 __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __grid_constant__ LaunchGroups L) {
     constexpr int E = kRows / G;
+    constexpr bool kTcFir = (MODE == 1 && G == 16);   // FIR on the tensor cores; whole lines only
     extern __shared__ __align__(128) unsigned char smem[];
+    if constexpr (kTcFir) {
+        if (L.n_seg > 1) {   // the host never splits these lines
+            if (threadIdx.x == 0) set_status(SUPRA_EINVAL);
+            return;
+        }
+    }
     int gi, line;
-    locate_item(L, blockIdx.x, gi, line);
+    const int n_seg = kTcFir ? 1 : max(L.n_seg, 1);
+    locate_item(L, kTcFir ? (int)blockIdx.x : (int)blockIdx.x / n_seg, gi, line);
     const FrameGroup &fg = L.g[gi];
     const DevPlan *P = fg.plan;
     const int nf = min(fg.n, G);
     const int NT = P->n_tiles;
     const int nd = P->n_depth;
+    // Depth segment: tiles [T0, T1) of the line emit their outputs.  With the envelope,
+    // a segment after the first also beamforms tile T0 - 1 (its RF becomes the FIR's
+    // leading halo; its outputs belong to the previous segment), and the last segment
+    // runs the lag tile after the last one.
+    const int seg = kTcFir ? 0 : (int)blockIdx.x % n_seg;
+    const int T0 = kTcFir ? 0 : seg * NT / n_seg, T1 = kTcFir ? NT : (seg + 1) * NT / n_seg;
+    const int tb = (MODE == 1 && T0 > 0) ? T0 - 1 : T0;
+    const int te = T1 + ((MODE == 1 && seg == n_seg - 1) ? 1 : 0);
     const SmemLayout lay(G, MODE, kSlotSamples);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
     uint64_t *empty = full + kStages;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kStages);
-    constexpr bool kTcFir = (MODE == 1 && G == 16);
     uint64_t *fir_bar = reinterpret_cast<uint64_t *>(smem + lay.bars + 72);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.bars + 80);
     uint64_t *ring_bar = reinterpret_cast<uint64_t *>(smem + lay.bars + 88);
@@ -852,7 +867,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
         // passes; stages never mix transmits and only the tile's final pass marks its
         // last stage.  Without compounding there is one pass per tile.
         const int n_comp = EXT ? P->n_comp : 1;   // compile-time 1 for plans with a plain transmit model
-        for (int vt = 0; vt < NT * n_comp && ok; ++vt) {
+        for (int vt = tb * n_comp; vt < T1 * n_comp && ok; ++vt) {
             const int tile = vt / n_comp, ci = vt - tile * n_comp;
             const bool final_ci = ci == n_comp - 1;
             const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
@@ -956,14 +971,14 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
     int sb = 0;                 // stage buffer of the next stage
     uint32_t parity = 0;        // its full-barrier phase parity
     bool aborted = false;
-    for (int tile = 0; tile < NT + (MODE == 1 ? 1 : 0); ++tile) {
+    for (int tile = tb; tile < te; ++tile) {
         const int i0 = tile * kTD;
         const int i = i0 + m;
         u64 acc2[G / 2 > 0 ? G / 2 : 1];
 #pragma unroll
         for (int q = 0; q < (G / 2 > 0 ? G / 2 : 1); ++q) acc2[q] = 0ull;
         float acc1 = 0.f, wsum = 0.f;
-        if (tile < NT) {
+        if (tile < T1) {
             const float r = P->depth0 + (float)i * P->depth_step;
             const float px = fmaf(r, lg.dx, lg.ox), py = fmaf(r, lg.dy, lg.oy), pz = fmaf(r, lg.dz, lg.oz);
             const float qx = fminf(fmaxf(px, P->xmin), P->xmax);
@@ -1066,7 +1081,8 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
 #pragma unroll
             for (int g = 0; g < G; ++g) ring[g * lay.ring_stride + a] = v[g];
             consumer_sync();
-            fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, P->log_a2, P->log_b2);
+            if (tile >= T0)   // a halo tile's outputs belong to the previous segment
+                fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, P->log_a2, P->log_b2);
             consumer_sync();
             // keep the last kHalo RF samples as the next tile's leading halo
             for (int k = m; k < G * kHalo; k += kConsumers) {

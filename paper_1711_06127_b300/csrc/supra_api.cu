@@ -153,6 +153,20 @@ bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Depth segments per line for a launch of `items` lines whose shortest line has
+// min_tiles depth tiles: a launch that leaves SMs idle (fewer lines than two
+// resident CTAs per SM) splits its lines so that the segments still fit in one
+// wave.  16-frame B-mode launches (the tensor-core FIR) keep whole lines.
+int depth_segments(int items, int min_tiles, int G, int mode) {
+    if (mode == 1 && G == 16) return 1;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int slots = 2 * sms;
+    const int s = items > 0 ? slots / items : 1;
+    return std::max(1, std::min(s, min_tiles));
+}
+
 // kernel choice for a frame group size
 int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
 
@@ -173,7 +187,7 @@ int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
             return SUPRA_ECUDA;
         if (dev < kMaxDev) ready[dev].store(1, std::memory_order_release);
     }
-    kern<<<L.total_lines, das_threads<G, MODE>(), lay.total, st>>>(L);
+    kern<<<L.total_lines * std::max(L.n_seg, 1), das_threads<G, MODE>(), lay.total, st>>>(L);
     return check_cuda(cudaGetLastError());
 }
 
@@ -710,6 +724,7 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
     L.uniform = 1;
+    L.n_seg = depth_segments(L.total_lines, plan->host.n_tiles, 1, 0);
     return launch_das(1, 0, plan->ext, L, static_cast<cudaStream_t>(stream));
 }
 
@@ -813,11 +828,14 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
             if (!present[class_of(Gc)][comp]) continue;
             LaunchGroups L{};
             L.uniform = 1;
+            int min_tiles = 1 << 30;
             auto flush = [&]() -> int {
                 if (L.n_groups == 0) return SUPRA_OK;
+                L.n_seg = depth_segments(L.total_lines, min_tiles, Gc, 1);
                 const int rc = launch_das(Gc, 1, comp == 1, L, st);
                 L = LaunchGroups{};
                 L.uniform = 1;
+                min_tiles = 1 << 30;
                 return rc;
             };
             for (const Grp &gr : groups) {
@@ -849,6 +867,7 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
                 }
                 if (L.n_groups > 0 && L.g[0].plan != g.plan) L.uniform = 0;
                 L.total_lines += gr.p->host.n_lines;
+                min_tiles = std::min(min_tiles, gr.p->host.n_tiles);
                 ++L.n_groups;
                 if (L.n_groups == kMaxGroupsPerLaunch) {
                     const int rc = flush();
