@@ -872,17 +872,23 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
             const bool final_ci = ci == n_comp - 1;
             const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
             const int nbox = (b.y - b.x + 1) * (b.w - b.z + 1) * (halves ? 2 : 1);
-            // pass 1: how many elements can be active in this tile
-            int nact = 0;
-            for (int jb = 0; jb < nbox; jb += 32) {
-                int e, ia, ib;
-                float4 xe;
-                const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
-                nact += __popc(__ballot_sync(0xffffffffu, a));
+            // Stage the active elements, E per stage, and mark the tile's last stage.  With a few
+            // elements per stage (G >= 8) a full stage is handed over when the next element
+            // needs a slot or the pass ends, so the last stage is known then; with many (a
+            // stage of G < 8 frames empties fast) a first pass counts the stages, so that each
+            // is handed over as soon as it is full.
+            constexpr bool kDefer = G >= 8;
+            int nst = 0, emitted = 0;
+            if constexpr (!kDefer) {
+                int nact = 0;
+                for (int jb = 0; jb < nbox; jb += 32) {
+                    int e, ia, ib;
+                    float4 xe;
+                    const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                    nact += __popc(__ballot_sync(0xffffffffu, a));
+                }
+                nst = max(1, (nact + E - 1) / E);
             }
-            const int nst = max(1, (nact + E - 1) / E);
-            int emitted = 0;
-            // pass 2: stage them, E per stage
             for (int jb = 0; jb < nbox && ok; jb += 32) {
                 int e, ia, ib;
                 float4 xe;
@@ -904,6 +910,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
                 }
                 uint32_t mask = __ballot_sync(0xffffffffu, a);
                 while (mask) {
+                    if (kDefer && slot == E) finalize(false);   // more elements follow
                     if (slot == 0 && !acquire()) {
                         ok = false;
                         break;
@@ -922,17 +929,17 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
                     // drop the `take` lowest lanes of the mask
                     for (int t = 0; t < take; ++t) mask &= mask - 1u;
                     slot += take;
-                    if (slot == E) {
+                    if (!kDefer && slot == E) {
                         ++emitted;
                         finalize(final_ci && emitted == nst);
                     }
                 }
             }
-            if (ok && (slot > 0 || (emitted == 0 && final_ci))) {
+            // the pass's last stage (an empty one when the tile's final pass staged nothing)
+            if (ok && (slot > 0 || (final_ci && (kDefer || emitted == 0)))) {
                 if (slot == 0 && !acquire()) {
                     ok = false;
                 } else {
-                    ++emitted;
                     finalize(final_ci);
                 }
             }
