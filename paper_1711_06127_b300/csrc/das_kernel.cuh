@@ -21,7 +21,7 @@
 //   * warps 0..7 (consumers) wait on "full", compute the delay, the linear
 //     interpolation weights and the apodization weight of each element once,
 //     apply them to all G frames, and release the buffer on its "empty"
-//     mbarrier.  A ring of kStages buffers keeps the HBM stream going while the
+//     mbarrier.  A ring of stage buffers keeps the HBM stream going while the
 //     consumers work; consumers and producer never meet at a CTA barrier.
 // Frames of one plan share their delays, which is what makes a batch cheaper
 // per frame than a single frame.
@@ -60,8 +60,12 @@ constexpr int kCtaThreads = 288;     // + one producer warp
 // the G = 16 envelope kernel has a tenth warp that issues the tensor-core FIR
 template <int G, int MODE>
 __host__ __device__ constexpr int das_threads() { return (MODE == 1 && G == 16) ? kCtaThreads + 32 : kCtaThreads; }
-constexpr int kRows = 32;            // rows staged per stage = producer lanes
-constexpr int kStages = 4;
+// Rows (frame rows of E = rows / G elements) per stage and stages in the ring: 16-frame
+// groups stage 3 elements per stage in 3 stages (fewer hand-overs per element), the
+// others 32 rows (E <= 32 producer lanes) in 4.
+__host__ __device__ constexpr int rows_of(int G) { return G == 16 ? 48 : 32; }
+__host__ __device__ constexpr int stages_of(int G) { return G == 16 ? 3 : 4; }
+constexpr int kMaxStages = 4;
 constexpr float kMagic = 8421376.0f; // 2^23 + 2^15
 
 struct ElemMeta {
@@ -212,16 +216,16 @@ constexpr uint32_t kFirColLo = 64, kFirColD = 128;
 struct SmemLayout {
     int bars, meta, taps, ring, stage, total, ring_stride;
     __host__ __device__ SmemLayout(int G, int mode, int W) {
-        bars = 0;                                             // full[kStages], empty[kStages], abort flag,
+        bars = 0;                                             // full[kMaxStages], empty[kMaxStages], abort flag,
                                                               // FIR done (72), tensor-memory base (80),
                                                               // FIR ring ready (88)
-        meta = 128;                                           // [kStages][kRows] ElemMeta
-        taps = meta + kStages * kRows * (int)sizeof(ElemMeta); // [kTapSlots] float4 (c, c, s, s)
+        meta = 128;                                           // [stages][rows] ElemMeta
+        taps = meta + stages_of(G) * rows_of(G) * (int)sizeof(ElemMeta); // [kTapSlots] float4 (c, c, s, s)
         ring = taps + (mode == 1 ? kTapSlots * 16 : 0);
         ring_stride = ((kRingLen - 1) + ((kRingLen - 1) >> 3) + 1 + 3) & ~3;
         stage = ring + (mode == 1 ? (G == 16 ? kRing16Bytes : G * ring_stride * 4) : 0);
         stage = (stage + 127) & ~127;
-        total = stage + kStages * kRows * W * 2;
+        total = stage + stages_of(G) * rows_of(G) * W * 2;
     }
 };
 
@@ -500,7 +504,7 @@ __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, 
                                               float qx, float qy, float inv_a, float base, int kt,
                                               bool use_y, float wa, float wb, float fsc,
                                               u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1, float &wsum) {
-    constexpr int E = kRows / G;
+    constexpr int E = rows_of(G) / G;
     if constexpr (E <= 4) {
         // geometry of every slot first (independent chains), then the frame loops
         Geo g[E];
@@ -754,6 +758,7 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
 template <int G, int MODE, bool EXT>
 __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __grid_constant__ LaunchGroups L) {
+    constexpr int kRows = rows_of(G), kStages = stages_of(G);
     constexpr int E = kRows / G;
     constexpr bool kTcFir = (MODE == 1 && G == 16);   // FIR on the tensor cores; whole lines only
     extern __shared__ __align__(128) unsigned char smem[];
@@ -781,8 +786,8 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
     const int te = T1 + ((MODE == 1 && seg == n_seg - 1) ? 1 : 0);
     const SmemLayout lay(G, MODE, kSlotSamples);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
-    uint64_t *empty = full + kStages;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kStages);
+    uint64_t *empty = full + kMaxStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kMaxStages);
     uint64_t *fir_bar = reinterpret_cast<uint64_t *>(smem + lay.bars + 72);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.bars + 80);
     uint64_t *ring_bar = reinterpret_cast<uint64_t *>(smem + lay.bars + 88);
