@@ -10,6 +10,8 @@ CASE: apod_train   gradient of 151552 feature rows (tcgen05 forward + backward)
       apod_features feature rows of the same frame
       mv           exact minimum variance (L = 32) of the same frame
       das3d        fused B-mode of one 32x32-line pyramid volume (3 GiB of records)
+      das3d_batch16 fused B-mode of 16 volumes of an 8x8-line pyramid in one batched call
+                   (the 16-frame kernel; 3 GiB of records)
 """
 from __future__ import annotations
 
@@ -57,6 +59,15 @@ def main(case: str) -> int:
         ch = phantom.synth_channels(s, phantom.default_phantom(s, 3000), 3000, device=dev)
         for _ in range(2):
             plan.bmode(ch)
+    elif case == "das3d_batch16":
+        s = phantom.config3(8)
+        plan = supra.Plan(**s.params())
+        batch = torch.empty((16, *plan.ch_shape), dtype=torch.int16, device=dev)
+        for k in range(16):
+            batch[k].copy_(phantom.synth_channels(s, phantom.default_phantom(s, 3000 + k), 3000 + k, device=dev))
+        outs = [torch.empty(plan.out_shape, dtype=torch.uint8, device=dev) for _ in range(16)]
+        for _ in range(2):
+            supra.bmode_batched([plan] * 16, list(batch), outs)
     else:
         raise SystemExit(f"unknown case {case!r}")
     torch.cuda.synchronize()
