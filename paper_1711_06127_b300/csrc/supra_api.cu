@@ -153,16 +153,29 @@ bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Multiprocessors of the current device (queried once per device).
+int sm_count() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cached[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+    if (dev < kMaxDev) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    if (dev < kMaxDev) cached[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 // Depth segments per line for a launch of `items` lines whose shortest line has
 // min_tiles depth tiles: a launch that leaves SMs idle (fewer lines than two
 // resident CTAs per SM) splits its lines so that the segments still fit in one
 // wave.  16-frame B-mode launches (the tensor-core FIR) keep whole lines.
 int depth_segments(int items, int min_tiles, int G, int mode) {
     if (mode == 1 && G == 16) return 1;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int slots = 2 * sms;
+    const int slots = 2 * sm_count();
     const int s = items > 0 ? slots / items : 1;
     return std::max(1, std::min(s, min_tiles));
 }
@@ -220,9 +233,7 @@ struct ScanBatch {
 
 int launch_scan(const ScanBatch &S, cudaStream_t st) {
     if (S.launch.n == 0) return SUPRA_OK;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     // linear layouts go to the separable kernel, the others to the tiled one
     ScanLaunch lin{}, gen{};
     long long lin_blocks = 1, gen_tiles = 1;
