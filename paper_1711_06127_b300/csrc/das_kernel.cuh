@@ -539,7 +539,8 @@ __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, 
 // iq = sum_k' g_k' rf(o + 31 - k'), code = floor(a2 log2|iq|^2 + b2) clamped to [0, 255]
 // (|iq|^2 = 0 gives -inf and code 0, as env = 0 does).
 __device__ __forceinline__ uint32_t code_of(float q, float a2, float b2) {
-    return (uint32_t)fminf(fmaxf(floorf(fmaf(a2, __log2f(q), b2)), 0.f), 255.f);
+    // floor with the conversion's saturation at 0 (also for -inf), after clamping at 255
+    return __float2uint_rd(fminf(fmaf(a2, __log2f(q), b2), 255.f));
 }
 
 __device__ __forceinline__ void store_codes8(uint8_t *row, int o, int nd, const uint32_t (&c)[8]) {
