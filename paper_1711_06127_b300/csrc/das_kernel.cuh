@@ -3,13 +3,15 @@
 // log-compression nodes (Sec. 2 items 3-4, Table 1 "Envelope", "Log comp.")
 // fused behind it.
 //
-// One CTA owns one scanline of a group of G frames that share a plan and
+// One CTA owns one scanline of a group of G frames that share a plan (or one
+// depth segment of it, when a launch has too few lines to fill the GPU) and
 // streams the line's depth axis in tiles of kTD = 256 samples, one consumer
 // thread per depth sample.  The CTA is warp-specialized:
 //   * warp 8 (producer) walks the tiles.  Its 32 lanes take 32 elements of the
 //     tile's aperture box at a time, bound the depths of the tile at which each
 //     element can be inside the F-number aperture, drop elements that never
-//     are, and pack the others E = 32 / G to a stage.  For each element it
+//     are, and pack the others E to a stage (3 for G = 16 in a ring of three
+//     stages; 32 / G otherwise, four stages).  For each element it
 //     stages the record window those depths read -- one of four widths (80,
 //     144, 208 or 272 samples) -- for all G frames with the TMA engine,
 //     completing on the stage's "full" mbarrier.  When the group's frames lie
@@ -43,9 +45,10 @@
 // demodulating FIR runs over it, and the log-compressed codes are written out.
 // With G = 16 the FIR runs on the tensor cores (tcgen05): within a tile it is
 // a product of one fixed banded Toeplitz matrix of taps with the ring, so the
-// taps sit in tensor memory for the whole CTA, the ring is the FP16 B operand
-// in shared memory and the accumulators come back from tensor memory; other
-// group sizes run it register-blocked on the FP32 cores.
+// taps sit in tensor memory for the whole CTA, the ring is the B operand in
+// shared memory (both split into FP16 hi + lo parts, FP32 accumulation), a
+// tenth warp issues the products and the consumers read the accumulators out
+// one tile later; other group sizes run it register-blocked on the FP32 cores.
 #pragma once
 #include <cuda_fp16.h>
 
