@@ -50,7 +50,8 @@ struct Smem {
     static constexpr int DZ1 = DZ2 + (T ? 16384 : 0);    // [pix][hid1]
     static constexpr int DZ3 = DZ1 + (T ? 16384 : 0);    // [pix][out]
     static constexpr int BIAS = DZ3 + (T ? 32768 : 0);   // float b1[64], b2[64], b3[128]
-    static constexpr int TOTAL = BIAS + 256 * 4;
+    static constexpr int X2 = BIAS + 256 * 4;            // training: the next tile's [pix][in] (+ ones)
+    static constexpr int TOTAL = X2 + (T ? 36864 : 0);
 };
 static_assert(Smem<kTrain>::TOTAL <= 227 * 1024, "training tile exceeds shared memory");
 static_assert(2 * (Smem<kInfer>::TOTAL + 1024) <= 228 * 1024, "two inference CTAs per SM");
@@ -93,6 +94,12 @@ __device__ __forceinline__ void unpack8(uint4 u, float *v) {
 __device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int row) {
     return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
 }
+// 16-byte global -> shared copy that completes asynchronously (cp.async), and its waits
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Element range of (line, depth tile): the tile's element box (conservative: elements
 // outside it are outside the aperture at every depth of the tile, their samples are 0),
@@ -163,6 +170,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     constexpr uint32_t kCols = MODE == kTrain ? 512 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar_dw1;   // training: completion of dW1 (never waited on; see below)
     __shared__ uint32_t tmem_base;
     __shared__ float red[2][NT / 32];
     __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
@@ -170,6 +178,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     const int row = t & (kTile - 1), half = t / kTile;
     if (t == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&bar_dw1, 1);
         fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
@@ -178,6 +187,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
         chunk(sm, S::X, 16, row) = ones;
         chunk(sm, S::X, 17, row) = ones;
+        chunk(sm, S::X2, 16, row) = ones;
+        chunk(sm, S::X2, 17, row) = ones;
         chunk(sm, S::H1, 8, row) = ones;
         chunk(sm, S::H1, 9, row) = ones;
         chunk(sm, S::H2, 8, row) = ones;
@@ -207,7 +218,39 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     bool ok = true, first = true;
     float loss_acc = 0.0f, cnt_acc = 0.0f;
 
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // Training: the next tile's feature rows are copied into the other X buffer (cp.async)
+    // while this tile runs; its masks, norms and labels wait in registers.  The copy into a
+    // buffer is issued after the next Z1 products complete, so the dW1 products of the tile
+    // before, which read that buffer, are complete too (one thread issues all products, and
+    // they complete in order).
+    uint32_t nmk[4] = {0u, 0u, 0u, 0u};
+    float nnrm = 0.0f, ntgt = 0.0f;
+    bool nok = false;
+    auto prefetch = [&](long long tl, int xo) {
+        const long long pp = tl * kTile + row;
+        nok = pp < a.n;
+        const long long rw = pp * a.stride;
+        if (nok) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + rw * kIn);
+#pragma unroll
+            for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) cp_async16(&chunk(sm, xo, c, row), src + c);
+            const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + rw);
+            nmk[0] = m4.x, nmk[1] = m4.y, nmk[2] = m4.z, nmk[3] = m4.w;
+            nnrm = __ldg(a.norm + rw);
+            ntgt = nnrm > 0.0f ? __ldg(a.label + rw) / nnrm : 0.0f;
+        } else {
+#pragma unroll
+            for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) chunk(sm, xo, c, row) = make_uint4(0u, 0u, 0u, 0u);
+            nmk[0] = nmk[1] = nmk[2] = nmk[3] = 0u;
+            nnrm = ntgt = 0.0f;
+        }
+        cp_async_commit();
+    };
+    if (MODE == kTrain && (long long)blockIdx.x < n_tiles) prefetch(blockIdx.x, S::X);
+
+    int iter = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
+        const int xo = (MODE == kTrain && (iter & 1)) ? S::X2 : S::X;   // this tile's X buffer
         // ---- inputs: one row of X per pixel (each half writes its chunks)
         uint32_t mk[4] = {0u, 0u, 0u, 0u};
         float nrm = 0.0f, tgt = 0.0f;
@@ -242,6 +285,13 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 chunk(sm, S::X, c, row) = pack8(v);
             }
             nrm = n2v[0] + n2v[1];   // this half's share of ||x||^2 (square root below)
+        } else if (MODE == kTrain) {
+            cp_async_wait_all();
+            p = tile * kTile + row;
+            row_ok = nok;
+            mk[0] = nmk[0], mk[1] = nmk[1], mk[2] = nmk[2], mk[3] = nmk[3];
+            nrm = nnrm;
+            tgt = ntgt;
         } else {
             p = tile * kTile + row;
             row_ok = p < a.n;
@@ -271,10 +321,11 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 
         // ---- Z1 = X W1^T
         if (t == 0) {
-            mma_chain(tm + kT64, sb + S::X, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
+            mma_chain(tm + kT64, sb + xo, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
             tc::mma_commit(&bar);
         }
         ok = mma_wait(&bar, phase) && ok;
+        if (MODE == kTrain && tile + gridDim.x < n_tiles) prefetch(tile + gridDim.x, xo == S::X ? S::X2 : S::X);
         const float scale = (MODE == kInfer) ? (nrm > 0.0f ? 1.0f / nrm : 0.0f) : 1.0f;
 #pragma unroll
         for (int q = q2; q < q2 + 2 / H; ++q) {
@@ -340,7 +391,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             float v[32], x[32];
             tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, row), x + 8 * c);
+            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
@@ -374,7 +425,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 float v[32], x[32];
                 tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::X, 4 * q + c, row), x + 8 * c);
+                for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float pe = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
@@ -443,14 +494,19 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         if (!ok) break;
         tc::fence_after_sync();
 
-        // ---- [dW1 | db1] += dZ1^T [X | 1]; complete before X and DZ1 are rewritten
+        // ---- [dW1 | db1] += dZ1^T [X | 1]; not waited for: the next tile's Z1 products complete
+        // after it (before this X buffer is refilled or DZ1 rewritten), and the final commit below
+        // covers the last tile
         if (t == 0) {
-            mma_chain(tm + kDW1, sb + S::DZ1, 128, 2048, sb + S::X, 128, 2048, tc::idesc_bf16(128, 144, true, true), 8,
+            mma_chain(tm + kDW1, sb + S::DZ1, 128, 2048, sb + xo, 128, 2048, tc::idesc_bf16(128, 144, true, true), 8,
                       !first);
-            tc::mma_commit(&bar);
+            tc::mma_commit(&bar_dw1);
         }
-        ok = mma_wait(&bar, phase) && ok;
         first = false;
+    }
+    if (MODE == kTrain && !first) {   // every product issued so far, the last dW1 included
+        if (t == 0) tc::mma_commit(&bar);
+        ok = mma_wait(&bar, phase) && ok;
     }
     ok = __syncthreads_and(ok);   // the last wait of a tile is not followed by a barrier
     if (!ok && t == 0) set_status(SUPRA_ETIMEOUT);
@@ -553,20 +609,38 @@ __global__ void __launch_bounds__(128) features_kernel(const DevPlan *__restrict
     norm[pix] = nr;
 }
 
-// grad = sum of per-CTA partials / valid-pixel count (FP64 sums in CTA order);
-// thread kParams writes the loss.
-__global__ void reduce_kernel(const float *__restrict__ partial, int n_parts, float *__restrict__ grad,
-                              float *__restrict__ loss) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > kParams) return;
-    double cnt = 0.0, s = 0.0;
-    for (int c = 0; c < n_parts; ++c) {
-        cnt += partial[(long long)c * kPartStride + kParams + 1];
-        s += partial[(long long)c * kPartStride + j];
+// grad = sum of the per-CTA partials / valid-pixel count; index kParams is the loss.
+// Sums in a fixed order, so the result does not depend on scheduling: a block takes 32
+// indices, its warp g sums partials g, g + 8, g + 16, ... of each, and the eight warp
+// sums are added in warp order.  FP32 (this GPU's FP64 rate is a small fraction of
+// its FP32 rate); the error of these short sums stays near 1e-6 of the result.
+constexpr int kReduceCols = 32, kReduceGroups = 8;
+__global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(const float *__restrict__ partial,
+                                                                            int n_parts, float *__restrict__ grad,
+                                                                            float *__restrict__ loss) {
+    __shared__ float part_sum[kReduceGroups][kReduceCols + 1];
+    __shared__ float part_cnt[kReduceGroups];
+    const int lane = threadIdx.x % kReduceCols, g = threadIdx.x / kReduceCols;
+    const int j = blockIdx.x * kReduceCols + lane;
+    float s = 0.0f, cnt = 0.0f;
+    for (int c = g; c < n_parts; c += kReduceGroups) {
+        const float *row = partial + (long long)c * kPartStride;
+        if (j <= kParams) s += row[j];
+        if (lane == 0) cnt += row[kParams + 1];
     }
-    const double v = cnt > 0.0 ? s / cnt : 0.0;
-    if (j < kParams) grad[j] = (float)v;
-    else if (loss) *loss = (float)v;
+    part_sum[g][lane] = s;
+    if (lane == 0) part_cnt[g] = cnt;
+    __syncthreads();
+    if (g == 0 && j <= kParams) {
+        float tot = 0.0f, ct = 0.0f;
+        for (int k = 0; k < kReduceGroups; ++k) {
+            tot += part_sum[k][lane];
+            ct += part_cnt[k];
+        }
+        const float v = ct > 0.0f ? tot / ct : 0.0f;
+        if (j < kParams) grad[j] = v;
+        else if (loss) *loss = v;
+    }
 }
 
 // Adam with bias correction (c1 = 1 / (1 - beta1^step), c2 = 1 / (1 - beta2^step)).

@@ -1066,7 +1066,8 @@ int supra_apod_grad(const float *params, int64_t n, int64_t stride, const uint16
     a.partial = static_cast<float *>(workspace);
     const int rc = launch_apod<apod::kTrain>(a, tiles, 1, st);
     if (rc != SUPRA_OK) return rc;
-    apod::reduce_kernel<<<(apod::kParams + 1 + 255) / 256, 256, 0, st>>>(a.partial, grid, grad, loss);
+    apod::reduce_kernel<<<(apod::kParams + 1 + apod::kReduceCols - 1) / apod::kReduceCols,
+                          apod::kReduceCols * apod::kReduceGroups, 0, st>>>(a.partial, grid, grad, loss);
     return check_cuda(cudaGetLastError());
 }
 
