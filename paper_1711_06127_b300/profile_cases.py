@@ -6,6 +6,8 @@ on the device at most.
     python -m paper_1711_06127_b300.profile_cases CASE
 
 CASE: apod_train   gradient of 151552 feature rows (tcgen05 forward + backward)
+      apod_minibatch eight training steps (gradient, reduction, Adam) of 65536-pixel
+                   minibatches of 1.57 M feature rows
       apod_infer   fused gather + network beamformer, 128 el x 256 lines x 2048 samples
       apod_features feature rows of the same frame
       mv           exact minimum variance (L = 32) of the same frame
@@ -41,6 +43,20 @@ def main(case: str) -> int:
         tr = apod.Trainer(phantom.apod_init(2, out_scale=1.0, bias_scale=0.05))
         for _ in range(2):
             tr.compute_grad(data)
+    elif case == "apod_minibatch":
+        n = 65536 * 24
+        X, mask, norm, t = phantom.apod_random_batch(1, n)
+        xh = np.divide(X, norm[:, None], out=np.zeros_like(X), where=norm[:, None] > 0)
+        words = np.stack([(mask[:, 32 * w:32 * (w + 1)].astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(1)
+                          for w in range(4)], 1).astype(np.uint32)
+        data = apod.Dataset(torch.as_tensor(xh).to(torch.bfloat16).to(dev),
+                            torch.as_tensor(words.view(np.int32)).to(dev),
+                            torch.as_tensor(norm.astype(np.float32)).to(dev),
+                            torch.as_tensor((t * norm).astype(np.float32)).to(dev))
+        tr = apod.Trainer(phantom.apod_init(2, out_scale=1.0, bias_scale=0.05))
+        for k in range(8):   # interleaved minibatches, as Trainer.epoch takes them
+            tr.compute_grad(data, k, 24)
+            tr.apply()
     elif case in ("apod_infer", "apod_features", "mv"):
         s = phantom.config2()
         plan = supra.Plan(**dict(s.params(), grid=None))
