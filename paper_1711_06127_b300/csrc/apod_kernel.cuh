@@ -126,20 +126,24 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo
 template <int MODE>
 __device__ __forceinline__ void stage_weights(const float *__restrict__ prm, unsigned char *sm, int t, int nt) {
     using S = Smem<MODE>;
+    // loads batched 8 deep, so that each thread waits for a few round trips to L2, not dozens
+#pragma unroll 8
     for (int k = t; k < kH1 * kIn; k += nt) {
         const int n = k >> 7, i = k & 127;
         *reinterpret_cast<__nv_bfloat16 *>(sm + S::W1 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
-            __float2bfloat16_rn(prm[kOffW1 + k]);
+            __float2bfloat16_rn(__ldg(prm + kOffW1 + k));
     }
+#pragma unroll 8
     for (int k = t; k < kH2 * kH1; k += nt) {
         const int n = k >> 6, i = k & 63;
         *reinterpret_cast<__nv_bfloat16 *>(sm + S::W2 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
-            __float2bfloat16_rn(prm[kOffW2 + k]);
+            __float2bfloat16_rn(__ldg(prm + kOffW2 + k));
     }
+#pragma unroll 8
     for (int k = t; k < kIn * kH2; k += nt) {
         const int n = k >> 6, i = k & 63;
         *reinterpret_cast<__nv_bfloat16 *>(sm + S::W3 + (i >> 3) * 2048 + n * 16 + (i & 7) * 2) =
-            __float2bfloat16_rn(prm[kOffW3 + k]);
+            __float2bfloat16_rn(__ldg(prm + kOffW3 + k));
     }
     float *bias = reinterpret_cast<float *>(sm + S::BIAS);
     for (int k = t; k < 256; k += nt)
