@@ -653,6 +653,18 @@ __device__ __forceinline__ void fir_tc_issue(uint32_t tbase, uint32_t ring_saddr
     tc::mma_commit(bar);
 }
 
+// The lag tile after a line's last tile has outputs t < 32 only: block 0's products.
+__device__ __forceinline__ void fir_tc_issue_block0(uint32_t tbase, uint32_t ring_saddr, uint64_t *bar) {
+    constexpr uint32_t idesc = tc::idesc_f16(128, 32, false, true);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint64_t bd = tc::smem_desc(ring_saddr + 1024u * kk, 512, 128);
+        tc::mma_f16_ta(tbase + kFirColD, tbase + 8u * kk, bd, idesc, kk > 0);
+        tc::mma_f16_ta(tbase + kFirColD, tbase + kFirColLo + 8u * kk, bd, idesc, true);
+    }
+    tc::mma_commit(bar);
+}
+
 // Warp w reads lanes 32 (w % 4) .. of blocks 2 (w / 4) and 2 (w / 4) + 1: lane j
 // holds part j / 16 of output t = 64 blk + 16 (w % 4) + j % 16 for the 16 frames
 // (the sum of a block's hi and lo columns).
@@ -972,7 +984,8 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __
                 for (int t = 0; t <= NT; ++t) {
                     if (!wait_phase(ring_bar, (uint32_t)(t & 1), abort_flag)) break;
                     tc::fence_after_sync();
-                    fir_tc_issue(tbase, ring_saddr, fir_bar);
+                    if (t < NT) fir_tc_issue(tbase, ring_saddr, fir_bar);
+                    else fir_tc_issue_block0(tbase, ring_saddr, fir_bar);
                 }
             }
             return;
