@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
 #pragma unroll
     for (int f = 0; f < kScanGroup; ++f) bm[f] = L.f[f0 + (f < nf ? f : 0)].bm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int xl = warp * 4 + c, x = xb + xl;
         const float u = (fmaf((float)x, P->gsx, P->gox) - P->u0) * P->du_inv;
