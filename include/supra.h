@@ -290,6 +290,15 @@ SUPRA_API int supra_apod_grad(const float *params, int64_t n, int64_t stride, co
 SUPRA_API int supra_apod_adam(float *params, float *m, float *v, const float *grad, int32_t step, float lr,
                               float beta1, float beta2, float eps, void *stream);
 
+/* One training step: supra_apod_grad on the given rows (grad and loss written
+ * as it writes them), then supra_apod_adam with that gradient, the gradient
+ * reduction and the update fused into one kernel.  Arguments, ownership and
+ * errors as the two calls (step counts from 1). */
+SUPRA_API int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, float beta1, float beta2,
+                              float eps, int64_t n, int64_t stride, const uint16_t *feat, const uint32_t *mask,
+                              const float *norm, const float *label, float *grad, float *loss, void *workspace,
+                              size_t workspace_bytes, void *stream);
+
 /* Learned-apodization beamformer: rf float [n_lines][n_depth] from int16
  * channels [n_tx][n_el][n_samples], delays, interpolation and aperture as in
  * supra_beamform, weights from the network (one fused kernel).

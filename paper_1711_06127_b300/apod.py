@@ -1,5 +1,5 @@
 """Learned apodization: training and evaluation driver over the C ABI
-(supra_apod_forward / supra_apod_grad / supra_apod_adam).  Argument
+(supra_apod_forward / supra_apod_grad / supra_apod_adam / supra_apod_step).  Argument
 marshalling, minibatch bookkeeping and checkpoints only; the network's
 forward and backward passes and the optimiser step run in libsupra's
 kernels.
@@ -121,6 +121,26 @@ class Trainer:
                                       self.grad.data_ptr(), self.step_count, self.lr, self.betas[0], self.betas[1],
                                       self.eps, _stream_ptr(stream)), "supra_apod_adam")
 
+    def step(self, data: Dataset, base=0, stride=1, n=None, loss_out=None, stream=None):
+        """One training step: the gradient over rows base, base + stride, ...
+        (n rows) and the Adam update, in two launches (supra_apod_step).  The
+        minibatch loss goes to loss_out (a one-element device tensor) or to
+        self.loss; self.grad holds the gradient."""
+        total = _check_rows(data.feat, data.mask, data.norm, data.label)
+        if n is None:
+            n = (total - base + stride - 1) // stride
+        if n <= 0 or base + (n - 1) * stride >= total:
+            raise ValueError("row range outside the dataset")
+        out = self.loss if loss_out is None else loss_out
+        if out.numel() < 1 or not out.is_contiguous():
+            raise ValueError("loss_out must be a contiguous device tensor of at least one element")
+        self.step_count += 1
+        _check(load().supra_apod_step(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.step_count,
+                                      self.lr, self.betas[0], self.betas[1], self.eps, int(n), int(stride),
+                                      _ptr(data.feat, base), _ptr(data.mask, base), _ptr(data.norm, base),
+                                      _ptr(data.label, base), self.grad.data_ptr(), out.data_ptr(), self.ws.data_ptr(),
+                                      self.ws.numel(), _stream_ptr(stream)), "supra_apod_step")
+
     def epoch(self, data: Dataset, n_batches: int, seed: int, stream=None) -> float:
         """One pass over the data in n_batches interleaved minibatches (order
         shuffled with `seed`); returns the mean minibatch loss."""
@@ -129,9 +149,7 @@ class Trainer:
         order = np.random.default_rng(int(seed)).permutation(int(n_batches))
         losses = torch.zeros(len(order), dtype=torch.float32, device=self.params.device)
         for j, k in enumerate(order):
-            self.compute_grad(data, int(k), int(n_batches), stream=stream)
-            losses[j : j + 1].copy_(self.loss)
-            self.apply(stream)
+            self.step(data, int(k), int(n_batches), loss_out=losses[j : j + 1], stream=stream)
         return float(losses.mean())
 
     # ---- checkpoints -----------------------------------------------------

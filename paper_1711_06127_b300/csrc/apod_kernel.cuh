@@ -647,18 +647,58 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(con
     }
 }
 
+// One parameter's Adam update with bias correction (c1 = 1 / (1 - beta1^step), c2 = 1 / (1 - beta2^step)).
+__device__ __forceinline__ void adam_update(float *p, float *m, float *v, int j, float gj, float lr, float beta1,
+                                            float beta2, float eps, float c1, float c2) {
+    const float mj = fmaf(beta1, m[j], (1.0f - beta1) * gj);
+    const float vj = fmaf(beta2, v[j], (1.0f - beta2) * gj * gj);
+    m[j] = mj;
+    v[j] = vj;
+    p[j] -= lr * (mj * c1) / (sqrtf(vj * c2) + eps);
+}
+
+// reduce_kernel followed by the Adam update of each reduced parameter (one kernel for the
+// training step's tail); the gradient and the loss are written as reduce_kernel writes them.
+__global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_adam_kernel(
+    const float *__restrict__ partial, int n_parts, float *__restrict__ grad, float *__restrict__ loss,
+    float *__restrict__ p, float *__restrict__ m, float *__restrict__ v, float lr, float beta1, float beta2, float eps,
+    float c1, float c2) {
+    __shared__ float part_sum[kReduceGroups][kReduceCols + 1];
+    __shared__ float part_cnt[kReduceGroups];
+    const int lane = threadIdx.x % kReduceCols, g = threadIdx.x / kReduceCols;
+    const int j = blockIdx.x * kReduceCols + lane;
+    float s = 0.0f, cnt = 0.0f;
+    for (int c = g; c < n_parts; c += kReduceGroups) {
+        const float *row = partial + (long long)c * kPartStride;
+        if (j <= kParams) s += row[j];
+        if (lane == 0) cnt += row[kParams + 1];
+    }
+    part_sum[g][lane] = s;
+    if (lane == 0) part_cnt[g] = cnt;
+    __syncthreads();
+    if (g == 0 && j <= kParams) {
+        float tot = 0.0f, ct = 0.0f;
+        for (int k = 0; k < kReduceGroups; ++k) {
+            tot += part_sum[k][lane];
+            ct += part_cnt[k];
+        }
+        const float gj = ct > 0.0f ? tot / ct : 0.0f;
+        if (j < kParams) {
+            grad[j] = gj;
+            adam_update(p, m, v, j, gj, lr, beta1, beta2, eps, c1, c2);
+        } else if (loss) {
+            *loss = gj;
+        }
+    }
+}
+
 // Adam with bias correction (c1 = 1 / (1 - beta1^step), c2 = 1 / (1 - beta2^step)).
 __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                             const float *__restrict__ g, int n, float lr, float beta1, float beta2, float eps, float c1,
                             float c2) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const float gj = g[j];
-    const float mj = fmaf(beta1, m[j], (1.0f - beta1) * gj);
-    const float vj = fmaf(beta2, v[j], (1.0f - beta2) * gj * gj);
-    m[j] = mj;
-    v[j] = vj;
-    p[j] -= lr * (mj * c1) / (sqrtf(vj * c2) + eps);
+    adam_update(p, m, v, j, g[j], lr, beta1, beta2, eps, c1, c2);
 }
 
 }  // namespace apod

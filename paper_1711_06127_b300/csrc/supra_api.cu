@@ -1071,6 +1071,34 @@ int supra_apod_grad(const float *params, int64_t n, int64_t stride, const uint16
     return check_cuda(cudaGetLastError());
 }
 
+int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, float beta1, float beta2, float eps,
+                    int64_t n, int64_t stride, const uint16_t *feat, const uint32_t *mask, const float *norm,
+                    const float *label, float *grad, float *loss, void *workspace, size_t workspace_bytes,
+                    void *stream) {
+    if (!params || !m || !v || !feat || !mask || !norm || !label || !grad || !workspace || n <= 0 || stride < 1 ||
+        step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps > 0.0f))
+        return SUPRA_EINVAL;
+    if (!aligned16(feat) || !aligned16(mask)) return SUPRA_EINVAL;
+    const long long tiles = (n + apod::kTile - 1) / apod::kTile;
+    const int sms = device_sms();
+    if (sms <= 0) return SUPRA_ECUDA;
+    const int grid = (int)std::min<long long>(tiles, sms);
+    if (workspace_bytes < (size_t)grid * apod::kPartStride * sizeof(float)) return SUPRA_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    apod::Args a{};
+    a.params = params, a.feat = feat, a.mask = mask, a.norm = norm, a.label = label, a.n = n, a.stride = stride;
+    a.partial = static_cast<float *>(workspace);
+    const int rc = launch_apod<apod::kTrain>(a, tiles, 1, st);
+    if (rc != SUPRA_OK) return rc;
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
+    apod::reduce_adam_kernel<<<(apod::kParams + 1 + apod::kReduceCols - 1) / apod::kReduceCols,
+                               apod::kReduceCols * apod::kReduceGroups, 0, st>>>(a.partial, grid, grad, loss, params, m,
+                                                                                 v, lr, beta1, beta2, eps, c1, c2);
+    return check_cuda(cudaGetLastError());
+}
+
 int supra_apod_adam(float *params, float *m, float *v, const float *grad, int32_t step, float lr, float beta1,
                     float beta2, float eps, void *stream) {
     if (!params || !m || !v || !grad || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||

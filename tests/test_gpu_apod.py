@@ -153,6 +153,28 @@ def test_adam_matches_the_oracle():
     np.testing.assert_allclose(tr.m.cpu().numpy(), m, rtol=1e-5, atol=1e-9)
 
 
+def test_fused_training_step_equals_gradient_then_adam():
+    # supra_apod_step (gradient, then the reduction and the Adam update in one kernel) against the
+    # two separate calls (each checked against the oracle above), over three steps of strided minibatches
+    params = phantom.apod_init(62, out_scale=1.0, bias_scale=0.1)
+    dev, *_ = _rows(63, 3000)
+    a, b = apod.Trainer(params, lr=2e-3), apod.Trainer(params, lr=2e-3)
+    losses = torch.zeros(3, dtype=torch.float32, device="cuda")
+    for k in range(3):
+        ga, la = a.compute_grad(_data(dev), base=k, stride=3)
+        la = la.clone()
+        a.apply()
+        b.step(_data(dev), base=k, stride=3, loss_out=losses[k : k + 1])
+        torch.testing.assert_close(b.grad, ga, rtol=0, atol=0)
+        assert losses[k].item() == la.item()
+        torch.testing.assert_close(b.params, a.params, rtol=0, atol=0)
+        torch.testing.assert_close(b.m, a.m, rtol=0, atol=0)
+        torch.testing.assert_close(b.v, a.v, rtol=0, atol=0)
+    assert b.step_count == 3
+    with pytest.raises(ValueError):
+        b.step(_data(dev), base=0, stride=1, n=4000)
+
+
 def test_fused_inference_matches_the_oracle():
     s = small_linear(64, 8, 700)
     p = s.params()
