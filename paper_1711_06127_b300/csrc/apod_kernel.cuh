@@ -115,6 +115,67 @@ __device__ __forceinline__ ElemBox elem_box(const DevPlan *__restrict__ P, int l
     return ElemBox{b.z * P->el_nx + b.x, b.w * P->el_nx + b.y};
 }
 
+// ---- fused beamformer: the tile's sample windows staged in shared memory.
+// Per tile (128 depths of one line, inside one 256-depth delay tile), slot j holds samples
+// [ws_j, ws_j + kWinW) of the record of element box.lo + j (zero outside the record), ws_j a
+// multiple of 8.  The window bounds the two-way delay over the tile's depths as the
+// delay-and-sum producer does (the delay at the first and last depth and, where a path has its
+// minimum inside, the sum of the paths' minima; one sample before, two after).  Elements past
+// the last slot, windows wider than kWinW, plane-wave lines and unaligned records are not
+// staged (kNoWin): their samples come from global memory, so the values are the same.
+constexpr int kWinW = 144, kWinSlots = 32768 / (kWinW * 2), kNoWin = -0x40000000;
+
+__device__ __forceinline__ int tile_window(const DevPlan *__restrict__ P, const LineGeo &lg, int e, int i_a, int i_b) {
+    const float4 xe = __ldg(&P->elem[e]);
+    const float mx = lg.ox - xe.x, my = lg.oy - xe.y, mz = lg.oz - xe.z;
+    const float beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
+    const float gamma = mx * mx + my * my + mz * mz;
+    const int tile = i_a / kTD;
+    const int kt = __ldg(&P->tile_k[tile]);
+    const float ft = __ldg(&P->tile_f[tile]);
+    const float r0 = P->depth0 + (float)i_a * P->depth_step, r1 = P->depth0 + (float)i_b * P->depth_step;
+    const float s0 = ft + P->a1 * (float)(i_a - tile * kTD) + (path_excess(r0, lg.bt, lg.gt) + path_excess(r0, beta, gamma)) * P->fsc;
+    const float s1 = ft + P->a1 * (float)(i_b - tile * kTD) + (path_excess(r1, lg.bt, lg.gt) + path_excess(r1, beta, gamma)) * P->fsc;
+    float lo = fminf(s0, s1), hi = fmaxf(s0, s1);
+    if ((-beta > r0 && -beta < r1) || (-lg.bt > r0 && -lg.bt < r1)) {
+        const float re = fminf(fmaxf(-beta, r0), r1), rt = fminf(fmaxf(-lg.bt, r0), r1);
+        const float de = sqrtf(fmaxf(fmaf(re, re + 2.0f * beta, gamma), 0.0f));
+        const float dtp = sqrtf(fmaxf(fmaf(rt, rt + 2.0f * lg.bt, lg.gt), 0.0f));
+        lo = fminf(lo, (de + dtp) * P->fsc - P->t0fs - (float)kt);
+    }
+    const int lo_i = kt + (int)floorf(lo) - 1;
+    const int ws = (lo_i >> 3) << 3;
+    const int need = kt + (int)floorf(hi) + 2 - ws;
+    return need <= kWinW ? ws : kNoWin;
+}
+
+// element_sample with the two samples read from the staged window when it holds them.
+__device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict__ P, const PixelGeo &g, int e,
+                                                       bool &act, const int16_t *win, int ws) {
+    const float4 xe = __ldg(&P->elem[e]);
+    act = fabsf((xe.x - g.qx) * g.inv_a) <= 1.0f && fabsf((xe.y - g.qy) * g.inv_a) <= 1.0f;
+    if (!act) return 0.0f;
+    const float mx = g.lg.ox - xe.x, my = g.lg.oy - xe.y, mz = g.lg.oz - xe.z;
+    const float beta = g.lg.dx * mx + g.lg.dy * my + g.lg.dz * mz;
+    const float gamma = mx * mx + my * my + mz * mz;
+    const float s = g.base + path_excess(g.r, beta, gamma) * P->fsc;
+    const float fl = floorf(s);
+    const float phi = s - fl;
+    const long long k = (long long)g.kt + (long long)fl;
+    const long long d = k - ws;
+    float x0, x1;
+    if (d >= 0 && d + 1 < kWinW) {
+        x0 = (float)win[d];
+        x1 = (float)win[d + 1];
+    } else {
+        const int n_s = P->n_s;
+        const int16_t *rec = g.rec0 + (long long)e * n_s;
+        x0 = (k >= 0 && k < n_s) ? (float)__ldg(rec + k) : 0.0f;
+        x1 = (k + 1 >= 0 && k + 1 < n_s) ? (float)__ldg(rec + k + 1) : 0.0f;
+    }
+    return fmaf(phi, x1 - x0, x0);
+}
+
 // K steps of one MMA chain, issued by one thread (2 core matrices along K per step).
 __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo, uint32_t a_sbo, uint32_t b,
                                           uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc, int ksteps, bool acc) {
@@ -178,6 +239,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     __shared__ uint32_t tmem_base;
     __shared__ float red[2][NT / 32];
     __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
+    __shared__ int win_ws[MODE == kInfer ? kWinSlots : 1];   // fused beamformer: staged window starts
     const int t = threadIdx.x, warp = t >> 5;
     const int row = t & (kTile - 1), half = t / kTile;
     if (t == 0) {
@@ -271,6 +333,36 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const ElemBox box = elem_box(a.plan, line, (int)(tile % nblk) * kTile);
             PixelGeo g;
             if (row_ok) g = pixel_geo(a.plan, a.ch, line, i);
+            // stage the box elements' sample windows of this tile in the H1/H2 bytes (free until Z1)
+            const LineGeo lgt = a.plan->lines[line];
+            const int i_a = (int)(tile % nblk) * kTile, i_b = min(i_a + kTile - 1, nd - 1);
+            const int n_slots = min(box.hi - box.lo + 1, kWinSlots);
+            const bool staged = a.plan->bulk_ok && (reinterpret_cast<uintptr_t>(a.ch) & 15) == 0 && lgt.plane == 0;
+            int16_t *win = reinterpret_cast<int16_t *>(sm + S::H1);
+            if (staged) {
+                if (t < n_slots) win_ws[t] = tile_window(a.plan, lgt, box.lo + t, i_a, i_b);
+                __syncthreads();
+                const int n_s = a.plan->n_s;
+                const int16_t *rec_base = a.ch + (long long)lgt.tx * n_el * n_s;
+                constexpr int kChunks = kWinW / 8;
+                for (int q = t; q < n_slots * kChunks; q += NT) {
+                    const int j = q / kChunks, c = q - j * kChunks;
+                    const int ws = win_ws[j];
+                    if (ws == kNoWin) continue;
+                    const int s0 = ws + 8 * c;
+                    int16_t *dst = win + j * kWinW + 8 * c;
+                    const int16_t *src = rec_base + (long long)(box.lo + j) * n_s + s0;
+                    if (s0 >= 0 && s0 + 8 <= n_s) {
+                        cp_async16(dst, src);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) dst[u] = (s0 + u >= 0 && s0 + u < n_s) ? src[u] : (int16_t)0;
+                    }
+                }
+                cp_async_commit();
+                cp_async_wait_all();
+                __syncthreads();
+            }
 #pragma unroll 1
             for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) {
                 if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
@@ -282,7 +374,14 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 for (int j = 0; j < 8; ++j) {
                     const int e = 8 * c + j;
                     bool act = false;
-                    v[j] = (row_ok && e < n_el && box.has(e)) ? element_sample(a.plan, g, e, act) : 0.0f;
+                    if (row_ok && e < n_el && box.has(e)) {
+                        const int jw = e - box.lo;
+                        v[j] = (staged && jw < n_slots && win_ws[jw] != kNoWin)
+                                   ? element_sample_staged(a.plan, g, e, act, win + jw * kWinW, win_ws[jw])
+                                   : element_sample(a.plan, g, e, act);
+                    } else {
+                        v[j] = 0.0f;
+                    }
                     n2v[j & 1] = fmaf(v[j], v[j], n2v[j & 1]);
                     if (act) mk[e >> 5] |= 1u << (e & 31);
                 }
