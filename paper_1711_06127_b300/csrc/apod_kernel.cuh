@@ -125,11 +125,14 @@ __device__ __forceinline__ ElemBox elem_box(const DevPlan *__restrict__ P, int l
 // staged (kNoWin): their samples come from global memory, so the values are the same.
 constexpr int kWinW = 144, kWinSlots = 32768 / (kWinW * 2), kNoWin = -0x40000000;
 
-__device__ __forceinline__ int tile_window(const DevPlan *__restrict__ P, const LineGeo &lg, int e, int i_a, int i_b) {
+// Also returns the element's receive terms beta = d.(o - x_e), gamma = |o - x_e|^2 (per line and
+// element, shared by the tile's pixels).
+__device__ __forceinline__ int tile_window(const DevPlan *__restrict__ P, const LineGeo &lg, int e, int i_a, int i_b,
+                                           float &beta, float &gamma) {
     const float4 xe = __ldg(&P->elem[e]);
     const float mx = lg.ox - xe.x, my = lg.oy - xe.y, mz = lg.oz - xe.z;
-    const float beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
-    const float gamma = mx * mx + my * my + mz * mz;
+    beta = lg.dx * mx + lg.dy * my + lg.dz * mz;
+    gamma = mx * mx + my * my + mz * mz;
     const int tile = i_a / kTD;
     const int kt = __ldg(&P->tile_k[tile]);
     const float ft = __ldg(&P->tile_f[tile]);
@@ -149,15 +152,14 @@ __device__ __forceinline__ int tile_window(const DevPlan *__restrict__ P, const 
     return need <= kWinW ? ws : kNoWin;
 }
 
-// element_sample with the two samples read from the staged window when it holds them.
+// element_sample with the element's receive terms given and the two samples read from the
+// staged window when it holds them.
 __device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict__ P, const PixelGeo &g, int e,
-                                                       bool &act, const int16_t *win, int ws) {
+                                                       bool &act, const int16_t *win, int ws, float beta,
+                                                       float gamma) {
     const float4 xe = __ldg(&P->elem[e]);
     act = fabsf((xe.x - g.qx) * g.inv_a) <= 1.0f && fabsf((xe.y - g.qy) * g.inv_a) <= 1.0f;
     if (!act) return 0.0f;
-    const float mx = g.lg.ox - xe.x, my = g.lg.oy - xe.y, mz = g.lg.oz - xe.z;
-    const float beta = g.lg.dx * mx + g.lg.dy * my + g.lg.dz * mz;
-    const float gamma = mx * mx + my * my + mz * mz;
     const float s = g.base + path_excess(g.r, beta, gamma) * P->fsc;
     const float fl = floorf(s);
     const float phi = s - fl;
@@ -240,6 +242,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     __shared__ float red[2][NT / 32];
     __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
     __shared__ int win_ws[MODE == kInfer ? kWinSlots : 1];   // fused beamformer: staged window starts
+    __shared__ float win_bg[MODE == kInfer ? kWinSlots : 1][2];   // and the elements' beta, gamma
     const int t = threadIdx.x, warp = t >> 5;
     const int row = t & (kTile - 1), half = t / kTile;
     if (t == 0) {
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const bool staged = a.plan->bulk_ok && (reinterpret_cast<uintptr_t>(a.ch) & 15) == 0 && lgt.plane == 0;
             int16_t *win = reinterpret_cast<int16_t *>(sm + S::H1);
             if (staged) {
-                if (t < n_slots) win_ws[t] = tile_window(a.plan, lgt, box.lo + t, i_a, i_b);
+                if (t < n_slots) win_ws[t] = tile_window(a.plan, lgt, box.lo + t, i_a, i_b, win_bg[t][0], win_bg[t][1]);
                 __syncthreads();
                 const int n_s = a.plan->n_s;
                 const int16_t *rec_base = a.ch + (long long)lgt.tx * n_el * n_s;
@@ -377,7 +380,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                     if (row_ok && e < n_el && box.has(e)) {
                         const int jw = e - box.lo;
                         v[j] = (staged && jw < n_slots && win_ws[jw] != kNoWin)
-                                   ? element_sample_staged(a.plan, g, e, act, win + jw * kWinW, win_ws[jw])
+                                   ? element_sample_staged(a.plan, g, e, act, win + jw * kWinW, win_ws[jw],
+                                                           win_bg[jw][0], win_bg[jw][1])
                                    : element_sample(a.plan, g, e, act);
                     } else {
                         v[j] = 0.0f;
