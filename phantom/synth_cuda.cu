@@ -7,23 +7,27 @@
 //   sum over (scatterer p, transmit t) pairs of
 //     a_p * exp(-(k/fs - T)^2 / (2 s^2)) * cos(2 pi fc (k/fs - T)),  |k/fs - T| <= half,
 //   T = (|p - o_t| + |p - x_e|) / c  (a plane-wave transmit of direction n: n.(p - o_t) + |p - x_e|),
-// with a_p already including the transmit-beam weight.  One CTA accumulates 8
-// elements of one transmit in shared memory.
+// with a_p already including the transmit-beam weight.  One CTA accumulates 4
+// elements of one transmit in shared memory, in 32.32 fixed point with integer
+// atomics: each term is rounded to a multiple of 2^-32 and integer sums do not
+// depend on the order the threads add them in, so the records are the same bits
+// on every run.
 #include <cuda_runtime.h>
 #include <math.h>
 
 namespace {
 
-constexpr int kElems = 8;
+constexpr int kElems = 4;
+constexpr float kFix = 4294967296.0f;   // 2^32
 
 __global__ void __launch_bounds__(256) echo_kernel(int n_el, int n_s, const float *__restrict__ elem,
                                                    const float *__restrict__ tx_origin,
                                                    const float *__restrict__ tx_dir, const int *__restrict__ start,
                                                    const float4 *__restrict__ pairs, float c, float fs, float fc,
                                                    float sig, float half, int J, float *__restrict__ out) {
-    extern __shared__ float acc[];   // [kElems][n_s]
+    extern __shared__ unsigned long long acc[];   // [kElems][n_s], two's complement 32.32 fixed point
     const int t = blockIdx.x, e0 = blockIdx.y * kElems;
-    for (int k = threadIdx.x; k < kElems * n_s; k += blockDim.x) acc[k] = 0.0f;
+    for (int k = threadIdx.x; k < kElems * n_s; k += blockDim.x) acc[k] = 0ull;
     __syncthreads();
     const float ox = tx_origin[3 * t], oy = tx_origin[3 * t + 1], oz = tx_origin[3 * t + 2];
     // plane-wave transmit (unit direction, zero for a spherical wave from the origin)
@@ -45,14 +49,16 @@ __global__ void __launch_bounds__(256) echo_kernel(int n_el, int n_s, const floa
                 if (k < 0 || k >= n_s) continue;
                 const float dt = (float)k / fs - T;
                 if (fabsf(dt) > half) continue;
-                atomicAdd(&acc[j * n_s + k], q.w * expf(-dt * dt * inv2s2) * cosf(w * dt));
+                const float v = q.w * expf(-dt * dt * inv2s2) * cosf(w * dt);
+                atomicAdd(&acc[j * n_s + k], (unsigned long long)llrintf(v * kFix));
             }
         }
     }
     __syncthreads();
     for (int j = 0; j < kElems && e0 + j < n_el; ++j) {
         float *dst = out + ((long long)t * n_el + e0 + j) * n_s;
-        for (int k = threadIdx.x; k < n_s; k += blockDim.x) dst[k] = acc[j * n_s + k];
+        for (int k = threadIdx.x; k < n_s; k += blockDim.x)
+            dst[k] = (float)((double)(long long)acc[j * n_s + k] * (1.0 / 4294967296.0));
     }
 }
 
@@ -67,7 +73,7 @@ extern "C" __attribute__((visibility("default"))) int phantom_echoes(int n_tx, i
                                                                      const float *pairs, float c, float fs, float fc,
                                                                      float sig, float half, int J, float *out,
                                                                      void *stream) {
-    const size_t smem = sizeof(float) * kElems * (size_t)n_s;
+    const size_t smem = sizeof(unsigned long long) * kElems * (size_t)n_s;
     if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
     cudaFuncSetAttribute(echo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(n_tx, (n_el + kElems - 1) / kElems);
