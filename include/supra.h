@@ -449,6 +449,21 @@ SUPRA_API int supra_bmode_noalloc(const supra_plan *plan, const int16_t *ch, uin
  * negative SUPRA_E* code of the first failure.  Synchronizes the device. */
 SUPRA_API int supra_device_status(int32_t clear);
 
+/* Self-test of the bounded device waits that every kernel's mbarrier waits use.
+ * Launches one CTA of 96 threads on the current device (default stream) whose
+ * mbarrier never completes (nothing arrives on it):
+ *   - thread 0 waits with a budget of budget_cycles SM clock cycles;
+ *   - thread 32 waits as the beamforming kernel's stage consumers do, giving up
+ *     when the CTA's abort word is raised, which thread 64 does after
+ *     budget_cycles cycles of its own (bounded spin on clock64).
+ * Both waits give up, set the device status word to SUPRA_ETIMEOUT and return;
+ * the context stays usable (read and clear the word with supra_device_status).
+ * budget_cycles: 1 << 10 .. 1 << 31.  out_host (host, may be NULL): int32[2],
+ * element k = 1 where wait k reported the timeout.  Returns SUPRA_OK,
+ * SUPRA_EINVAL (budget out of range, before any CUDA call) or SUPRA_ECUDA.
+ * Synchronizes the device. */
+SUPRA_API int supra_selftest_bounded_wait(int64_t budget_cycles, int32_t *out_host);
+
 /* Static description of a return code. */
 SUPRA_API const char *supra_strerror(int code);
 

@@ -30,7 +30,7 @@ EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "su
            "supra_render", "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode", "supra_server_create",
            "supra_server_submit", "supra_server_submit_trace", "supra_server_poll", "supra_server_wait",
            "supra_server_release", "supra_server_get_stats", "supra_server_now", "supra_server_destroy",
-           "supra_device_status", "supra_strerror", "supra_version")
+           "supra_selftest_bounded_wait", "supra_device_status", "supra_strerror", "supra_version")
 APOD_PARAMS, APOD_INPUTS = 20736, 128
 
 
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_autotune_bmode.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.c_size_t,
                                          ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_float)]
+    lib.supra_selftest_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
     lib.supra_device_status.argtypes = [ctypes.c_int32]
     lib.supra_strerror.argtypes = [ctypes.c_int]
     lib.supra_strerror.restype = ctypes.c_char_p
@@ -428,6 +429,15 @@ def render(vol, grid: dict, camera: dict, width: int, height: int, mode: str = "
 def device_status(clear: bool = True) -> int:
     """Device-side failure code since the last clear (0 = none); synchronizes."""
     return int(load().supra_device_status(1 if clear else 0))
+
+
+def selftest_bounded_wait(budget_cycles: int = 1 << 20) -> tuple:
+    """Runs the bounded-wait self-test (an mbarrier that never completes, waited on
+    with a cycle budget and with the abort-word path); returns the two waits' timeout
+    flags.  The device status word is left at ETIMEOUT for the caller to read."""
+    out = (ctypes.c_int32 * 2)()
+    _check(load().supra_selftest_bounded_wait(int(budget_cycles), out), "supra_selftest_bounded_wait")
+    return int(out[0]), int(out[1])
 
 
 def version() -> str:

@@ -278,6 +278,36 @@ void ScanBatch::add(const supra_plan *p, const uint8_t *bm, uint8_t *img) {
     launch.f[launch.n++] = ScanFrame{p->dev, bm, img};
 }
 
+// One CTA, 96 threads: two waits on an mbarrier that never completes (see
+// supra_selftest_bounded_wait).
+__global__ void __launch_bounds__(96) bounded_wait_selftest_kernel(long long budget, int *out) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_word;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_word = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    volatile int *abort_flag = &abort_word;
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait_bounded(&bar, 0u, budget);
+        out[0] = ok ? 0 : 1;
+        if (!ok) set_status(SUPRA_ETIMEOUT);
+    } else if (threadIdx.x == 32) {
+        const bool ok = wait_phase(&bar, 0u, abort_flag);
+        out[1] = ok ? 0 : 1;
+        if (!ok) set_status(SUPRA_ETIMEOUT);
+    } else if (threadIdx.x == 64) {
+        const long long t0 = clock64();
+        while (clock64() - t0 <= budget) {
+        }
+        *abort_flag = 1;
+    }
+}
+
+__device__ int g_selftest[2];
+
 }  // namespace
 
 // ---------------------------------------------------------------- learned-apodization launch helpers
@@ -1118,6 +1148,22 @@ int supra_apod_mlp(const supra_plan *plan, const float *params, const int16_t *c
     a.params = params, a.plan = plan->dev, a.ch = ch, a.rf = rf;
     const long long tiles = (long long)plan->host.n_lines * ((plan->host.n_depth + apod::kTile - 1) / apod::kTile);
     return launch_apod<apod::kInfer>(a, tiles, 2, static_cast<cudaStream_t>(stream));
+}
+
+int supra_selftest_bounded_wait(int64_t budget_cycles, int32_t *out_host) {
+    if (budget_cycles < (1LL << 10) || budget_cycles > (1LL << 31)) return SUPRA_EINVAL;
+    int *d = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void **>(&d), g_selftest) != cudaSuccess) return SUPRA_ECUDA;
+    if (cudaMemset(d, 0, 2 * sizeof(int)) != cudaSuccess) return SUPRA_ECUDA;
+    bounded_wait_selftest_kernel<<<1, 96>>>((long long)budget_cycles, d);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return SUPRA_ECUDA;
+    int h[2] = {0, 0};
+    if (cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return SUPRA_ECUDA;
+    if (out_host) {
+        out_host[0] = h[0];
+        out_host[1] = h[1];
+    }
+    return SUPRA_OK;
 }
 
 int supra_device_status(int32_t clear) {

@@ -107,3 +107,9 @@ def test_null_arguments_are_rejected(lib):
     assert lib.supra_plan_get_info(None, None) == supra.EINVAL
     assert lib.supra_bmode_workspace_size(0, None) == 0
     lib.supra_plan_destroy(None)
+
+
+def test_selftest_budget_out_of_range_is_rejected_before_any_cuda_call(lib):
+    assert lib.supra_selftest_bounded_wait(0, None) == supra.EINVAL
+    assert lib.supra_selftest_bounded_wait(1 << 9, None) == supra.EINVAL
+    assert lib.supra_selftest_bounded_wait((1 << 31) + 1, None) == supra.EINVAL
