@@ -191,16 +191,23 @@ class ClockSampler:
                 "samples": len(self.samples), "source": src}
 
 
+def kernel_source_hash():
+    """Hash of the beamforming kernel's source and the library's compiler flags."""
+    from paper_1711_06127_b300 import build
+
+    src = os.path.join(ROOT, "paper_1711_06127_b300", "csrc", "das_kernel.cuh")
+    return hashlib.sha256(open(src, "rb").read() + " ".join(build.CFLAGS).encode()).hexdigest()[:16]
+
+
 def kernel_traffic():
     """DRAM traffic per launch of the beamforming kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+    summary, only if it was taken on the current kernel source and flags."""
     path = os.path.join(ROOT, "profiles", "das_kernel_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1711_06127_b300", "csrc", "das_kernel.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     if rec.get("source_sha256_16") != h:
         return None
     return rec.get("bytes_per_launch_full_workload")

@@ -14,6 +14,11 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsupra.so")
 SOURCES = ["supra_api.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# -ftz=true: FP32 subnormals flush to zero, so the approximate intrinsics (rsqrt, reciprocal,
+# cos, log2, exp) compile without their subnormal rescaling steps.  No FP32 value of the
+# chain is subnormal (squared distances are clamped at 1e-30, weights and samples are far
+# from 1e-38), and the outputs on the workloads are the same bits as without the flag.
+CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true"]
 
 
 def nvcc() -> str:
@@ -34,7 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(f) <= t for f in _deps()):
             return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), *ARCH, *CFLAGS, "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "-shared", "-I", INCLUDE, "-I", CSRC,
            "-o", LIB + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES], "-lcudart"]
     if verbose:
