@@ -525,14 +525,27 @@ __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, 
             wsum += g[ej].w;
         }
     } else {
-#pragma unroll 2
-        for (int ej = 0; ej < E; ++ej) {
-            const ElemMeta md = meta[ej];
-            if (!meta_valid(md)) break;   // valid slots are a prefix
-            const Geo g = element_geo(md, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc);
-            if (!g.go) continue;
-            element_frames_w<G>(sbuf + ej * G * kSlotSamples, meta_widx(md), g, acc2, acc1);
-            wsum += g.w;
+        // groups of four slots: their geometry first (independent chains), then their samples;
+        // valid slots are a prefix, and an invalid slot's `go` is false
+        constexpr int kGrp = 4;
+        static_assert(E % kGrp == 0, "slot groups");
+#pragma unroll 1
+        for (int e0 = 0; e0 < E; e0 += kGrp) {
+            if (!meta_valid(meta[e0])) break;
+            Geo g[kGrp];
+            int widx[kGrp];
+#pragma unroll
+            for (int j = 0; j < kGrp; ++j) {
+                const ElemMeta md = meta[e0 + j];
+                widx[j] = meta_widx(md);
+                g[j] = element_geo(md, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc);
+            }
+#pragma unroll
+            for (int j = 0; j < kGrp; ++j) {
+                if (!g[j].go) continue;
+                element_frames_w<G>(sbuf + (e0 + j) * G * kSlotSamples, widx[j], g[j], acc2, acc1);
+                wsum += g[j].w;
+            }
         }
     }
 }
