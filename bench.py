@@ -234,9 +234,26 @@ def cpu_oracle_rate(s, chs_host, budget_s=12.0, max_frames=None):
         if el >= budget_s or (max_frames and done >= max_frames):
             break
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def das_rate(fn, budget):
+        n, t1 = 0, time.perf_counter()
+        while True:
+            fn(p, chs_host[n % len(chs_host)])
+            n += 1
+            e = time.perf_counter() - t1
+            if e >= budget:
+                return per_frame * n / e, n, e
+
+    # beside the chain: the beamforming node alone, the FP64 oracle loops and the same loops in FP32
+    r64, n64, e64 = das_rate(oracle.das, budget_s / 4)
+    r32, n32, e32 = das_rate(oracle.das_f32, budget_s / 4)
     return {"value": per_frame * done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{done} whole frame(s) of the 128-element/256-line/2048-sample workload through the "
-                      f"FP64 oracle chain (DAS in C/OpenMP, envelope/log/scan conversion in numpy), {el:.1f} s"}
+                      f"FP64 oracle chain (DAS in C/OpenMP, envelope/log/scan conversion in numpy), {el:.1f} s",
+            "das_only": {"fp64": {"value": r64, "unit": UNIT, "frames": n64, "seconds": e64},
+                         "fp32": {"value": r32, "unit": UNIT, "frames": n32, "seconds": e32},
+                         "note": "receive delay-and-sum alone on whole frames, same C/OpenMP loops in FP64 "
+                                 "(the oracle) and FP32 (a timing reference, not an oracle)"}}
 
 
 def run_reference(args):

@@ -12,6 +12,7 @@ states no formula for any of them, so every function here is the textbook
 definition of the named step, written out plainly:
 
   das           receive delay-and-sum beamforming           (oracle.c, C + OpenMP)
+  das_f32       the same loops in FP32: a CPU timing column beside the oracle, not an oracle
   fir_taps      windowed-sinc low-pass (Blackman), unit DC gain
   envelope      IQ demodulation: mix with exp(-j 2 pi fc t), low-pass, 2|iq|
   logcompress   20 log10(env/ref) mapped from [-D, 0] dB to [0, 255], half-up rounding
@@ -55,6 +56,7 @@ def lib():
         path = _build.build()
         _lib = ctypes.CDLL(path)
         _lib.oracle_das.argtypes = [ctypes.POINTER(_Geom), ctypes.c_void_p, ctypes.c_void_p]
+        _lib.oracle_das_f32.argtypes = [ctypes.POINTER(_Geom), ctypes.c_void_p, ctypes.c_void_p]
         _lib.oracle_das_points.argtypes = [ctypes.POINTER(_Geom), ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib.oracle_aperture.argtypes = [ctypes.POINTER(_Geom), ctypes.c_int32, ctypes.c_int32,
@@ -100,6 +102,18 @@ def das(p: dict, ch) -> np.ndarray:
     assert ch.shape == (g.tx.shape[0], g.elem.shape[0], int(p["n_samples"])), ch.shape
     rf = np.zeros((g.lo.shape[0], int(p["n_depth"])), dtype=np.float64)
     lib().oracle_das(g.ref, ch.ctypes.data, rf.ctypes.data)
+    return rf
+
+
+def das_f32(p: dict, ch) -> np.ndarray:
+    """The delay-and-sum loops of `das` in single precision (oracle.c,
+    oracle_das_f32): a CPU timing reference beside the FP64 oracle, not an
+    oracle.  rf float32 [n_lines, n_depth]."""
+    ch = np.ascontiguousarray(np.asarray(ch), dtype=np.int16)
+    g = Geometry(p)
+    assert ch.shape == (g.tx.shape[0], g.elem.shape[0], int(p["n_samples"])), ch.shape
+    rf = np.zeros((g.lo.shape[0], int(p["n_depth"])), dtype=np.float32)
+    lib().oracle_das_f32(g.ref, ch.ctypes.data, rf.ctypes.data)
     return rf
 
 

@@ -191,6 +191,89 @@ void oracle_das(const or_geom *g, const int16_t *ch, double *rf)
     }
 }
 
+/*
+ * The same delay-and-sum loops in single precision, for a CPU timing column
+ * beside the FP64 oracle (the two differ only in the precision of the
+ * arithmetic).  It is a timing reference, not an oracle: tests compare it with
+ * oracle_das within single-precision rounding.
+ */
+static float window_at_f(int window, float u)
+{
+    const float pi = 3.14159265358979f;
+    if (window == OR_WINDOW_HANN) return 0.5f * (1.0f + cosf(pi * u));
+    if (window == OR_WINDOW_HAMMING) return 0.54f + 0.46f * cosf(pi * u);
+    return 1.0f;
+}
+
+static float das_point_tx_f(const or_geom *g, const float *elem, const float ext[4], const int16_t *ch_tx,
+                            int32_t t, int32_t line, int32_t i)
+{
+    const double *od = g->line_origin + 3 * line, *dd = g->line_dir + 3 * line;
+    const float r = (float)g->depth0 + (float)i * (float)g->depth_step;
+    float p[3], q[2];
+    for (int k = 0; k < 3; ++k) p[k] = (float)od[k] + r * (float)dd[k];
+    q[0] = p[0] < ext[0] ? ext[0] : (p[0] > ext[1] ? ext[1] : p[0]);
+    q[1] = p[1] < ext[2] ? ext[2] : (p[1] > ext[3] ? ext[3] : p[1]);
+    float a = p[2] / (2.0f * (float)g->fnumber);
+    if (a < (float)g->min_half_aperture) a = (float)g->min_half_aperture;
+    const double *ot = g->tx_origin + 3 * t;
+    float tx_path;
+    if (g->tx_dir && (g->tx_dir[3 * t] != 0.0 || g->tx_dir[3 * t + 1] != 0.0 || g->tx_dir[3 * t + 2] != 0.0)) {
+        const double *n = g->tx_dir + 3 * t;
+        const float len = sqrtf((float)(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]));
+        tx_path = ((float)n[0] * (p[0] - (float)ot[0]) + (float)n[1] * (p[1] - (float)ot[1]) +
+                   (float)n[2] * (p[2] - (float)ot[2])) / len;
+    } else {
+        const float dx = p[0] - (float)ot[0], dy = p[1] - (float)ot[1], dz = p[2] - (float)ot[2];
+        tx_path = sqrtf(dx * dx + dy * dy + dz * dz);
+    }
+    const float inv_c = 1.0f / (float)g->c, fs = (float)g->fs, t0 = (float)g->t0;
+    float num = 0.0f, den = 0.0f;
+    for (int e = 0; e < g->n_el; ++e) {
+        const float *x = elem + 3 * e;
+        const float ux = (x[0] - q[0]) / a, uy = (x[1] - q[1]) / a;
+        if (fabsf(ux) > 1.0f || fabsf(uy) > 1.0f) continue;
+        const float w = window_at_f(g->window, ux) * window_at_f(g->window, uy);
+        const float dx = p[0] - x[0], dy = p[1] - x[1], dz = p[2] - x[2];
+        const float s = ((tx_path + sqrtf(dx * dx + dy * dy + dz * dz)) * inv_c - t0) * fs;
+        const float k = floorf(s);
+        const float phi = s - k;
+        const long j = (long)k;
+        const int16_t *rec = ch_tx + (long)e * g->n_s;
+        const float v0 = (j >= 0 && j < g->n_s) ? (float)rec[j] : 0.0f;
+        const float v1 = (j + 1 >= 0 && j + 1 < g->n_s) ? (float)rec[j + 1] : 0.0f;
+        num += w * ((1.0f - phi) * v0 + phi * v1);
+        den += w;
+    }
+    return den > 0.0f ? num / den : 0.0f;
+}
+
+void oracle_das_f32(const or_geom *g, const int16_t *ch, float *rf)
+{
+    double extd[4];
+    array_extent(g, extd);
+    const float ext[4] = {(float)extd[0], (float)extd[1], (float)extd[2], (float)extd[3]};
+    float *elem = (float *)malloc(sizeof(float) * 3 * (size_t)(g->n_el > 0 ? g->n_el : 1));
+    if (!elem) return;
+    for (int k = 0; k < 3 * g->n_el; ++k) elem[k] = (float)g->elem[k];
+    long rec_tx = (long)g->n_el * g->n_s;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t l = 0; l < g->n_lines; ++l) {
+        for (int32_t i = 0; i < g->n_depth; ++i) {
+            float v;
+            if (g->compound) {
+                v = 0.0f;
+                for (int32_t t = 0; t < g->n_tx; ++t) v += das_point_tx_f(g, elem, ext, ch + rec_tx * t, t, l, i);
+                v /= (float)g->n_tx;
+            } else {
+                v = das_point_tx_f(g, elem, ext, ch + rec_tx * g->line_tx[l], g->line_tx[l], l, i);
+            }
+            rf[(long)l * g->n_depth + i] = v;
+        }
+    }
+    free(elem);
+}
+
 /* Selected points only: point k is (lines[k], depths[k]); its transmit
  * event's records are at ch_tx[k] ([n_el][n_s]).  Used for sampled checks of
  * frames too large for a full CPU pass (one transmit per line: no

@@ -195,3 +195,13 @@ def test_compounding_averages_the_transmits():
     rec = np.zeros((3,) + ch.shape[1:], np.int16)
     rec[2] = ch[0]
     np.testing.assert_allclose(oracle.das(dict(p, compound=1), rec), one[2] / 3.0, rtol=1e-12, atol=1e-9)
+
+
+def test_fp32_timing_variant_matches_the_oracle_within_single_precision():
+    """oracle_das_f32 runs the oracle's loops in single precision (a CPU timing
+    reference): its frame agrees with the FP64 oracle to single-precision rounding."""
+    s = small_linear(32, 24, 700)
+    ch = phantom.synth_channels(s, phantom.default_phantom(s, 11), 11).numpy()
+    a = oracle.das(s.params(), ch)
+    b = oracle.das_f32(s.params(), ch).astype(np.float64)
+    assert np.abs(a - b).max() <= 5e-4 * np.abs(a).max()
