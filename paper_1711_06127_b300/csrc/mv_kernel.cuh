@@ -24,8 +24,10 @@ template <typename T>
 __host__ __device__ constexpr int mv_warps() { return sizeof(T) == 8 ? 4 : 8; }   // pixels per CTA (one per warp); static smem < 48 KB
 constexpr int kMvMaxL = 32;
 
+// FP32: four CTAs per SM (registers capped at 64; the factorisation is a chain of dependent
+// steps per warp, so resident warps, not registers, bound it)
 template <typename T>
-__global__ void __launch_bounds__(mv_warps<T>() * 32) mv_kernel(const DevPlan *__restrict__ P,
+__global__ void __launch_bounds__(mv_warps<T>() * 32, sizeof(T) == 8 ? 1 : 4) mv_kernel(const DevPlan *__restrict__ P,
                                                                 const int16_t *__restrict__ ch, float *__restrict__ rf,
                                                                 int Lreq, float loading) {
     constexpr int kMvWarps = mv_warps<T>();
