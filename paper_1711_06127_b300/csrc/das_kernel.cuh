@@ -785,8 +785,10 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // -------------------------------------------------------------------------------------------------
 // MODE 0: write RF (float [n_lines][n_depth] per frame).
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
-template <int G, int MODE, bool EXT>
-__global__ void __launch_bounds__(das_threads<G, MODE>(), 2) das_kernel(const __grid_constant__ LaunchGroups L) {
+// MINB: resident CTAs per SM the registers are sized for (3 only for one-frame launches with
+// at least three CTAs per SM of work; their shared memory allows it)
+template <int G, int MODE, bool EXT, int MINB = 2>
+__global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const __grid_constant__ LaunchGroups L) {
     constexpr int kRows = rows_of(G), kStages = stages_of(G);
     constexpr int E = kRows / G;
     constexpr bool kTcFir = (MODE == 1 && G == 16);   // FIR on the tensor cores; whole lines only

@@ -183,13 +183,13 @@ int depth_segments(int items, int min_tiles, int G, int mode) {
 // kernel choice for a frame group size
 int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
 
-template <int G, int MODE, bool EXT>
+template <int G, int MODE, bool EXT, int MINB = 2>
 int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
     // the shared-memory opt-in is set once per device (it outlives the call)
     constexpr int kMaxDev = 64;
     static std::atomic<int> ready[kMaxDev];
     const SmemLayout lay(G, MODE, kSlotSamples);
-    auto kern = das_kernel<G, MODE, EXT>;
+    auto kern = das_kernel<G, MODE, EXT, MINB>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SUPRA_ECUDA;
     if (dev >= kMaxDev || ready[dev].load(std::memory_order_acquire) == 0) {
@@ -206,7 +206,14 @@ int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
 
 template <bool EXT>
 int launch_das_c(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
-    if (G == 1) return mode == 0 ? launch_das_t<1, 0, EXT>(L, st) : launch_das_t<1, 1, EXT>(L, st);
+    if (G == 1) {
+        // one frame per CTA: three resident CTAs per SM (fewer registers) when the launch has
+        // work for them, e.g. the many lines of a volume; two otherwise, so that a launch of
+        // fewer CTAs than three per SM still spreads over all SMs
+        const bool three = (long long)L.total_lines * std::max(L.n_seg, 1) >= 3LL * sm_count();
+        if (three) return mode == 0 ? launch_das_t<1, 0, EXT, 3>(L, st) : launch_das_t<1, 1, EXT, 3>(L, st);
+        return mode == 0 ? launch_das_t<1, 0, EXT>(L, st) : launch_das_t<1, 1, EXT>(L, st);
+    }
     if (mode == 0) return SUPRA_EINVAL;
     switch (G) {
         case 2: return launch_das_t<2, 1, EXT>(L, st);
