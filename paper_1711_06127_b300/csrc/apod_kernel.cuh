@@ -476,12 +476,21 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             tc::mma_commit(&bar);
         }
         ok = mma_wait(&bar, phase) && ok;
-        // reductions over this thread's outputs in 4 independent partials (latency, not order, matters)
+        // reductions over this thread's outputs in 4 independent partials (latency, not order, matters).
+        // Training reads its two 32-column blocks in one tensor-memory round trip per pass.
+        constexpr bool kPair = MODE == kTrain && 4 / H == 2;
+        float vv[kPair ? 2 : 1][32];
+        auto load_pair = [&]() {
+            if constexpr (kPair) tc::tmem_ld32x2(tm + lane + kT128 + 32 * q4, tm + lane + kT128 + 32 * (q4 + 1), vv[0], vv[1]);
+        };
         float zm4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        load_pair();
 #pragma unroll
-        for (int q = q4; q < q4 + 4 / H; ++q) {
-            float v[32];
-            tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
+        for (int k = 0; k < 4 / H; ++k) {
+            const int q = q4 + k;
+            float vl[32];
+            if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
+            const float *v = kPair ? vv[k] : vl;
 #pragma unroll
             for (int j = 0; j < 32; ++j)
                 if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], v[j] + b3[32 * q + j]);
@@ -493,10 +502,13 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             zmax = fmaxf(xrow[0][0][row], xrow[0][1][row]);
         }
         float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        load_pair();
 #pragma unroll
-        for (int q = q4; q < q4 + 4 / H; ++q) {
-            float v[32], x[32];
-            tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
+        for (int k = 0; k < 4 / H; ++k) {
+            const int q = q4 + k;
+            float vl[32], x[32];
+            if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
+            const float *v = kPair ? vv[k] : vl;
 #pragma unroll
             for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
@@ -527,19 +539,22 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 cnt_acc += valid ? 1.0f : 0.0f;
             }
             const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f;
+            load_pair();
 #pragma unroll
-            for (int q = q4; q < q4 + 4 / H; ++q) {
-                float v[32], x[32];
-                tc::tmem_ld32(tm + lane + kT128 + 32 * q, v);
+            for (int k = 0; k < 4 / H; ++k) {
+                const int q = q4 + k;
+                float vl[32], x[32], dz[32];
+                if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
+                const float *v = kPair ? vv[k] : vl;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float pe = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
-                    v[j] = pe * (x[j] - yh) * g;
+                    dz[j] = pe * (x[j] - yh) * g;
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = pack8(v + 8 * c);
+                for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = pack8(dz + 8 * c);
             }
         }
         tc::fence_async_smem();
