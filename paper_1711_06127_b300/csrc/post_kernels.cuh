@@ -301,8 +301,13 @@ __global__ void __launch_bounds__(256) scanconvert_kernel(const __grid_constant_
 // time, so both lines it interpolates are read within one or two cache lines per
 // load; the tiles go through shared memory so that rows are written out
 // coalesced.  Same arithmetic as scan_coords / lerp_lines.
+// When the tile's lines and depths fit (kLinStageLines lines, kLinStageRow bytes a line), the
+// CTA first copies them from every frame into shared memory with 16-byte loads (each line's
+// bytes from the 16-byte boundary at or below its first depth) and interpolates from there.
+constexpr int kLinStageLines = 20, kLinStageRow = 288;
 __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_constant__ ScanLaunch L) {
     __shared__ uint8_t tile[kScanGroup][64][33];
+    __shared__ __align__(16) uint8_t stg[kScanGroup][kLinStageLines][kLinStageRow];
     const int f0 = L.g0[blockIdx.y], nf = L.gn[blockIdx.y];
     const DevPlan *P = L.f[f0].plan;
     const int nx = P->gnx, nz = P->gnz, nlx = P->lines_x, nd = P->n_depth;
@@ -313,6 +318,68 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
 #pragma unroll
     for (int f = 0; f < kScanGroup; ++f) bm[f] = L.f[f0 + (f < nf ? f : 0)].bm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the lines and depths this tile reads (the clamped maps are monotonic in x and z)
+    int lo_l, hi_l, lo_d, hi_d;
+    {
+        int ia, ib, da, db;
+        float fr;
+        lerp_axis((fmaf((float)xb, P->gsx, P->gox) - P->u0) * P->du_inv, nlx, ia, fr);
+        lerp_axis((fmaf((float)min(xb + 31, nx - 1), P->gsx, P->gox) - P->u0) * P->du_inv, nlx, ib, fr);
+        lerp_axis((fmaf((float)zb, P->gsz, P->goz) - P->apz - P->v0) * P->dv_inv, nd, da, fr);
+        lerp_axis((fmaf((float)min(zb + 63, nz - 1), P->gsz, P->goz) - P->apz - P->v0) * P->dv_inv, nd, db, fr);
+        lo_l = min(ia, ib), hi_l = min(max(ia, ib) + 1, nlx - 1);
+        lo_d = min(da, db), hi_d = min(max(da, db) + 1, nd - 1);
+    }
+    const long long frame_bytes = (long long)nlx * nd;
+    bool staged = hi_l - lo_l + 1 <= kLinStageLines && hi_d - lo_d + 1 + 15 <= kLinStageRow && (frame_bytes & 15) == 0;
+#pragma unroll
+    for (int f = 0; f < kScanGroup; ++f) staged = staged && (reinterpret_cast<uintptr_t>(bm[f]) & 15) == 0;
+    if (staged) {
+        const int nL = hi_l - lo_l + 1, nC = (hi_d - lo_d + 1 + 15 + 15) >> 4;   // 16-byte chunks a line
+        for (int k = threadIdx.x; k < nf * nL * nC; k += blockDim.x) {
+            const int f = k / (nL * nC), r = k - f * (nL * nC), l = r / nC, c = r - l * nC;
+            const long long a = (((long long)(lo_l + l) * nd + lo_d) & ~15LL) + 16 * c;
+            if (a < frame_bytes)   // chunks past the frame's last byte are never read
+                *reinterpret_cast<uint4 *>(&stg[f][l][16 * c]) = __ldg(reinterpret_cast<const uint4 *>(bm[f] + a));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int xl = warp * 4 + c, x = xb + xl;
+            const float u = (fmaf((float)x, P->gsx, P->gox) - P->u0) * P->du_inv;
+            const bool in_u = x < nx && u >= -kInsideEps && u <= (float)(nlx - 1) + kInsideEps;
+            int ix;
+            float fx;
+            lerp_axis(u, nlx, ix, fx);
+            const int ix1 = ix + 1 < nlx ? ix + 1 : ix;
+            // byte of depth lo_d of line l in its staged row: (l nd + lo_d) mod 16
+            const int o0 = (int)(((long long)ix * nd + lo_d) & 15) - lo_d;
+            const int o1 = (int)(((long long)ix1 * nd + lo_d) & 15) - lo_d;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int zl = h * 32 + lane, z = zb + zl;
+                const float rz = fmaf((float)z, P->gsz, P->goz) - P->apz;
+                const float v = (rz - P->v0) * P->dv_inv;
+                const bool in = in_u && z < nz && v >= -kInsideEps && v <= (float)(nd - 1) + kInsideEps;
+                int iv;
+                float fv;
+                lerp_axis(v, nd, iv, fv);
+                const int dv = iv + 1 < nd ? 1 : 0;
+#pragma unroll
+                for (int f = 0; f < kScanGroup; ++f) {
+                    uint8_t out = 0;
+                    if (in && f < nf) {
+                        const uint8_t *b0 = &stg[f][ix - lo_l][o0 + iv];
+                        const uint8_t *b1 = &stg[f][ix1 - lo_l][o1 + iv];
+                        const float c0 = fmaf(fv, (float)b0[dv] - (float)b0[0], (float)b0[0]);
+                        const float c1 = fmaf(fv, (float)b1[dv] - (float)b1[0], (float)b1[0]);
+                        out = (uint8_t)fminf(fmaxf(floorf(fmaf(fx, c1 - c0, c0) + 0.5f), 0.0f), 255.0f);
+                    }
+                    tile[f][zl][xl] = out;
+                }
+            }
+        }
+    } else {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int xl = warp * 4 + c, x = xb + xl;
@@ -345,6 +412,7 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
                 tile[f][zl][xl] = out;
             }
         }
+    }
     }
     __syncthreads();
     // per frame, 64 rows x 32 bytes: thread -> (row, 8-byte chunk)
