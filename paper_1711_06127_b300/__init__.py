@@ -17,7 +17,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsupra.so")
+# SUPRA_LIBRARY selects another build of the library (the checked test variant,
+# libsupra_checked.so); by default the in-tree libsupra.so.
+LIB_PATH = os.environ.get("SUPRA_LIBRARY") or os.path.join(_HERE, "libsupra.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EINTERNAL, EWORKSPACE = 0, -1, -2, -3, -4, -5, -6
 WINDOWS = {"rect": 0, "hann": 1, "hamming": 2}

@@ -1,6 +1,6 @@
 """Build libsupra.so in-tree with nvcc for sm_103a (B300).
 
-    python -m paper_1711_06127_b300.build [--force]
+    python -m paper_1711_06127_b300.build [--force] [--checked]
 """
 import os
 import shutil
@@ -12,6 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsupra.so")
+LIB_CHECKED = os.path.join(HERE, "libsupra_checked.so")   # test variant: -DSUPRA_CHECKED
 SOURCES = ["supra_api.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: FP32 subnormals flush to zero, so the approximate intrinsics (rsqrt, reciprocal,
@@ -34,20 +35,24 @@ def _deps():
     return files
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Builds libsupra.so, or with checked=True the test variant libsupra_checked.so whose
+    kernels check their index and alignment invariants (SUPRA_CHECK) and report a failure
+    as SUPRA_EINTERNAL."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(f) <= t for f in _deps()):
-            return LIB
-    cmd = [nvcc(), *ARCH, *CFLAGS, "-Xcompiler", "-fPIC",
+            return lib
+    cmd = [nvcc(), *ARCH, *CFLAGS, *(["-DSUPRA_CHECKED"] if checked else []), "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "-shared", "-I", INCLUDE, "-I", CSRC,
-           "-o", LIB + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES], "-lcudart"]
+           "-o", lib + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES], "-lcudart"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -113,6 +113,20 @@ __device__ int g_status = 0;
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
 
+// Checked build (-DSUPRA_CHECKED, a test variant of the library): SUPRA_CHECK(cond) is false, and
+// the device status word records SUPRA_EINTERNAL, when an index or alignment invariant fails; the
+// caller then skips the access.  The default build compiles every check out (the condition is not
+// evaluated).
+#ifdef SUPRA_CHECKED
+__device__ __forceinline__ bool supra_check(bool ok) {
+    if (!ok) set_status(SUPRA_EINTERNAL);
+    return ok;
+}
+#define SUPRA_CHECK(cond) supra_check(cond)
+#else
+#define SUPRA_CHECK(cond) true
+#endif
+
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

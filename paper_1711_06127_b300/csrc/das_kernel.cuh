@@ -402,6 +402,8 @@ __device__ __forceinline__ uint32_t stage_element(const ProdConst &C, const Fram
                                                   int e, const ElemMeta &m, int16_t *slot_base, uint64_t *full) {
     const int wsamp = width_of(meta_widx(m));
     if (fg.tma) {
+        // the tensor map counts sample pairs: x = ws / 2 must be 16-byte aligned (ws % 8 == 0)
+        if (!SUPRA_CHECK((m.ws & 7) == 0)) return 0u;
         tma_load_4d(slot_base, &fg.tmap[meta_widx(m)], m.ws >> 1, e, tx, 0, full);
         return (uint32_t)(G * wsamp * 2);
     }
@@ -417,7 +419,9 @@ __device__ __forceinline__ uint32_t stage_element(const ProdConst &C, const Fram
             for (int k = max(c1, c0) - ws; k < wsamp; ++k) row[k] = 0;
         }
         if (fg.bulk) {
-            if (c1 > c0) {
+            if (c1 > c0 &&
+                SUPRA_CHECK(((reinterpret_cast<uintptr_t>(row + (c0 - ws)) | reinterpret_cast<uintptr_t>(fg.ch[f] + rec + c0) |
+                              (uintptr_t)((c1 - c0) * 2)) & 15) == 0)) {
                 fence_proxy_async_smem();
                 bulk_g2s(row + (c0 - ws), fg.ch[f] + rec + c0, (uint32_t)(c1 - c0) * 2u, full);
                 total += (uint32_t)(c1 - c0) * 2u;
@@ -456,6 +460,11 @@ __device__ __forceinline__ Geo element_geo(const ElemMeta &md, int i, float r, f
     const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);            // |p - x_e| + r
     const float s = fmaf(__fdividef(num, den), fsc, base);
     const float fl = floorf(s);
+#ifdef SUPRA_CHECKED
+    // every sample pair an in-aperture depth reads lies inside the element's staged window
+    const int raw = kt + (int)fl - md.ws;
+    SUPRA_CHECK(!in || !meta_valid(md) || (raw >= 0 && raw + 1 < width_of(meta_widx(md))));
+#endif
     g.w = w;
     g.w1 = w * (s - fl);
     g.w0 = w - g.w1;

@@ -368,7 +368,9 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
 #pragma unroll
                 for (int f = 0; f < kScanGroup; ++f) {
                     uint8_t out = 0;
-                    if (in && f < nf) {
+                    if (in && f < nf &&
+                        SUPRA_CHECK(ix >= lo_l && ix1 - lo_l < kLinStageLines && o0 + iv >= 0 && o1 + iv >= 0 &&
+                                    o0 + iv + dv < kLinStageRow && o1 + iv + dv < kLinStageRow)) {
                         const uint8_t *b0 = &stg[f][ix - lo_l][o0 + iv];
                         const uint8_t *b1 = &stg[f][ix1 - lo_l][o1 + iv];
                         const float c0 = fmaf(fv, (float)b0[dv] - (float)b0[0], (float)b0[0]);
