@@ -166,8 +166,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Wait for a phase, giving up after ~budget cycles or when another thread has
-// flagged an abort.
 // try_wait that lets the thread sleep (up to ~20 us) until the phase completes,
 // so waiting warps do not take issue slots from working ones.
 __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
@@ -182,6 +180,8 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
     return ok != 0;
 }
 
+// Wait for a phase, giving up after ~2^31 cycles or when another thread has
+// flagged an abort.
 __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     if (mbar_try_wait_sleep(bar, parity)) return true;
     const long long t0 = clock64();
@@ -566,19 +566,6 @@ __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, 
 __device__ __forceinline__ uint32_t code_of(float q, float a2, float b2) {
     // floor with the conversion's saturation at 0 (also for -inf), after clamping at 255
     return __float2uint_rd(fminf(fmaf(a2, __log2f(q), b2), 255.f));
-}
-
-__device__ __forceinline__ void store_codes8(uint8_t *row, int o, int nd, const uint32_t (&c)[8]) {
-    if (o >= 0 && o + 8 <= nd && (reinterpret_cast<uintptr_t>(row + o) & 7) == 0) {
-        uint2 v;
-        v.x = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
-        v.y = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
-        *reinterpret_cast<uint2 *>(row + o) = v;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (o + j >= 0 && o + j < nd) row[o + j] = (uint8_t)c[j];
-    }
 }
 
 // ---- G = 16: the FIR on the tensor cores.  Per 64-output block b of the tile,
