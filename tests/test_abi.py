@@ -36,6 +36,28 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_every_declared_symbol():
+    """The checked test variant (-DSUPRA_CHECKED) has the same ABI."""
+    path = build.build(checked=True)
+    checked = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(checked, name), name
+    assert checked.supra_selftest_bounded_wait(0, None) == supra.EINVAL
+
+
+def test_library_override_selects_another_build():
+    """SUPRA_LIBRARY points the binding at another build of the library."""
+    import subprocess
+    import sys
+
+    path = build.build(checked=True)
+    code = "import paper_1711_06127_b300 as s; print(s.LIB_PATH)"
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, SUPRA_LIBRARY=path),
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == path
+
+
 def test_strerror_and_version(lib):
     assert supra.strerror(0) == "ok"
     assert supra.strerror(supra.EINVAL) == "invalid argument"
