@@ -22,11 +22,18 @@ correction.
 
 Precision.  The method's products are BF16 x BF16 with FP32 accumulation.
 With bf16=True the oracle rounds every product operand to BF16 (round to
-nearest even) exactly where the method defines one -- weights, the layer
-inputs h1 and h2, and the output gradients dz, dz2, dz1 -- and keeps FP64 for
-everything else, so the ReLU decisions are taken on the same values as the
-kernels take them.  Biases, softmax, loss and Adam are never rounded.  With
-bf16=False (default) everything is FP64.
+nearest even) exactly where the method defines one -- weights, the network
+input xh, the layer inputs h1 and h2, and the output gradients dz, dz2, dz1 --
+and keeps FP64 for everything else, so the ReLU decisions are taken on the same
+values as the kernels take them.  Biases, softmax, loss and Adam are never
+rounded.  With bf16=False (default) everything is FP64.  Two readings fix where
+a rounding sits:
+  * the network's input operand is the normalised xh = x / ||x|| rounded to
+    BF16, in training and in inference alike (one network function);
+  * the loss is a mean, i.e. a sum over pixels divided by their count n: the
+    BF16 output-gradient operand of a pixel is the derivative of that pixel's
+    squared error, 2 (yh - t) w (x - yh), and 1/n scales the FP32 sums, so no
+    per-pixel operand depends on how many pixels share the minibatch.
 """
 from __future__ import annotations
 
@@ -80,18 +87,14 @@ def features(p: dict, ch_tx, line: int, i: int):
     return x, mask
 
 
-def forward(params, X, mask, bf16: bool = False, x_scale=None):
+def forward(params, X, mask, bf16: bool = False):
     """Network on a batch: X[B,128] normalised inputs xh, mask[B,128].
-    x_scale[B] (optional): X holds unnormalised samples and xh = X * x_scale,
-    applied after the first product (the fused beamformer's form).
     Returns (yh[B], w[B,128], cache); yh = sum_e w_e X_e."""
     P = unpack(params)
     X = _q(X, bf16)
     mask = np.asarray(mask, bool)
     W1, W2, W3 = (_q(P[k], bf16) for k in ("W1", "W2", "W3"))
     z1 = X @ W1.T
-    if x_scale is not None:
-        z1 = z1 * np.asarray(x_scale, np.float64)[:, None]
     z1 = z1 + P["b1"]
     h1 = _q(np.maximum(z1, 0.0), bf16)
     z2 = h1 @ W2.T + P["b2"]
@@ -168,17 +171,11 @@ def batch(p: dict, ch, labels=None, lines=None, depths=None):
 
 
 def beamform(p: dict, ch, params, lines=None, depths=None, bf16: bool = False) -> np.ndarray:
-    """Learned-apodization output y = sum_e w_e x_e at the selected pixels,
-    [len(lines), len(depths)].  With bf16=True the raw samples x enter the
-    first product in BF16 and 1 / ||x|| scales its result (the fused
-    beamformer's form); y = sum_e w_e bf16(x_e)."""
+    """Learned-apodization output y = ||x|| sum_e w_e xh_e = sum_e w_e x_e at
+    the selected pixels, [len(lines), len(depths)].  With bf16=True the network
+    input is xh rounded to BF16, as in training."""
     lines = list(range(len(p["line_tx"]))) if lines is None else list(lines)
     depths = list(range(int(p["n_depth"]))) if depths is None else list(depths)
     X, mask, norm, _ = batch(p, ch, None, lines, depths)
-    if bf16:
-        raw = X * norm[:, None]
-        inv = np.divide(1.0, norm, out=np.zeros_like(norm), where=norm > 0)
-        y, _, _ = forward(params, raw, mask, True, x_scale=inv)
-        return y.reshape(len(lines), len(depths))
-    yh, _, _ = forward(params, X, mask)
+    yh, _, _ = forward(params, X, mask, bf16)
     return (yh * norm).reshape(len(lines), len(depths))

@@ -157,11 +157,16 @@ def test_bf16_mode_rounds_operands_only():
     np.testing.assert_array_equal(ca[1], cb[1])
 
 
-def test_unnormalised_input_with_scale_equals_normalised_input():
-    params = phantom.apod_init(15, out_scale=1.0, bias_scale=0.1)
-    X, mask, norm, _ = phantom.apod_random_batch(16, 30)
-    Xh = X.astype(np.float64) / norm[:, None]
-    yh, w, _ = apod.forward(params, Xh, mask)
-    y, w2, _ = apod.forward(params, X.astype(np.float64), mask, x_scale=1.0 / norm)
-    np.testing.assert_allclose(w2, w, rtol=1e-10, atol=1e-14)
-    np.testing.assert_allclose(y, yh * norm, rtol=1e-10)
+def test_beamform_scales_with_the_records():
+    # the network sees xh = x / ||x||: records scaled by two give the same weights (the
+    # power-of-two scale leaves xh and its BF16 rounding unchanged) and twice the output
+    s = phantom.linear_setup(24, 0.3e-3, 3, 300, fc=5e6, fs=40e6)
+    p = s.params()
+    ch = phantom.random_channels(s, 17, amplitude=4000).numpy()
+    params = phantom.apod_init(18, out_scale=2.0, bias_scale=0.1)
+    lines, depths = [0, 1, 2], list(range(0, 300, 7))
+    for bf16 in (False, True):
+        y1 = apod.beamform(p, ch, params, lines, depths, bf16=bf16)
+        y2 = apod.beamform(p, 2 * ch, params, lines, depths, bf16=bf16)
+        assert np.any(y1 != 0)
+        np.testing.assert_array_equal(y2, 2 * y1)
