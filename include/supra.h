@@ -432,11 +432,15 @@ SUPRA_API void supra_server_destroy(supra_server *s);
  * framework's pool.  It runs the same kernels as supra_bmode, taking the
  * scratch for the frame's log-compressed lines from a fixed 8 MiB array in the
  * library's device memory, and allocates nothing.
- *   - Frames whose n_lines * n_depth exceeds 8 MiB (8388608 bytes) are
- *     rejected with SUPRA_EINVAL before anything is launched.
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture.
+ *   - Frames whose workspace, supra_bmode_workspace_size(1, &plan), exceeds
+ *     8 MiB (8388608 bytes) are rejected with SUPRA_EINVAL before anything is
+ *     launched.  That is n_lines * n_depth bytes for one-band plans; plans
+ *     with frequency compounding (n_bands > 1) also need two FP32 RF-sized
+ *     buffers (9 bytes per line sample), so their frames may be 1/9 as large.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and keeps it for that device's context; make that
+ *     first call before any stream capture.  After a device reset the next
+ *     call looks it up again (it also counts as a first call).
  *   - Every call on a device uses the same array and leaves its contents
  *     behind; calls whose work overlaps on the GPU (different streams, host
  *     threads) race on it and must be ordered by the caller.  No part of the

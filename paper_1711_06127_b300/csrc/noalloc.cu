@@ -9,6 +9,7 @@
 // another framework's pool that this library cannot reach.  This entry point
 // takes its scratch from a fixed array in the library's own device memory
 // instead, and otherwise runs exactly the kernels supra_bmode runs.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -24,25 +25,63 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;   // context the address belongs to (0: unknown)
+    void *ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context (0 if the driver cannot
+// tell), through the runtime's driver entry points (no libcuda link).  A device
+// reset destroys the primary context and the next one gets a new id, so an
+// address looked up in the old context is never reused.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(p);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 // Device address of the scratch array on the current device.  In host code the
 // array's name only stands for the symbol, so its address has to be asked for
-// once per device with that device current.
+// once per device (and context) with that device current.
 int scratch_on_current_device(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SUPRA_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return SUPRA_EINVAL;
+    // (0 when no context is current yet: the address is then looked up again, which makes
+    // the primary context current, and cached from the next call on)
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr &s = g_scratch[dev];
+    if (!s.ptr || s.ctx_id != ctx || ctx == 0) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return SUPRA_ECUDA;
         }
-        g_scratch_ptr[dev] = p;
+        s.ptr = p;
+        s.ctx_id = ctx;
     }
-    *out = g_scratch_ptr[dev];
+    *out = s.ptr;
     return SUPRA_OK;
 }
 
