@@ -24,6 +24,17 @@ template <typename T>
 __host__ __device__ constexpr int mv_warps() { return sizeof(T) == 8 ? 4 : 8; }   // pixels per CTA (one per warp); static smem < 48 KB
 constexpr int kMvMaxL = 32;
 
+__device__ __forceinline__ float inv_sqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double inv_sqrt(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ void load4(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+
 // FP32: four CTAs per SM (registers capped at 64; the factorisation is a chain of dependent
 // steps per warp, so resident warps, not registers, bound it)
 template <typename T>
@@ -33,6 +44,7 @@ __global__ void __launch_bounds__(mv_warps<T>() * 32, sizeof(T) == 8 ? 1 : 4) mv
     constexpr int kMvWarps = mv_warps<T>();
     __shared__ float xs[kMvWarps][kMvMaxM];
     __shared__ T Rm[kMvWarps][kMvMaxL][kMvMaxL + 1];
+    __shared__ __align__(16) T Cb[kMvWarps][2][kMvMaxL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int line = blockIdx.y;
     const int i = blockIdx.x * kMvWarps + warp;
@@ -122,39 +134,58 @@ __global__ void __launch_bounds__(mv_warps<T>() * 32, sizeof(T) == 8 ? 1 : 4) mv
         if (lane < L && j < L) rr[j] = R[lane][j] + (j == lane ? delta : (T)0);
         else rr[j] = (j == lane) ? (T)1 : (T)0;
     }
-    // Cholesky R = G G^T, lane i keeps row i of G in rr[0..i]
+    // Cholesky R = G G^T, lane i keeps row i of G in rr[0..i] and lane k the reciprocal
+    // 1 / G[k][k] (multiplications instead of divisions in the factorisation and both
+    // solves).  Column k reaches the lanes through a per-warp shared buffer (double
+    // buffered), read four entries at a time.
     bool bad = false;
+    T dinv = (T)1;
+    T *colbuf = Cb[warp][0];
 #pragma unroll
     for (int k = 0; k < kMvMaxL; ++k) {
         const T dkk = __shfl_sync(0xffffffffu, rr[k], k);
         bad |= !(dkk > (T)0);
-        const T gkk = sqrt(dkk > (T)0 ? dkk : (T)1);
-        if (lane == k) rr[k] = gkk;
-        else if (lane > k) rr[k] = rr[k] / gkk;
+        const T ginv = inv_sqrt(dkk > (T)0 ? dkk : (T)1);
+        if (lane == k) {
+            rr[k] = dkk * ginv;
+            dinv = ginv;
+        } else if (lane > k) {
+            rr[k] *= ginv;
+        }
+        if (k + 1 < kMvMaxL) {
+            T *col = colbuf + (k & 1) * kMvMaxL;
+            col[lane] = rr[k];
+            __syncwarp();
 #pragma unroll
-        for (int j = k + 1; j < kMvMaxL; ++j) {
-            const T gjk = __shfl_sync(0xffffffffu, rr[k], j);
-            if (lane >= j) rr[j] -= rr[k] * gjk;
+            for (int jb = (k + 1) & ~3; jb < kMvMaxL; jb += 4) {
+                T g4[4];
+                load4(col + jb, g4);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = jb + t;
+                    if (j > k && lane >= j) rr[j] -= rr[k] * g4[t];
+                }
+            }
         }
     }
     // forward G y = b (b = 1 on the first L dimensions)
     T yv = 0, sacc = 0;
 #pragma unroll
     for (int j = 0; j < kMvMaxL; ++j) {
-        if (lane == j) yv = ((j < L ? (T)1 : (T)0) - sacc) / rr[j];
+        if (lane == j) yv = ((j < L ? (T)1 : (T)0) - sacc) * dinv;
         const T yj = __shfl_sync(0xffffffffu, yv, j);
         if (lane > j) sacc += rr[j] * yj;
     }
-    // backward G^T z = y with G from shared memory
+    // backward G^T z = y with G from shared memory (the diagonal as its reciprocal)
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < kMvMaxL; ++j)
-        if (j <= lane) R[lane][j] = rr[j];
+        if (j <= lane) R[lane][j] = j == lane ? dinv : rr[j];
     __syncwarp();
     T zv = 0, tacc = 0;
 #pragma unroll
     for (int j = kMvMaxL - 1; j >= 0; --j) {
-        if (lane == j) zv = (yv - tacc) / R[j][j];
+        if (lane == j) zv = (yv - tacc) * R[j][j];
         const T zj = __shfl_sync(0xffffffffu, zv, j);
         if (lane < j) tacc += R[j][lane] * zj;
     }
