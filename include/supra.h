@@ -331,19 +331,54 @@ SUPRA_API int supra_render(const supra_grid *grid, const uint8_t *vol, const sup
                            void *stream);
 
 /* ------------------------------------------------------------------------
- * Tuning.  Frames of one plan that are adjacent in a batch share a DAS tile
- * (frames x 256 depths x 1 line) of up to max_group frames: larger tiles
- * share the delay and weight arithmetic across frames, smaller ones expose
- * more tiles to the 148 SMs.  Set before the plan is shared across threads.
+ * Tuning (no counterpart in the paper, whose nodes have fixed launch
+ * shapes).  A plan carries the tile shape its frames are beamformed with:
+ *   frames_per_group    1, 2, 4, 8 or 16: frames of one plan that are adjacent
+ *                       in a batch share a DAS tile (frames x 256 depths x 1
+ *                       line) -- larger tiles share the delay and weight
+ *                       arithmetic across frames, smaller ones expose more
+ *                       tiles to the SMs;
+ *   elements_per_stage, stages
+ *                       16-frame groups: element windows per staging-ring
+ *                       stage and ring depth, 3 x 3 (default) or 2 x 4;
+ *   depth_segments      0 = automatic (lines split along depth so that a
+ *                       launch with few lines fills one wave), k >= 1: k
+ *                       segments per line (1 = whole lines), at most 64;
+ *                       16-frame groups always keep whole lines;
+ *   ctas_per_sm         one-frame launches: 0 = automatic, 2 or 3 resident
+ *                       CTAs per SM (registers sized for that many).
+ * A batched launch that mixes plans takes depth_segments and ctas_per_sm from
+ * its first frame's plan.  Set before the plan is shared across threads.
  * ------------------------------------------------------------------------ */
+typedef struct supra_tile_shape {
+    int32_t frames_per_group;
+    int32_t elements_per_stage;
+    int32_t stages;
+    int32_t depth_segments;
+    int32_t ctas_per_sm;
+} supra_tile_shape;
+
+/* SUPRA_EINVAL for a value outside the lists above. */
+SUPRA_API int supra_plan_set_tile_shape(supra_plan *plan, const supra_tile_shape *shape);
+SUPRA_API int supra_plan_get_tile_shape(const supra_plan *plan, supra_tile_shape *shape);
+/* frames_per_group alone (the other settings unchanged). */
 SUPRA_API int supra_plan_set_max_group(supra_plan *plan, int32_t max_group);   /* 1, 2, 4, 8 or 16 */
 SUPRA_API int32_t supra_plan_get_max_group(const supra_plan *plan);
 
 /* Autotuner: times supra_bmode_batched of n frames of `plan` (device
- * pointers as for supra_bmode_batched; outputs are overwritten) for each
- * frames-per-tile class with CUDA events on `stream` (reps timed calls after
- * one warm-up each), keeps the fastest in the plan and returns it with its
- * time per call.  Synchronizes the stream. */
+ * pointers as for supra_bmode_batched; outputs are overwritten) with CUDA
+ * events on `stream` (reps timed calls after one warm-up each) for the shape
+ * in effect and then for each frames-per-group class crossed with the
+ * settings its launches use (stage shapes of 16-frame groups; depth segments
+ * 0, 1, 2, 4, 8 of the others; CTAs per SM 0, 2, 3 of one-frame launches),
+ * keeps the fastest shape in the plan and returns it with its time per call
+ * and the time of the shape in effect before (start_ms; may be NULL).  The
+ * outputs do not depend on the shape.  Synchronizes the stream; on an error
+ * the plan keeps its shape. */
+SUPRA_API int supra_autotune_tile_shape(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out,
+                                        void *workspace, size_t workspace_bytes, int32_t reps, void *stream,
+                                        supra_tile_shape *best, float *best_ms, float *start_ms);
+/* The same search, returning only the frames-per-group class it picked. */
 SUPRA_API int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out,
                                    void *workspace, size_t workspace_bytes, int32_t reps, void *stream,
                                    int32_t *best_group, float *best_ms);

@@ -29,7 +29,8 @@ EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "su
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
            "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_apod_features", "supra_apod_forward",
            "supra_apod_workspace_size", "supra_apod_grad", "supra_apod_adam", "supra_apod_step", "supra_apod_mlp",
-           "supra_render", "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode", "supra_server_create",
+           "supra_render", "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode",
+           "supra_plan_set_tile_shape", "supra_plan_get_tile_shape", "supra_autotune_tile_shape", "supra_server_create",
            "supra_server_submit", "supra_server_submit_trace", "supra_server_poll", "supra_server_wait",
            "supra_server_release", "supra_server_get_stats", "supra_server_now", "supra_server_destroy",
            "supra_selftest_bounded_wait", "supra_device_status", "supra_strerror", "supra_version")
@@ -64,6 +65,11 @@ class _Rx(ctypes.Structure):
 class _Post(ctypes.Structure):
     _fields_ = [("fir_taps", ctypes.c_int32), ("fir_cutoff", ctypes.c_double), ("dyn_range_db", ctypes.c_double),
                 ("log_ref", ctypes.c_double), ("n_bands", ctypes.c_int32), ("band_step", ctypes.c_double)]
+
+
+class _TileShape(ctypes.Structure):
+    _fields_ = [("frames_per_group", ctypes.c_int32), ("elements_per_stage", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("depth_segments", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class _Grid(ctypes.Structure):
@@ -131,6 +137,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_autotune_bmode.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.c_size_t,
                                          ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_float)]
+    lib.supra_plan_set_tile_shape.argtypes = [P, ctypes.POINTER(_TileShape)]
+    lib.supra_plan_get_tile_shape.argtypes = [P, ctypes.POINTER(_TileShape)]
+    lib.supra_autotune_tile_shape.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P), P,
+                                              ctypes.c_size_t, ctypes.c_int32, P, ctypes.POINTER(_TileShape),
+                                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.supra_selftest_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
     lib.supra_device_status.argtypes = [ctypes.c_int32]
     lib.supra_strerror.argtypes = [ctypes.c_int]
@@ -346,6 +357,40 @@ class Plan:
         return feat, mask, norm
 
     # ---- tuning ------------------------------------------------------------
+    @property
+    def tile_shape(self) -> dict:
+        s = _TileShape()
+        _check(load().supra_plan_get_tile_shape(self.handle, ctypes.byref(s)), "supra_plan_get_tile_shape")
+        return {k: int(getattr(s, k)) for k, _ in _TileShape._fields_}
+
+    @tile_shape.setter
+    def tile_shape(self, shape: dict):
+        cur = self.tile_shape
+        cur.update(shape)
+        s = _TileShape(**{k: int(v) for k, v in cur.items()})
+        _check(load().supra_plan_set_tile_shape(self.handle, ctypes.byref(s)), "supra_plan_set_tile_shape")
+
+    def autotune_shape(self, chs, outs=None, workspace=None, reps=3, stream=None):
+        """Times the fused chain on these frames (device tensors of this plan)
+        for the shape in effect and each candidate tile shape, keeps the
+        fastest; returns (shape, ms, ms of the shape in effect before)."""
+        import torch
+
+        n = len(chs)
+        outs = [torch.empty(self.out_shape, dtype=torch.uint8, device=c.device) for c in chs] if outs is None else outs
+        need = workspace_size([self] * n)
+        if need and workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=chs[0].device)
+        PA = ctypes.c_void_p * n
+        ca = PA(*[_dev_tensor(c, torch.int16, self.ch_shape, "ch") for c in chs])
+        oa = PA(*[_dev_tensor(o, torch.uint8, self.out_shape, "out") for o in outs])
+        s, ms, ms0 = _TileShape(), ctypes.c_float(), ctypes.c_float()
+        _check(load().supra_autotune_tile_shape(self.handle, n, ca, oa,
+                                                workspace.data_ptr() if workspace is not None else None, need,
+                                                int(reps), _stream_ptr(stream), ctypes.byref(s), ctypes.byref(ms),
+                                                ctypes.byref(ms0)), "supra_autotune_tile_shape")
+        return {k: int(getattr(s, k)) for k, _ in _TileShape._fields_}, float(ms.value), float(ms0.value)
+
     @property
     def max_group(self) -> int:
         return int(load().supra_plan_get_max_group(self.handle))

@@ -64,10 +64,12 @@ constexpr int kCtaThreads = 288;     // + one producer warp
 template <int G, int MODE>
 __host__ __device__ constexpr int das_threads() { return (MODE == 1 && G == 16) ? kCtaThreads + 32 : kCtaThreads; }
 // Rows (frame rows of E = rows / G elements) per stage and stages in the ring: 16-frame
-// groups stage 3 elements per stage in 3 stages (fewer hand-overs per element), the
-// others 32 rows (E <= 32 producer lanes) in 4.
-__host__ __device__ constexpr int rows_of(int G) { return G == 16 ? 48 : 32; }
-__host__ __device__ constexpr int stages_of(int G) { return G == 16 ? 3 : 4; }
+// groups stage 3 elements per stage in 3 stages (stage shape SH = 0: fewer hand-overs per
+// element) or 2 elements in 4 stages (SH = 1: a deeper ring), the others 32 rows (E <= 32
+// producer lanes) in 4.
+__host__ __device__ constexpr int rows_of(int G, int SH = 0) { return G == 16 ? (SH == 1 ? 32 : 48) : 32; }
+__host__ __device__ constexpr int stages_of(int G, int SH = 0) { return G == 16 ? (SH == 1 ? 4 : 3) : 4; }
+constexpr int kStageShapes = 2;
 constexpr int kMaxStages = 4;
 constexpr float kMagic = 8421376.0f; // 2^23 + 2^15
 
@@ -218,17 +220,17 @@ constexpr uint32_t kFirColLo = 64, kFirColD = 128;
 // Shared-memory layout, identical on host and device.
 struct SmemLayout {
     int bars, meta, taps, ring, stage, total, ring_stride;
-    __host__ __device__ SmemLayout(int G, int mode, int W) {
+    __host__ __device__ SmemLayout(int G, int mode, int W, int SH = 0) {
         bars = 0;                                             // full[kMaxStages], empty[kMaxStages], abort flag,
                                                               // FIR done (72), tensor-memory base (80),
                                                               // FIR ring ready (88)
         meta = 128;                                           // [stages][rows] ElemMeta
-        taps = meta + stages_of(G) * rows_of(G) * (int)sizeof(ElemMeta); // [kTapSlots] float4 (c, c, s, s)
+        taps = meta + stages_of(G, SH) * rows_of(G, SH) * (int)sizeof(ElemMeta); // [kTapSlots] float4 (c, c, s, s)
         ring = taps + (mode == 1 ? kTapSlots * 16 : 0);
         ring_stride = ((kRingLen - 1) + ((kRingLen - 1) >> 3) + 1 + 3) & ~3;
         stage = ring + (mode == 1 ? (G == 16 ? kRing16Bytes : G * ring_stride * 4) : 0);
         stage = (stage + 127) & ~127;
-        total = stage + stages_of(G) * rows_of(G) * W * 2;
+        total = stage + stages_of(G, SH) * rows_of(G, SH) * W * 2;
     }
 };
 
@@ -269,9 +271,11 @@ struct ProdConst {
 // 16 samples of a test point can pass only if that point is within
 // lip * 16 * depth_step of passing.  Returns false if no depth can.
 // With `halves`, item j is half j % 2 of box element j / 2 (depth steps coarser
-// than c / (2 fs) make a whole tile's window too wide for one slot).
+// than c / (2 fs) make a whole tile's window too wide for one slot).  Depths
+// before i_first are left out (a halo tile is needed for its last depths only).
 __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo &lg, float lip, short4 b, int tile,
-                                              bool halves, int j, int &e, float4 &xe, int &ia, int &ib) {
+                                              bool halves, int i_first, int j, int &e, float4 &xe, int &ia,
+                                              int &ib) {
     const int nbx = b.y - b.x + 1, nby = b.w - b.z + 1;
     const int je = halves ? j >> 1 : j;
     if (je >= nbx * nby) return false;
@@ -282,8 +286,9 @@ __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo 
     if (halves) {
         if (j & 1) i0 += kTD / 2;
         else i1 = min(i1, i0 + kTD / 2 - 1);
-        if (i0 > i1) return false;
     }
+    i0 = max(i0, i_first);
+    if (i0 > i1) return false;
     const float margin = lip * 16.0f * C.depth_step * 1.001f + 1e-9f;
     int first = -1, last = -1;
 #pragma unroll
@@ -480,7 +485,7 @@ __device__ __forceinline__ void element_frames(const int16_t *rows, const Geo &g
     if constexpr (G == 1) {
         const float x0 = __uint_as_float(biased(row[0])) - kMagic;
         const float x1 = __uint_as_float(biased(row[1])) - kMagic;
-        acc1 = fmaf(g.w0, x0, fmaf(g.w1, x1, acc1));
+        acc1 = fmaf(g.w1, x1, fmaf(g.w0, x0, acc1));   // the frame-pair loop's order
     } else {
         const u64 W0 = pack2(g.w0, g.w0), W1 = pack2(g.w1, g.w1), NB = pack2(-kMagic, -kMagic);
 #pragma unroll
@@ -511,12 +516,12 @@ __device__ __forceinline__ void element_frames_w(const int16_t *rows, int widx, 
 
 constexpr int kSlotSamples = width_of(kNumWidths - 1);   // samples per frame row reserved in a slot
 
-template <int G>
+template <int G, int SH>
 __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int i, float r,
                                               float qx, float qy, float inv_a, float base, int kt,
                                               bool use_y, float wa, float wb, float fsc,
                                               u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1, float &wsum) {
-    constexpr int E = rows_of(G) / G;
+    constexpr int E = rows_of(G, SH) / G;
     if constexpr (E <= 4) {
         // geometry of every slot first (independent chains), then the frame loops
         Geo g[E];
@@ -783,9 +788,11 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 // MODE 1: envelope + log compression, write uint8 [n_lines][n_depth] per frame.
 // MINB: resident CTAs per SM the registers are sized for (3 only for one-frame launches with
 // at least three CTAs per SM of work; their shared memory allows it)
-template <int G, int MODE, bool EXT, int MINB = 2>
+// SH: stage shape (rows_of, stages_of).
+template <int G, int MODE, bool EXT, int MINB = 2, int SH = 0>
 __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const __grid_constant__ LaunchGroups L) {
-    constexpr int kRows = rows_of(G), kStages = stages_of(G);
+    constexpr int kRows = rows_of(G, SH), kStages = stages_of(G, SH);
+    static_assert(kStages <= kMaxStages, "barrier slots");
     constexpr int E = kRows / G;
     constexpr bool kTcFir = (MODE == 1 && G == 16);   // FIR on the tensor cores; whole lines only
     extern __shared__ __align__(128) unsigned char smem[];
@@ -811,7 +818,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
     const int T0 = kTcFir ? 0 : seg * NT / n_seg, T1 = kTcFir ? NT : (seg + 1) * NT / n_seg;
     const int tb = (MODE == 1 && T0 > 0) ? T0 - 1 : T0;
     const int te = T1 + ((MODE == 1 && seg == n_seg - 1) ? 1 : 0);
-    const SmemLayout lay(G, MODE, kSlotSamples);
+    const SmemLayout lay(G, MODE, kSlotSamples, SH);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
     uint64_t *empty = full + kMaxStages;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + lay.bars + 16 * kMaxStages);
@@ -903,6 +910,8 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
             const int tile = vt / n_comp, ci = vt - tile * n_comp;
             const bool final_ci = ci == n_comp - 1;
             const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
+            // a halo tile (before the segment's first) feeds the FIR its last kHalo depths only
+            const int i_first = tile * kTD + (tile < T0 ? kTD - kHalo : 0);
             const int nbox = (b.y - b.x + 1) * (b.w - b.z + 1) * (halves ? 2 : 1);
             // Stage the active elements, E per stage, and mark the tile's last stage.  With a few
             // elements per stage (G >= 8) a full stage is handed over when the next element
@@ -916,7 +925,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
                 for (int jb = 0; jb < nbox; jb += 32) {
                     int e, ia, ib;
                     float4 xe;
-                    const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                    const bool a = element_range(C, lg, lip, b, tile, halves, i_first, jb + lane, e, xe, ia, ib);
                     nact += __popc(__ballot_sync(0xffffffffu, a));
                 }
                 nst = max(1, (nact + E - 1) / E);
@@ -924,7 +933,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
             for (int jb = 0; jb < nbox && ok; jb += 32) {
                 int e, ia, ib;
                 float4 xe;
-                const bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                const bool a = element_range(C, lg, lip, b, tile, halves, i_first, jb + lane, e, xe, ia, ib);
                 ElemMeta m;
                 int tx;
                 if constexpr (EXT) {
@@ -1050,8 +1059,10 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
                         cur = ci;
                     }
                 }
-                consume_stage<G>(stages + sb * stage_elems, meta, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb, fsc,
-                                 acc2, acc1, wsum);
+                // a halo tile's depths before its last kHalo are not needed (warp-uniform)
+                if (tile >= T0 || warp >= (kTD - kHalo) / 32)
+                    consume_stage<G, SH>(stages + sb * stage_elems, meta, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb,
+                                     fsc, acc2, acc1, wsum);
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(&empty[sb]);
                 if (++sb == kStages) {

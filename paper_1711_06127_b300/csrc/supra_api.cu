@@ -27,6 +27,9 @@ struct supra_plan {
     int device = 0;
     int max_active = 0;     // upper bound on the elements inside one pixel's aperture
     std::atomic<int> max_group{kMaxGroup};   // frames per DAS tile (autotuned)
+    std::atomic<int> stage_shape{0};         // 16-frame groups: 0 = 3 elements x 3 stages, 1 = 2 x 4
+    std::atomic<int> depth_segments{0};      // segments per line, 0 = automatic (fill one wave)
+    std::atomic<int> ctas_per_sm{0};         // one-frame launches: 0 = automatic, 2 or 3
     bool ext = false;   // extended transmit model (a plane-wave line or compounding): its own kernels
 };
 
@@ -172,9 +175,11 @@ int sm_count() {
 // Depth segments per line for a launch of `items` lines whose shortest line has
 // min_tiles depth tiles: a launch that leaves SMs idle (fewer lines than two
 // resident CTAs per SM) splits its lines so that the segments still fit in one
-// wave.  16-frame B-mode launches (the tensor-core FIR) keep whole lines.
-int depth_segments(int items, int min_tiles, int G, int mode) {
+// wave.  16-frame B-mode launches (the tensor-core FIR) keep whole lines.  A
+// plan's depth_segments setting k >= 1 asks for k segments per line instead.
+int depth_segments(int items, int min_tiles, int G, int mode, int setting = 0) {
     if (mode == 1 && G == 16) return 1;
+    if (setting > 0) return std::max(1, std::min(setting, min_tiles));
     const int slots = 2 * sm_count();
     const int s = items > 0 ? slots / items : 1;
     return std::max(1, std::min(s, min_tiles));
@@ -183,13 +188,13 @@ int depth_segments(int items, int min_tiles, int G, int mode) {
 // kernel choice for a frame group size
 int group_template(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
 
-template <int G, int MODE, bool EXT, int MINB = 2>
+template <int G, int MODE, bool EXT, int MINB = 2, int SH = 0>
 int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
     // the shared-memory opt-in is set once per device (it outlives the call)
     constexpr int kMaxDev = 64;
     static std::atomic<int> ready[kMaxDev];
-    const SmemLayout lay(G, MODE, kSlotSamples);
-    auto kern = das_kernel<G, MODE, EXT, MINB>;
+    const SmemLayout lay(G, MODE, kSlotSamples, SH);
+    auto kern = das_kernel<G, MODE, EXT, MINB, SH>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SUPRA_ECUDA;
     if (dev >= kMaxDev || ready[dev].load(std::memory_order_acquire) == 0) {
@@ -204,13 +209,20 @@ int launch_das_t(const LaunchGroups &L, cudaStream_t st) {
     return check_cuda(cudaGetLastError());
 }
 
+// Launch-level tile settings of a launch (those of its first frame's plan).
+struct LaunchShape {
+    int stage_shape = 0;   // 16-frame groups
+    int ctas_per_sm = 0;   // one-frame launches: 0 = automatic, 2 or 3
+};
+
 template <bool EXT>
-int launch_das_c(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
+int launch_das_c(int G, int mode, const LaunchGroups &L, const LaunchShape &S, cudaStream_t st) {
     if (G == 1) {
         // one frame per CTA: three resident CTAs per SM (fewer registers) when the launch has
         // work for them, e.g. the many lines of a volume; two otherwise, so that a launch of
         // fewer CTAs than three per SM still spreads over all SMs
-        const bool three = (long long)L.total_lines * std::max(L.n_seg, 1) >= 3LL * sm_count();
+        const bool three = S.ctas_per_sm ? S.ctas_per_sm == 3
+                                         : (long long)L.total_lines * std::max(L.n_seg, 1) >= 3LL * sm_count();
         if (three) return mode == 0 ? launch_das_t<1, 0, EXT, 3>(L, st) : launch_das_t<1, 1, EXT, 3>(L, st);
         return mode == 0 ? launch_das_t<1, 0, EXT>(L, st) : launch_das_t<1, 1, EXT>(L, st);
     }
@@ -219,16 +231,17 @@ int launch_das_c(int G, int mode, const LaunchGroups &L, cudaStream_t st) {
         case 2: return launch_das_t<2, 1, EXT>(L, st);
         case 4: return launch_das_t<4, 1, EXT>(L, st);
         case 8: return launch_das_t<8, 1, EXT>(L, st);
-        default: return launch_das_t<16, 1, EXT>(L, st);
+        default:
+            return S.stage_shape == 1 ? launch_das_t<16, 1, EXT, 2, 1>(L, st) : launch_das_t<16, 1, EXT>(L, st);
     }
 }
 
 // ext: the groups' plans use an extended transmit model (plane waves and/or
 // compounding several transmits per line).  They run their own kernel
 // instantiation, so plans with spherical single transmits keep the plain code.
-int launch_das(int G, int mode, bool ext, const LaunchGroups &L, cudaStream_t st) {
+int launch_das(int G, int mode, bool ext, const LaunchGroups &L, const LaunchShape &S, cudaStream_t st) {
     if (L.total_lines == 0) return SUPRA_OK;
-    return ext ? launch_das_c<true>(G, mode, L, st) : launch_das_c<false>(G, mode, L, st);
+    return ext ? launch_das_c<true>(G, mode, L, S, st) : launch_das_c<false>(G, mode, L, S, st);
 }
 
 // Frames of one scan-conversion launch and their host-side plan records (grid sizing).
@@ -772,8 +785,10 @@ int supra_beamform(const supra_plan *plan, const int16_t *ch, float *rf, void *s
     L.g[0].ch[0] = ch;
     L.g[0].out[0] = rf;
     L.uniform = 1;
-    L.n_seg = depth_segments(L.total_lines, plan->host.n_tiles, 1, 0);
-    return launch_das(1, 0, plan->ext, L, static_cast<cudaStream_t>(stream));
+    L.n_seg = depth_segments(L.total_lines, plan->host.n_tiles, 1, 0, plan->depth_segments.load());
+    LaunchShape S;
+    S.ctas_per_sm = plan->ctas_per_sm.load();
+    return launch_das(1, 0, plan->ext, L, S, static_cast<cudaStream_t>(stream));
 }
 
 int supra_envelope(const supra_plan *plan, const float *rf, float *env, void *stream) {
@@ -868,26 +883,39 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
         }
         groups.push_back(g);
     }
-    bool present[5][2] = {};   // (group-size class, compounding) pairs that have groups
+    // One launch per (group-size class, compounding, stage shape) that has groups; launch-level
+    // settings (depth segments, CTAs per SM) come from the launch's first plan.
+    auto shape_of = [](const Grp &gr, int Gc) { return Gc == 16 ? gr.p->stage_shape.load(std::memory_order_relaxed) : 0; };
+    bool present[5][2][kStageShapes] = {};
     auto class_of = [](int Gc) { return Gc == 16 ? 0 : Gc == 8 ? 1 : Gc == 4 ? 2 : Gc == 2 ? 3 : 4; };
-    for (const Grp &gr : groups) present[class_of(group_template(gr.n))][gr.p->ext ? 1 : 0] = true;
+    for (const Grp &gr : groups) {
+        const int Gc = group_template(gr.n);
+        present[class_of(Gc)][gr.p->ext ? 1 : 0][shape_of(gr, Gc)] = true;
+    }
     for (int Gc : {16, 8, 4, 2, 1}) {
         for (int comp = 0; comp < 2; ++comp) {
-            if (!present[class_of(Gc)][comp]) continue;
+          for (int sh = 0; sh < kStageShapes; ++sh) {
+            if (!present[class_of(Gc)][comp][sh]) continue;
             LaunchGroups L{};
             L.uniform = 1;
             int min_tiles = 1 << 30;
+            const supra_plan *first = nullptr;
             auto flush = [&]() -> int {
                 if (L.n_groups == 0) return SUPRA_OK;
-                L.n_seg = depth_segments(L.total_lines, min_tiles, Gc, 1);
-                const int rc = launch_das(Gc, 1, comp == 1, L, st);
+                L.n_seg = depth_segments(L.total_lines, min_tiles, Gc, 1, first->depth_segments.load());
+                LaunchShape S;
+                S.stage_shape = sh;
+                S.ctas_per_sm = first->ctas_per_sm.load();
+                const int rc = launch_das(Gc, 1, comp == 1, L, S, st);
                 L = LaunchGroups{};
                 L.uniform = 1;
                 min_tiles = 1 << 30;
+                first = nullptr;
                 return rc;
             };
             for (const Grp &gr : groups) {
-                if (group_template(gr.n) != Gc || gr.p->ext != (comp == 1)) continue;
+                if (group_template(gr.n) != Gc || gr.p->ext != (comp == 1) || shape_of(gr, Gc) != sh) continue;
+                if (!first) first = gr.p;
                 FrameGroup &g = L.g[L.n_groups];
                 g.plan = gr.p->dev;
                 g.line0 = L.total_lines;
@@ -924,6 +952,7 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
             }
             const int rc = flush();
             if (rc) return rc;
+          }
         }
     }
     // scan conversion of the frames with a grid
@@ -1019,23 +1048,71 @@ int32_t supra_plan_get_max_group(const supra_plan *plan) {
     return plan ? plan->max_group.load(std::memory_order_relaxed) : SUPRA_EINVAL;
 }
 
-int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out, void *workspace,
-                         size_t workspace_bytes, int32_t reps, void *stream, int32_t *best_group, float *best_ms) {
+int supra_plan_set_tile_shape(supra_plan *plan, const supra_tile_shape *s) {
+    if (!plan || !s) return SUPRA_EINVAL;
+    const int g = s->frames_per_group;
+    if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16) return SUPRA_EINVAL;
+    int sh;
+    if (s->elements_per_stage == 3 && s->stages == 3) sh = 0;
+    else if (s->elements_per_stage == 2 && s->stages == 4) sh = 1;
+    else return SUPRA_EINVAL;
+    if (s->depth_segments < 0 || s->depth_segments > 64) return SUPRA_EINVAL;
+    if (s->ctas_per_sm != 0 && s->ctas_per_sm != 2 && s->ctas_per_sm != 3) return SUPRA_EINVAL;
+    plan->max_group.store(g);
+    plan->stage_shape.store(sh);
+    plan->depth_segments.store(s->depth_segments);
+    plan->ctas_per_sm.store(s->ctas_per_sm);
+    return SUPRA_OK;
+}
+
+int supra_plan_get_tile_shape(const supra_plan *plan, supra_tile_shape *s) {
+    if (!plan || !s) return SUPRA_EINVAL;
+    s->frames_per_group = plan->max_group.load();
+    const int sh = plan->stage_shape.load();
+    s->elements_per_stage = sh == 1 ? 2 : 3;
+    s->stages = sh == 1 ? 4 : 3;
+    s->depth_segments = plan->depth_segments.load();
+    s->ctas_per_sm = plan->ctas_per_sm.load();
+    return SUPRA_OK;
+}
+
+int supra_autotune_tile_shape(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out,
+                              void *workspace, size_t workspace_bytes, int32_t reps, void *stream,
+                              supra_tile_shape *best_shape, float *best_ms, float *start_ms) {
     if (!plan || n < 1 || !ch || !out || reps < 1) return SUPRA_EINVAL;
     std::vector<const supra_plan *> plans(n, plan);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    supra_tile_shape before{};
+    supra_plan_get_tile_shape(plan, &before);
+    // candidates: the shape in effect first (its time is start_ms), then every frames-per-group
+    // class with the settings that class's launches use -- the stage shape for 16-frame groups,
+    // depth segments for the others (0 = automatic, then 1, 2, 4, 8 per line), resident CTAs
+    // per SM for one-frame launches
+    std::vector<supra_tile_shape> cand{before};
+    for (int g : {16, 8, 4, 2, 1}) {
+        if (g > 1 && g / 2 >= n) continue;   // same launches as a smaller class
+        const bool tc = g == 16 && n > 8;     // 16-frame groups: whole lines, FIR on the tensor cores
+        for (int sh = 0; sh < (tc ? kStageShapes : 1); ++sh)
+            for (int seg : {0, 1, 2, 4, 8}) {
+                if (tc && seg) continue;
+                for (int c : {0, 2, 3}) {
+                    if (c && g != 1) continue;
+                    cand.push_back({g, sh == 1 ? 2 : 3, sh == 1 ? 4 : 3, seg, c});
+                }
+            }
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return SUPRA_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return SUPRA_ECUDA;
     }
-    const int before = plan->max_group.load();
-    int best = before, rc = SUPRA_OK;
-    float best_t = INFINITY;
-    for (int g : {16, 8, 4, 2, 1}) {
-        if (g > 1 && g / 2 >= n) continue;   // same launches as a smaller class
-        plan->max_group.store(g);
+    int rc = SUPRA_OK;
+    supra_tile_shape best = before;
+    float best_t = INFINITY, first_t = INFINITY;
+    for (size_t c = 0; c < cand.size() && !rc; ++c) {
+        rc = supra_plan_set_tile_shape(plan, &cand[c]);
+        if (rc) break;
         rc = supra_bmode_batched(n, plans.data(), ch, out, workspace, workspace_bytes, stream);   // warm-up
         if (rc) break;
         cudaEventRecord(e0, st);
@@ -1050,14 +1127,26 @@ int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *const *ch, 
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= (float)reps;
-        if (ms < best_t) best_t = ms, best = g;
+        if (c == 0) first_t = ms;
+        if (ms < best_t) best_t = ms, best = cand[c];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    plan->max_group.store(rc ? before : best);
+    supra_plan_set_tile_shape(plan, rc ? &before : &best);
     if (rc) return rc;
-    if (best_group) *best_group = best;
+    if (best_shape) *best_shape = best;
     if (best_ms) *best_ms = best_t;
+    if (start_ms) *start_ms = first_t;
+    return SUPRA_OK;
+}
+
+int supra_autotune_bmode(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out, void *workspace,
+                         size_t workspace_bytes, int32_t reps, void *stream, int32_t *best_group, float *best_ms) {
+    supra_tile_shape s{};
+    const int rc = supra_autotune_tile_shape(plan, n, ch, out, workspace, workspace_bytes, reps, stream, &s, best_ms,
+                                             nullptr);
+    if (rc) return rc;
+    if (best_group) *best_group = s.frames_per_group;
     return SUPRA_OK;
 }
 

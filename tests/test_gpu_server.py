@@ -143,6 +143,50 @@ def test_autotuner_picks_a_frames_per_tile_class_and_keeps_results():
     plan.max_group = 16
 
 
+def test_tile_shapes_give_the_same_images_and_the_tuner_keeps_its_pick():
+    # A 16-frame group and a 3-frame tail of contiguous frames under every kind of tile shape
+    # the tuner can pick.  Shapes that keep 16-frame groups give the untuned plan's images byte
+    # for byte; smaller groups run the demodulating filter on the FP32 cores instead of the
+    # tensor cores, and all of them (any group size, depth segments, CTAs per SM) give one
+    # another's images byte for byte and the untuned ones within the B-mode tolerance.
+    a, _, _ = _setups()
+    p = a.params()
+    plan = supra.Plan(**p)
+    batch = torch.stack([phantom.synth_channels(a, phantom.make_phantom(a, 40 + i, 400), 40 + i) for i in range(19)])
+    chs = list(batch.cuda())
+    ref = [o.cpu().numpy() for o in supra.bmode_batched([plan] * 19, chs)]
+    default = plan.tile_shape
+    assert default == {"frames_per_group": 16, "elements_per_stage": 3, "stages": 3, "depth_segments": 0,
+                       "ctas_per_sm": 0}
+
+    def images(shape):
+        tuned = supra.Plan(**p)
+        tuned.tile_shape = shape
+        assert tuned.tile_shape == shape
+        return [o.cpu().numpy() for o in supra.bmode_batched([tuned] * 19, chs)]
+
+    for k, (o, r) in enumerate(zip(images(dict(default, elements_per_stage=2, stages=4)), ref)):
+        np.testing.assert_array_equal(o, r, err_msg=f"2 x 4 stages, frame {k}")
+    ref_fp32 = images(dict(default, frames_per_group=8))
+    for o, r in zip(ref_fp32, ref):
+        assert_gray(o, r)
+    shapes = [dict(default, frames_per_group=g, depth_segments=s) for g in (8, 2) for s in (1, 3)]
+    shapes += [dict(default, frames_per_group=1, depth_segments=s, ctas_per_sm=c) for s in (0, 2) for c in (2, 3)]
+    for sh in shapes:
+        for k, (o, r) in enumerate(zip(images(sh), ref_fp32)):
+            np.testing.assert_array_equal(o, r, err_msg=f"{sh} frame {k}")
+    best, ms, ms0 = plan.autotune_shape(chs, reps=2)
+    assert plan.tile_shape == best and ms > 0 and ms0 > 0 and ms <= ms0
+    want = ref if best["frames_per_group"] == 16 else ref_fp32
+    for o, r in zip(supra.bmode_batched([plan] * 19, chs), want):
+        np.testing.assert_array_equal(o.cpu().numpy(), r)
+    with pytest.raises(supra.SupraError):
+        plan.tile_shape = dict(default, elements_per_stage=4, stages=2)
+    with pytest.raises(supra.SupraError):
+        plan.tile_shape = dict(default, ctas_per_sm=1)
+    assert supra.device_status() == 0
+
+
 def test_rejects_requests_that_cannot_run():
     a, _, _ = _setups()
     plan = supra.Plan(**a.params())
