@@ -271,11 +271,9 @@ struct ProdConst {
 // 16 samples of a test point can pass only if that point is within
 // lip * 16 * depth_step of passing.  Returns false if no depth can.
 // With `halves`, item j is half j % 2 of box element j / 2 (depth steps coarser
-// than c / (2 fs) make a whole tile's window too wide for one slot).  Depths
-// before i_first are left out (a halo tile is needed for its last depths only).
+// than c / (2 fs) make a whole tile's window too wide for one slot).
 __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo &lg, float lip, short4 b, int tile,
-                                              bool halves, int i_first, int j, int &e, float4 &xe, int &ia,
-                                              int &ib) {
+                                              bool halves, int j, int &e, float4 &xe, int &ia, int &ib) {
     const int nbx = b.y - b.x + 1, nby = b.w - b.z + 1;
     const int je = halves ? j >> 1 : j;
     if (je >= nbx * nby) return false;
@@ -286,9 +284,8 @@ __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo 
     if (halves) {
         if (j & 1) i0 += kTD / 2;
         else i1 = min(i1, i0 + kTD / 2 - 1);
+        if (i0 > i1) return false;
     }
-    i0 = max(i0, i_first);
-    if (i0 > i1) return false;
     const float margin = lip * 16.0f * C.depth_step * 1.001f + 1e-9f;
     int first = -1, last = -1;
 #pragma unroll
@@ -925,7 +922,8 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
                 for (int jb = 0; jb < nbox; jb += 32) {
                     int e, ia, ib;
                     float4 xe;
-                    const bool a = element_range(C, lg, lip, b, tile, halves, i_first, jb + lane, e, xe, ia, ib);
+                    bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                    if (tile < T0) a = a && ib >= i_first;
                     nact += __popc(__ballot_sync(0xffffffffu, a));
                 }
                 nst = max(1, (nact + E - 1) / E);
@@ -933,7 +931,11 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
             for (int jb = 0; jb < nbox && ok; jb += 32) {
                 int e, ia, ib;
                 float4 xe;
-                const bool a = element_range(C, lg, lip, b, tile, halves, i_first, jb + lane, e, xe, ia, ib);
+                bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                if (tile < T0) {   // halo tile: only depths from i_first on
+                    a = a && ib >= i_first;
+                    ia = max(ia, i_first);
+                }
                 ElemMeta m;
                 int tx;
                 if constexpr (EXT) {
