@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     constexpr uint32_t kCols = MODE == kTrain ? 512 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ __align__(8) uint64_t bar_dw1;   // training: completion of dW1 (never waited on; see below)
+    __shared__ __align__(8) uint64_t bar_dw1;   // training: completion of weight-gradient products (never waited on)
     __shared__ uint32_t tmem_base;
     __shared__ float red[2][NT / 32];
     __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     // before, which read that buffer, are complete too (one thread issues all products, and
     // they complete in order).
     uint32_t nmk[4] = {0u, 0u, 0u, 0u};
-    float nnrm = 0.0f, ntgt = 0.0f;
+    float nnrm = 0.0f, nlab = 0.0f;   // raw loads: nothing uses them before the next tile
     bool nok = false;
     auto prefetch = [&](long long tl, int xo) {
         const long long pp = tl * kTile + row;
@@ -306,12 +306,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + rw);
             nmk[0] = m4.x, nmk[1] = m4.y, nmk[2] = m4.z, nmk[3] = m4.w;
             nnrm = __ldg(a.norm + rw);
-            ntgt = nnrm > 0.0f ? __ldg(a.label + rw) / nnrm : 0.0f;
+            nlab = __ldg(a.label + rw);
         } else {
 #pragma unroll
             for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) chunk(sm, xo, c, row) = make_uint4(0u, 0u, 0u, 0u);
             nmk[0] = nmk[1] = nmk[2] = nmk[3] = 0u;
-            nnrm = ntgt = 0.0f;
+            nnrm = nlab = 0.0f;
         }
         cp_async_commit();
     };
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             row_ok = nok;
             mk[0] = nmk[0], mk[1] = nmk[1], mk[2] = nmk[2], mk[3] = nmk[3];
             nrm = nnrm;
-            tgt = ntgt;
+            tgt = nnrm > 0.0f ? nlab / nnrm : 0.0f;
         } else {
             p = tile * kTile + row;
             row_ok = p < a.n;
@@ -564,13 +564,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         tc::fence_after_sync();
         if (MODE != kTrain) continue;
 
-        // ---- dH2 = dZ3 W3;  [dW3 | db3] += dZ3^T [H2 | 1]
+        // ---- dH2 = dZ3 W3;  [dW3 | db3] += dZ3^T [H2 | 1].  Only dH2 is waited for: the
+        // weight-gradient products run while the threads form dZ2 (they read dZ3 and H2, which
+        // nothing writes before the next tile's products, issued after them, complete)
         if (t == 0) {
             mma_chain(tm + kT64, sb + S::DZ3, 2048, 128, sb + S::W3, 128, 2048, tc::idesc_bf16(128, 64, false, true), 8,
                       false);
+            tc::mma_commit(&bar);
             mma_chain(tm + kDW3, sb + S::DZ3, 128, 2048, sb + S::H2, 128, 2048, tc::idesc_bf16(128, 80, true, true), 8,
                       !first);
-            tc::mma_commit(&bar);
+            tc::mma_commit(&bar_dw1);
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
@@ -590,13 +593,15 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         if (!ok) break;
         tc::fence_after_sync();
 
-        // ---- dH1 = dZ2 W2;  [dW2 | db2] += dZ2^T [H1 | 1]
+        // ---- dH1 = dZ2 W2;  [dW2 | db2] += dZ2^T [H1 | 1], dW2 not waited for (as dW3; its
+        // discarded rows 64..127 read the DZ1 bytes that the threads write meanwhile)
         if (t == 0) {
             mma_chain(tm + kT64, sb + S::DZ2, 2048, 128, sb + S::W2, 128, 1024, tc::idesc_bf16(128, 64, false, true), 4,
                       false);
+            tc::mma_commit(&bar);
             mma_chain(tm + kDW2, sb + S::DZ2, 128, 2048, sb + S::H1, 128, 2048, tc::idesc_bf16(128, 80, true, true), 8,
                       !first);
-            tc::mma_commit(&bar);
+            tc::mma_commit(&bar_dw1);
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
