@@ -335,21 +335,26 @@ def bench_table1(args, dev, stream):
         bm = plan.logcompress(env, stream=stream)
         img = plan.scanconvert(bm, stream=stream)
         ws = torch.empty(max(1, supra.workspace_size([plan])), dtype=torch.uint8, device=dev)
-        # the frame's tile shape from the autotuner (depth segments and resident CTAs of one-frame
-        # launches), used by the fused chain and the beamforming node alike
-        fused_default = timed(lambda: plan.bmode(ch, img, ws, stream))
-        shape = None
+
+        def chains():
+            nodes = {"beamformer": timed(lambda: plan.beamform(ch, rf, stream)),
+                     "envelope": timed(lambda: plan.envelope(rf, env, stream)),
+                     "log_compression": timed(lambda: plan.logcompress(env, bm, stream)),
+                     "scan_conversion": timed(lambda: plan.scanconvert(bm, img, stream))}
+            fused = timed(lambda: plan.bmode(ch, img, ws, stream))
+            return {"node_ms": nodes, "unfused_total_ms": sum(nodes.values()), "fused_ms": fused,
+                    "fused_frames_per_s": 1e3 / fused}
+
+        # default tile shape, then the shape the autotuner picks for the fused chain (depth
+        # segments and resident CTAs of one-frame launches), which the beamforming node uses too
+        default = chains()
+        shape, tuned = None, None
         if not args.no_tune:
             shape, _, _ = plan.autotune_shape([ch], [img], ws, reps=10, stream=stream)
-        nodes = {"beamformer": timed(lambda: plan.beamform(ch, rf, stream)),
-                 "envelope": timed(lambda: plan.envelope(rf, env, stream)),
-                 "log_compression": timed(lambda: plan.logcompress(env, bm, stream)),
-                 "scan_conversion": timed(lambda: plan.scanconvert(bm, img, stream))}
-        fused = timed(lambda: plan.bmode(ch, img, ws, stream))
+            tuned = chains()
         out.append({"config": f"{n_tx}/{k}", "workload": st.name, "n_lines": st.n_lines, "n_samples": st.n_samples,
-                    "grid": "x".join(str(v) for v in plan.out_shape[::-1]),
-                    "node_ms": nodes, "unfused_total_ms": sum(nodes.values()), "fused_ms": fused,
-                    "fused_frames_per_s": 1e3 / fused, "tile_shape": shape, "fused_ms_default_shape": fused_default})
+                    "grid": "x".join(str(v) for v in plan.out_shape[::-1]), **(tuned or default),
+                    "tile_shape": shape, "default_shape": default})
     return out
 
 
@@ -463,7 +468,13 @@ def bench_apod(args, dev, stream):
     prep_s = time.perf_counter() - t0
     data = apod.Dataset(feat, mask, norm, label)
     tr = apod.Trainer(phantom.apod_init(7), lr=args.apod_lr)
-    n_batches = max(1, data.n // args.apod_batch)
+    # minibatches of at most eight 128-pixel tiles per SM (0 = that size): the gradient kernel runs one
+    # CTA per SM and pays a fixed cost per step (weight staging, tensor-memory allocation, partial
+    # gradients, the reduction and Adam launch) of about two and a half tiles, so a minibatch is a
+    # whole number of tile rounds and several of them long
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    batch_rows = args.apod_batch if args.apod_batch > 0 else 8 * 128 * sms
+    n_batches = max(1, -(-data.n // batch_rows))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     losses = []
     e0.record(stream)
@@ -1006,7 +1017,8 @@ def main(argv=None):
     ap.add_argument("--apod-train-frames", type=int, default=200)
     ap.add_argument("--apod-eval-frames", type=int, default=20)
     ap.add_argument("--apod-epochs", type=int, default=8)
-    ap.add_argument("--apod-batch", type=int, default=65536, help="pixels per minibatch")
+    ap.add_argument("--apod-batch", type=int, default=0,
+                    help="pixels per minibatch at most (0: eight 128-pixel tiles per SM, 151 552 on 148 SMs)")
     ap.add_argument("--apod-lr", type=float, default=1e-3)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")

@@ -32,7 +32,7 @@ constexpr int kIn = 128, kH1 = 64, kH2 = 64, kTile = 128;
 // flat parameter vector: W1 [64][128], b1, W2 [64][64], b2, W3 [128][64], b3
 constexpr int kOffW1 = 0, kOffB1 = 8192, kOffW2 = 8256, kOffB2 = 12352, kOffW3 = 12416, kOffB3 = 20608;
 constexpr int kParams = 20736;
-constexpr int kPartStride = kParams + 2;   // + loss sum, valid-pixel count
+constexpr int kPartStride = kParams + 4;   // + loss sum, valid-pixel count (rows 16-byte aligned)
 enum { kForward = 0, kTrain = 1, kInfer = 2 };
 
 // Shared-memory images, byte offsets.  A "[rows][cols] buffer" keeps 16-byte
@@ -186,28 +186,41 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo
                      idesc, acc || s > 0);
 }
 
+// Weights [n][i] (row-major, i fastest) of one matrix into its shared-memory image: element
+// (n, i) at img + (i / 8) * jstride + n * 16 + (i % 8) * 2, rounded to BF16.  Four consecutive
+// weights per thread and load (16-byte loads, all of a thread's loads in flight at once) when the
+// parameter vector is 16-byte aligned, one otherwise.
+template <int LOG2_IN>
+__device__ __forceinline__ void stage_matrix(const float *__restrict__ w, int count, unsigned char *img, int jstride,
+                                             bool vec, int t, int nt) {
+    constexpr int kRow = 1 << LOG2_IN;
+    if (vec) {
+        const float4 *w4 = reinterpret_cast<const float4 *>(w);
+#pragma unroll 4
+        for (int k4 = t; k4 < count / 4; k4 += nt) {
+            const float4 q = __ldg(w4 + k4);
+            const int k = 4 * k4, n = k >> LOG2_IN, i = k & (kRow - 1);
+            *reinterpret_cast<uint2 *>(img + (i >> 3) * jstride + n * 16 + (i & 7) * 2) =
+                make_uint2(pack_bf16(q.x, q.y), pack_bf16(q.z, q.w));
+        }
+    } else {
+#pragma unroll 8
+        for (int k = t; k < count; k += nt) {
+            const int n = k >> LOG2_IN, i = k & (kRow - 1);
+            *reinterpret_cast<__nv_bfloat16 *>(img + (i >> 3) * jstride + n * 16 + (i & 7) * 2) =
+                __float2bfloat16_rn(__ldg(w + k));
+        }
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ void stage_weights(const float *__restrict__ prm, unsigned char *sm, int t, int nt) {
     using S = Smem<MODE>;
-    // loads batched 8 deep, so that each thread waits for a few round trips to L2, not dozens
-#pragma unroll 8
-    for (int k = t; k < kH1 * kIn; k += nt) {
-        const int n = k >> 7, i = k & 127;
-        *reinterpret_cast<__nv_bfloat16 *>(sm + S::W1 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
-            __float2bfloat16_rn(__ldg(prm + kOffW1 + k));
-    }
-#pragma unroll 8
-    for (int k = t; k < kH2 * kH1; k += nt) {
-        const int n = k >> 6, i = k & 63;
-        *reinterpret_cast<__nv_bfloat16 *>(sm + S::W2 + (i >> 3) * 1024 + n * 16 + (i & 7) * 2) =
-            __float2bfloat16_rn(__ldg(prm + kOffW2 + k));
-    }
-#pragma unroll 8
-    for (int k = t; k < kIn * kH2; k += nt) {
-        const int n = k >> 6, i = k & 63;
-        *reinterpret_cast<__nv_bfloat16 *>(sm + S::W3 + (i >> 3) * 2048 + n * 16 + (i & 7) * 2) =
-            __float2bfloat16_rn(__ldg(prm + kOffW3 + k));
-    }
+    // the matrices start at multiples of four floats, so one alignment test covers them
+    const bool vec = (reinterpret_cast<uintptr_t>(prm) & 15) == 0;
+    stage_matrix<7>(prm + kOffW1, kH1 * kIn, sm + S::W1, 1024, vec, t, nt);
+    stage_matrix<6>(prm + kOffW2, kH2 * kH1, sm + S::W2, 1024, vec, t, nt);
+    stage_matrix<6>(prm + kOffW3, kIn * kH2, sm + S::W3, 2048, vec, t, nt);
     float *bias = reinterpret_cast<float *>(sm + S::BIAS);
     for (int k = t; k < 256; k += nt)
         bias[k] = k < 64 ? prm[kOffB1 + k] : k < 128 ? prm[kOffB2 + k - 64] : prm[kOffB3 + k - 128];
@@ -224,11 +237,19 @@ __device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t &phase) {
 // Threads per CTA: training and the fused beamformer split every pixel row over
 // two warpgroups (warps w and w + 4 share TMEM lanes 32 (w % 4).., each takes
 // half of every row's columns; in the beamformer each half gathers the elements
-// whose weights it computes), so two warps per scheduler hide each other's
-// gather, TMEM, shared-memory and MMA waits; the forward pass on stored rows
-// keeps one warpgroup.
+// whose weights it computes), so that two warps per scheduler hide each other's
+// TMEM, shared-memory and MMA waits; the forward pass on stored rows keeps one
+// warpgroup.  The kernel takes any power-of-two number of parts H = threads /
+// 128 up to 4 (a training split over four measured the same per tile).
 template <int MODE>
 __host__ __device__ constexpr int apod_threads() { return MODE == kForward ? 128 : 256; }
+
+// This thread's columns of a 64-wide accumulator: H parts of 64 / H columns, read in blocks of up to 32.
+template <int B>
+__device__ __forceinline__ void tmem_ld_block(uint32_t taddr, float (&v)[B]) {
+    if constexpr (B == 32) tc::tmem_ld32(taddr, v);
+    else tc::tmem_ld16(taddr, v);
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) apod_kernel(const Args a) {
@@ -251,42 +272,6 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
-    stage_weights<MODE>(a.params, sm, t, NT);
-    if (MODE == kTrain && half == 0) {
-        const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
-        chunk(sm, S::X, 16, row) = ones;
-        chunk(sm, S::X, 17, row) = ones;
-        chunk(sm, S::X2, 16, row) = ones;
-        chunk(sm, S::X2, 17, row) = ones;
-        chunk(sm, S::H1, 8, row) = ones;
-        chunk(sm, S::H1, 9, row) = ones;
-        chunk(sm, S::H2, 8, row) = ones;
-        chunk(sm, S::H2, 9, row) = ones;
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tm = tmem_base, lane = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t sb = tc::smem_u32(sm);
-    const float *b1 = reinterpret_cast<const float *>(sm + S::BIAS), *b2 = b1 + 64, *b3 = b1 + 128;
-    constexpr uint32_t kI64 = tc::idesc_bf16(128, 64, false, false), kI128 = tc::idesc_bf16(128, 128, false, false);
-    // this thread's column blocks of 32: 64-wide layers q in [q2, q2 + 2/H), the 128 outputs q in [q4, q4 + 4/H)
-    const int q2 = half * (2 / H), q4 = half * (4 / H);
-
-    long long n_tiles;
-    int nblk = 1, nd = 0;
-    if (MODE == kInfer) {
-        nd = a.plan->n_depth;
-        nblk = (nd + kTile - 1) / kTile;
-        n_tiles = (long long)a.plan->n_lines * nblk;
-    } else {
-        n_tiles = (a.n + kTile - 1) / kTile;
-    }
-    uint32_t phase = 0;
-    bool ok = true, first = true;
-    float loss_acc = 0.0f, cnt_acc = 0.0f;
-
     // Training: the next tile's feature rows are copied into the other X buffer (cp.async)
     // while this tile runs; its masks, norms and labels wait in registers.  The copy into a
     // buffer is issued after the next Z1 products complete, so the dW1 products of the tile
@@ -315,7 +300,47 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         cp_async_commit();
     };
-    if (MODE == kTrain && (long long)blockIdx.x < n_tiles) prefetch(blockIdx.x, S::X);
+    // the first tile's rows are requested before the weights are staged (the two latencies overlap)
+    if (MODE == kTrain && (long long)blockIdx.x < (a.n + kTile - 1) / kTile) prefetch(blockIdx.x, S::X);
+    stage_weights<MODE>(a.params, sm, t, NT);
+    if (MODE == kTrain && half == 0) {
+        const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        chunk(sm, S::X, 16, row) = ones;
+        chunk(sm, S::X, 17, row) = ones;
+        chunk(sm, S::X2, 16, row) = ones;
+        chunk(sm, S::X2, 17, row) = ones;
+        chunk(sm, S::H1, 8, row) = ones;
+        chunk(sm, S::H1, 9, row) = ones;
+        chunk(sm, S::H2, 8, row) = ones;
+        chunk(sm, S::H2, 9, row) = ones;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_base, lane = (uint32_t)(32 * (warp & 3)) << 16;
+    // 64-wide layers: this thread's columns c64 .. c64 + C64, in NB64 blocks of BW64
+    constexpr int C64 = 64 / H, BW64 = C64 < 32 ? C64 : 32, NB64 = C64 / BW64;
+    const int c64 = C64 * half;
+    const uint32_t sb = tc::smem_u32(sm);
+    const float *b1 = reinterpret_cast<const float *>(sm + S::BIAS), *b2 = b1 + 64, *b3 = b1 + 128;
+    constexpr uint32_t kI64 = tc::idesc_bf16(128, 64, false, false), kI128 = tc::idesc_bf16(128, 128, false, false);
+    // this thread's column blocks of 32 of the 128 outputs: q in [q4, q4 + 4/H)
+    const int q4 = half * (4 / H);
+
+    long long n_tiles;
+    int nblk = 1, nd = 0;
+    if (MODE == kInfer) {
+        nd = a.plan->n_depth;
+        nblk = (nd + kTile - 1) / kTile;
+        n_tiles = (long long)a.plan->n_lines * nblk;
+    } else {
+        n_tiles = (a.n + kTile - 1) / kTile;
+    }
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    float loss_acc = 0.0f, cnt_acc = 0.0f;
+
 
     int iter = 0;
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
@@ -435,13 +460,14 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         if (MODE == kTrain && tile + gridDim.x < n_tiles) prefetch(tile + gridDim.x, xo == S::X ? S::X2 : S::X);
         const float scale = (MODE == kInfer) ? (nrm > 0.0f ? 1.0f / nrm : 0.0f) : 1.0f;
 #pragma unroll
-        for (int q = q2; q < q2 + 2 / H; ++q) {
-            float v[32];
-            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+        for (int bk = 0; bk < NB64; ++bk) {
+            const int col = c64 + BW64 * bk;
+            float v[BW64];
+            tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(fmaf(v[j], scale, b1[32 * q + j]), 0.0f);
+            for (int j = 0; j < BW64; ++j) v[j] = fmaxf(fmaf(v[j], scale, b1[col + j]), 0.0f);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::H1, 4 * q + c, row) = pack8(v + 8 * c);
+            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::H1, col / 8 + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -456,13 +482,14 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
-        for (int q = q2; q < q2 + 2 / H; ++q) {
-            float v[32];
-            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+        for (int bk = 0; bk < NB64; ++bk) {
+            const int col = c64 + BW64 * bk;
+            float v[BW64];
+            tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + b2[32 * q + j], 0.0f);
+            for (int j = 0; j < BW64; ++j) v[j] = fmaxf(v[j] + b2[col + j], 0.0f);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::H2, 4 * q + c, row) = pack8(v + 8 * c);
+            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::H2, col / 8 + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -496,10 +523,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], v[j] + b3[32 * q + j]);
         }
         float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
-        if constexpr (H > 1) {   // the row's maximum over both halves
+        if constexpr (H > 1) {   // the row's maximum over its parts
             xrow[0][half][row] = zmax;
             __syncthreads();
-            zmax = fmaxf(xrow[0][0][row], xrow[0][1][row]);
+            zmax = xrow[0][0][row];
+#pragma unroll
+            for (int h = 1; h < H; ++h) zmax = fmaxf(zmax, xrow[0][h][row]);
         }
         float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         load_pair();
@@ -516,16 +545,22 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
                 se4[j & 3] += ez;
                 sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
+                if constexpr (kPair) vv[k][j] = ez;   // kept for the output gradient below
             }
         }
         float se = (se4[0] + se4[1]) + (se4[2] + se4[3]);
         float sx = (sx4[0] + sx4[1]) + (sx4[2] + sx4[3]);
-        if constexpr (H > 1) {   // the row's sums over both halves
+        if constexpr (H > 1) {   // the row's sums over its parts (pairwise, fixed order)
             xrow[1][half][row] = se;
             xrow[2][half][row] = sx;
             __syncthreads();
-            se = xrow[1][0][row] + xrow[1][1][row];
-            sx = xrow[2][0][row] + xrow[2][1][row];
+            if constexpr (H == 2) {
+                se = xrow[1][0][row] + xrow[1][1][row];
+                sx = xrow[2][0][row] + xrow[2][1][row];
+            } else {
+                se = (xrow[1][0][row] + xrow[1][1][row]) + (xrow[1][2][row] + xrow[1][3][row]);
+                sx = (xrow[2][0][row] + xrow[2][1][row]) + (xrow[2][2][row] + xrow[2][3][row]);
+            }
         }
         const float yh = se > 0.0f ? sx / se : 0.0f;
         if (MODE == kForward) {
@@ -539,18 +574,19 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 cnt_acc += valid ? 1.0f : 0.0f;
             }
             const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f;
-            load_pair();
 #pragma unroll
             for (int k = 0; k < 4 / H; ++k) {
                 const int q = q4 + k;
                 float vl[32], x[32], dz[32];
                 if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
-                const float *v = kPair ? vv[k] : vl;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float pe = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
+                    // w_e = exp(z_e - zmax) / sum: the exponentials of the pass above (the same values)
+                    float pe;
+                    if constexpr (kPair) pe = vv[k][j] * inv_se;
+                    else pe = ((mk[q] >> j) & 1u) ? __expf(vl[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
                     dz[j] = pe * (x[j] - yh) * g;
                 }
 #pragma unroll
@@ -577,15 +613,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
-        for (int q = q2; q < q2 + 2 / H; ++q) {
-            float v[32], h[32];
-            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+        for (int bk = 0; bk < NB64; ++bk) {
+            const int col = c64 + BW64 * bk;
+            float v[BW64], h[BW64];
+            tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H2, 4 * q + c, row), h + 8 * c);
+            for (int c = 0; c < BW64 / 8; ++c) unpack8(chunk(sm, S::H2, col / 8 + c, row), h + 8 * c);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
+            for (int j = 0; j < BW64; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ2, 4 * q + c, row) = pack8(v + 8 * c);
+            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::DZ2, col / 8 + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -605,15 +642,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
-        for (int q = q2; q < q2 + 2 / H; ++q) {
-            float v[32], h[32];
-            tc::tmem_ld32(tm + lane + kT64 + 32 * q, v);
+        for (int bk = 0; bk < NB64; ++bk) {
+            const int col = c64 + BW64 * bk;
+            float v[BW64], h[BW64];
+            tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) unpack8(chunk(sm, S::H1, 4 * q + c, row), h + 8 * c);
+            for (int c = 0; c < BW64 / 8; ++c) unpack8(chunk(sm, S::H1, col / 8 + c, row), h + 8 * c);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
+            for (int j = 0; j < BW64; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) chunk(sm, S::DZ1, 4 * q + c, row) = pack8(v + 8 * c);
+            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::DZ1, col / 8 + c, row) = pack8(v + 8 * c);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -641,29 +679,32 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     if (MODE == kTrain) {
         float *part = a.partial + (long long)blockIdx.x * kPartStride;
         // weight and bias gradients (unnormalised sums over this CTA's pixels); lane = row,
-        // each half takes half of every accumulator's weight columns
-        float v[32], w[16];
+        // each half takes half of every accumulator's weight columns.  Weight blocks are stored
+        // column by column (see param_of), so that a warp's store covers 32 consecutive floats.
+        float v[32], w[16], vb[BW64];
         const bool low = (warp & 3) < 2;   // rows 0..63: the 64-row accumulators dW2, dW1
         if (ok && !first) {
-            for (int q = q2; q < q2 + 2 / H; ++q) {
-                tc::tmem_ld32(tm + lane + kDW3 + 32 * q, v);
+            for (int bk = 0; bk < NB64; ++bk) {
+                const int col = c64 + BW64 * bk;
+                tmem_ld_block<BW64>(tm + lane + kDW3 + col, vb);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) part[kOffW3 + row * 64 + 32 * q + j] = v[j];
+                for (int j = 0; j < BW64; ++j) part[kOffW3 + (col + j) * 128 + row] = vb[j];
             }
             if (half == 0) {
                 tc::tmem_ld16(tm + lane + kDW3 + 64, w);
                 part[kOffB3 + row] = w[0];
             }
             if (low) {
-                for (int q = q2; q < q2 + 2 / H; ++q) {
-                    tc::tmem_ld32(tm + lane + kDW2 + 32 * q, v);
+                for (int bk = 0; bk < NB64; ++bk) {
+                    const int col = c64 + BW64 * bk;
+                    tmem_ld_block<BW64>(tm + lane + kDW2 + col, vb);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) part[kOffW2 + row * 64 + 32 * q + j] = v[j];
+                    for (int j = 0; j < BW64; ++j) part[kOffW2 + (col + j) * 64 + row] = vb[j];
                 }
                 for (int q = q4; q < q4 + 4 / H; ++q) {
                     tc::tmem_ld32(tm + lane + kDW1 + 32 * q, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) part[kOffW1 + row * 128 + 32 * q + j] = v[j];
+                    for (int j = 0; j < 32; ++j) part[kOffW1 + (32 * q + j) * 64 + row] = v[j];
                 }
                 if (half == 0) {
                     tc::tmem_ld16(tm + lane + kDW2 + 64, w);
@@ -742,6 +783,22 @@ __global__ void __launch_bounds__(128) features_kernel(const DevPlan *__restrict
 // sums are added in warp order.  FP32 (this GPU's FP64 rate is a small fraction of
 // its FP32 rate); the error of these short sums stays near 1e-6 of the result.
 constexpr int kReduceCols = 32, kReduceGroups = 8;
+
+// Parameter index of entry s of a per-CTA partial gradient: the weight blocks are stored column
+// by column (W1 [64][128] as [128][64], W2 [64][64] transposed, W3 [128][64] as [64][128]);
+// biases, the loss sum and the pixel count in place.
+__device__ __forceinline__ int param_of(int s) {
+    if (s < kOffB1) return (s & 63) * 128 + (s >> 6);
+    if (s >= kOffW2 && s < kOffB2) {
+        const int t = s - kOffW2;
+        return kOffW2 + (t & 63) * 64 + (t >> 6);
+    }
+    if (s >= kOffW3 && s < kOffB3) {
+        const int t = s - kOffW3;
+        return kOffW3 + (t & 127) * 64 + (t >> 7);
+    }
+    return s;
+}
 __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(const float *__restrict__ partial,
                                                                             int n_parts, float *__restrict__ grad,
                                                                             float *__restrict__ loss) {
@@ -765,7 +822,7 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(con
             ct += part_cnt[k];
         }
         const float v = ct > 0.0f ? tot / ct : 0.0f;
-        if (j < kParams) grad[j] = v;
+        if (j < kParams) grad[param_of(j)] = v;
         else if (loss) *loss = v;
     }
 }
@@ -807,8 +864,9 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_adam_kerne
         }
         const float gj = ct > 0.0f ? tot / ct : 0.0f;
         if (j < kParams) {
-            grad[j] = gj;
-            adam_update(p, m, v, j, gj, lr, beta1, beta2, eps, c1, c2);
+            const int jp = param_of(j);
+            grad[jp] = gj;
+            adam_update(p, m, v, jp, gj, lr, beta1, beta2, eps, c1, c2);
         } else if (loss) {
             *loss = gj;
         }
