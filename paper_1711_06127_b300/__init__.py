@@ -28,7 +28,7 @@ GEOMETRIES = {"linear": 0, "sector": 1, "pyramid": 2}
 EXPORTS = ("supra_plan_create", "supra_plan_destroy", "supra_plan_get_info", "supra_beamform", "supra_envelope",
            "supra_logcompress", "supra_scanconvert", "supra_bmode_workspace_size", "supra_bmode",
            "supra_bmode_batched", "supra_bmode_noalloc", "supra_mv", "supra_apod_features", "supra_apod_forward",
-           "supra_apod_workspace_size", "supra_apod_grad", "supra_apod_adam", "supra_apod_step", "supra_apod_mlp",
+           "supra_apod_workspace_size", "supra_apod_grad", "supra_apod_adam", "supra_apod_step", "supra_apod_epoch", "supra_apod_mlp",
            "supra_render", "supra_plan_set_max_group", "supra_plan_get_max_group", "supra_autotune_bmode",
            "supra_plan_set_tile_shape", "supra_plan_get_tile_shape", "supra_autotune_tile_shape", "supra_server_create",
            "supra_server_submit", "supra_server_submit_trace", "supra_server_poll", "supra_server_wait",
@@ -130,6 +130,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_apod_adam.argtypes = [P, P, P, P, ctypes.c_int32, F, F, F, F, P]
     lib.supra_apod_step.argtypes = [P, P, P, ctypes.c_int32, F, F, F, F, I64, I64, P, P, P, P, P, P, P,
                                     ctypes.c_size_t, P]
+    lib.supra_apod_epoch.argtypes = [P, P, P, ctypes.c_int32, F, F, F, F, I64, ctypes.c_int32, P, P, P, P, P, P,
+                                     P, P, ctypes.c_size_t, P]
     lib.supra_apod_mlp.argtypes = [P, P, P, P, P]
     lib.supra_render.argtypes = [ctypes.POINTER(_Grid), P, ctypes.POINTER(_Camera), P, P]
     lib.supra_plan_set_max_group.argtypes = [P, ctypes.c_int32]

@@ -143,13 +143,23 @@ class Trainer:
 
     def epoch(self, data: Dataset, n_batches: int, seed: int, stream=None) -> float:
         """One pass over the data in n_batches interleaved minibatches (order
-        shuffled with `seed`); returns the mean minibatch loss."""
+        shuffled with `seed`), the steps issued by the library in one call
+        (supra_apod_epoch); returns the mean minibatch loss."""
         import torch
 
-        order = np.random.default_rng(int(seed)).permutation(int(n_batches))
-        losses = torch.zeros(len(order), dtype=torch.float32, device=self.params.device)
-        for j, k in enumerate(order):
-            self.step(data, int(k), int(n_batches), loss_out=losses[j : j + 1], stream=stream)
+        total = _check_rows(data.feat, data.mask, data.norm, data.label)
+        n_batches = int(n_batches)
+        if n_batches < 1 or n_batches > total:
+            raise ValueError("n_batches must be in 1 .. number of rows")
+        order = np.ascontiguousarray(np.random.default_rng(int(seed)).permutation(n_batches), dtype=np.int32)
+        losses = torch.zeros(n_batches, dtype=torch.float32, device=self.params.device)
+        _check(load().supra_apod_epoch(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.step_count,
+                                       self.lr, self.betas[0], self.betas[1], self.eps, int(total), n_batches,
+                                       order.ctypes.data, data.feat.data_ptr(), data.mask.data_ptr(),
+                                       data.norm.data_ptr(), data.label.data_ptr(), self.grad.data_ptr(),
+                                       losses.data_ptr(), self.ws.data_ptr(), self.ws.numel(), _stream_ptr(stream)),
+               "supra_apod_epoch")
+        self.step_count += n_batches
         return float(losses.mean())
 
     # ---- checkpoints -----------------------------------------------------

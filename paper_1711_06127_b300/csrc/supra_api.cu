@@ -1225,6 +1225,24 @@ int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, f
     return check_cuda(cudaGetLastError());
 }
 
+int supra_apod_epoch(float *params, float *m, float *v, int32_t step0, float lr, float beta1, float beta2, float eps,
+                     int64_t n_rows, int32_t n_batches, const int32_t *order, const uint16_t *feat,
+                     const uint32_t *mask, const float *norm, const float *label, float *grad, float *losses,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+    if (!order || !losses || n_batches < 1 || n_rows < n_batches || step0 < 0) return SUPRA_EINVAL;
+    for (int b = 0; b < n_batches; ++b)
+        if (order[b] < 0 || order[b] >= n_batches) return SUPRA_EINVAL;
+    for (int b = 0; b < n_batches; ++b) {
+        const int64_t k = order[b];
+        const int64_t n = (n_rows - k + n_batches - 1) / n_batches;   // rows k, k + n_batches, ...
+        const int rc = supra_apod_step(params, m, v, step0 + b + 1, lr, beta1, beta2, eps, n, n_batches,
+                                       feat + k * apod::kIn, mask + k * 4, norm + k, label + k, grad, losses + b,
+                                       workspace, workspace_bytes, stream);
+        if (rc) return rc;
+    }
+    return SUPRA_OK;
+}
+
 int supra_apod_adam(float *params, float *m, float *v, const float *grad, int32_t step, float lr, float beta1,
                     float beta2, float eps, void *stream) {
     if (!params || !m || !v || !grad || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||

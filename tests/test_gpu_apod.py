@@ -218,6 +218,24 @@ def test_fused_training_step_equals_gradient_then_adam():
         b.step(_data(dev), base=0, stride=1, n=4000)
 
 
+def test_epoch_in_the_library_equals_the_steps_one_by_one():
+    # supra_apod_epoch (the minibatch loop in the library) against supra_apod_step called per
+    # minibatch in the same shuffled order: the same parameters, moments and losses, bit for bit
+    params = phantom.apod_init(64, out_scale=1.0, bias_scale=0.1)
+    dev, *_ = _rows(65, 4000)
+    a, b = apod.Trainer(params, lr=2e-3), apod.Trainer(params, lr=2e-3)
+    mean_loss = a.epoch(_data(dev), 5, seed=3)
+    losses = torch.zeros(5, dtype=torch.float32, device="cuda")
+    for j, k in enumerate(np.random.default_rng(3).permutation(5)):
+        b.step(_data(dev), int(k), 5, loss_out=losses[j : j + 1])
+    assert a.step_count == b.step_count == 5
+    for name in ("params", "m", "v", "grad"):
+        torch.testing.assert_close(getattr(a, name), getattr(b, name), rtol=0, atol=0)
+    assert mean_loss == float(losses.mean())
+    with pytest.raises(ValueError):
+        a.epoch(_data(dev), 0, seed=1)
+
+
 def test_fused_inference_matches_the_oracle():
     s = small_linear(64, 8, 700)
     p = s.params()
