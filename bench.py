@@ -468,7 +468,8 @@ def bench_apod(args, dev, stream):
     prep_s = time.perf_counter() - t0
     data = apod.Dataset(feat, mask, norm, label)
     tr = apod.Trainer(phantom.apod_init(7), lr=args.apod_lr)
-    # minibatches of at most eight 128-pixel tiles per SM (0 = that size): the gradient kernel runs one
+    # minibatches of interleaved blocks of 128 consecutive rows (each gradient tile reads one contiguous
+    # block), at most eight 128-pixel tiles per SM (0 = that size): the gradient kernel runs one
     # CTA per SM and pays a fixed cost per step (weight staging, tensor-memory allocation, partial
     # gradients, the reduction and Adam launch) of about two and a half tiles, so a minibatch is a
     # whole number of tile rounds and several of them long
@@ -479,7 +480,7 @@ def bench_apod(args, dev, stream):
     losses = []
     e0.record(stream)
     for ep in range(args.apod_epochs):
-        losses.append(tr.epoch(data, n_batches, seed=ep, stream=stream))
+        losses.append(tr.epoch(data, n_batches, seed=ep, stream=stream, chunk=128))
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)

@@ -299,17 +299,22 @@ SUPRA_API int supra_apod_step(float *params, float *m, float *v, int32_t step, f
                               const float *norm, const float *label, float *grad, float *loss, void *workspace,
                               size_t workspace_bytes, void *stream);
 
-/* One epoch of training: n_batches supra_apod_step calls, issued from the
- * library (no per-step round trip through the caller).  Minibatch b takes the
- * rows order[b], order[b] + n_batches, order[b] + 2 n_batches, ... < n_rows of
- * the feature arrays (interleaved minibatches; order: host array, a
- * permutation of 0 .. n_batches - 1) and is Adam step step0 + b + 1;
- * losses[b] (device float [n_batches]) receives its mean loss, grad the last
- * step's gradient.  Feature arrays as for supra_apod_step with stride 1 rows.
- * Errors: SUPRA_EINVAL (order entries out of range, n_rows < n_batches), else
- * as supra_apod_step, returned at the first failing step. */
+/* One epoch of training: n_batches minibatch steps (as supra_apod_step),
+ * issued by the library (no per-step round trip through the caller).  The
+ * rows are cut into chunks of `chunk` consecutive rows (1, or 128 = one tile
+ * of the gradient kernel; the last chunk may be partial) and minibatch b takes
+ * the chunks order[b], order[b] + n_batches, order[b] + 2 n_batches, ...
+ * (interleaved minibatches; order: host array, a permutation of 0 ..
+ * n_batches - 1); it is Adam step step0 + b + 1, losses[b] (device float
+ * [n_batches]) receives its mean loss, grad the last step's gradient.  With
+ * chunk = 1 every step equals supra_apod_step(rows order[b], stride
+ * n_batches); with 128 each tile reads consecutive rows (one contiguous
+ * block of feature rows per tile instead of rows n_batches apart).
+ * Errors: SUPRA_EINVAL (chunk not 1 or 128, order entries out of range,
+ * fewer chunks than minibatches), else as supra_apod_step, returned at the
+ * first failing step. */
 SUPRA_API int supra_apod_epoch(float *params, float *m, float *v, int32_t step0, float lr, float beta1, float beta2,
-                               float eps, int64_t n_rows, int32_t n_batches, const int32_t *order,
+                               float eps, int64_t n_rows, int32_t n_batches, int32_t chunk, const int32_t *order,
                                const uint16_t *feat, const uint32_t *mask, const float *norm, const float *label,
                                float *grad, float *losses, void *workspace, size_t workspace_bytes, void *stream);
 

@@ -130,8 +130,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.supra_apod_adam.argtypes = [P, P, P, P, ctypes.c_int32, F, F, F, F, P]
     lib.supra_apod_step.argtypes = [P, P, P, ctypes.c_int32, F, F, F, F, I64, I64, P, P, P, P, P, P, P,
                                     ctypes.c_size_t, P]
-    lib.supra_apod_epoch.argtypes = [P, P, P, ctypes.c_int32, F, F, F, F, I64, ctypes.c_int32, P, P, P, P, P, P,
-                                     P, P, ctypes.c_size_t, P]
+    lib.supra_apod_epoch.argtypes = [P, P, P, ctypes.c_int32, F, F, F, F, I64, ctypes.c_int32, ctypes.c_int32, P,
+                                     P, P, P, P, P, P, P, ctypes.c_size_t, P]
     lib.supra_apod_mlp.argtypes = [P, P, P, P, P]
     lib.supra_render.argtypes = [ctypes.POINTER(_Grid), P, ctypes.POINTER(_Camera), P, P]
     lib.supra_plan_set_max_group.argtypes = [P, ctypes.c_int32]

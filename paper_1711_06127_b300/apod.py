@@ -141,21 +141,23 @@ class Trainer:
                                       _ptr(data.label, base), self.grad.data_ptr(), out.data_ptr(), self.ws.data_ptr(),
                                       self.ws.numel(), _stream_ptr(stream)), "supra_apod_step")
 
-    def epoch(self, data: Dataset, n_batches: int, seed: int, stream=None) -> float:
+    def epoch(self, data: Dataset, n_batches: int, seed: int, stream=None, chunk: int = 1) -> float:
         """One pass over the data in n_batches interleaved minibatches (order
         shuffled with `seed`), the steps issued by the library in one call
-        (supra_apod_epoch); returns the mean minibatch loss."""
+        (supra_apod_epoch); returns the mean minibatch loss.  chunk: rows
+        interleaved one at a time (1) or in blocks of 128 consecutive rows
+        (128: each gradient tile reads one contiguous block)."""
         import torch
 
         total = _check_rows(data.feat, data.mask, data.norm, data.label)
         n_batches = int(n_batches)
-        if n_batches < 1 or n_batches > total:
-            raise ValueError("n_batches must be in 1 .. number of rows")
+        if chunk not in (1, 128) or n_batches < 1 or n_batches > -(-total // chunk):
+            raise ValueError("chunk must be 1 or 128 and n_batches in 1 .. number of chunks")
         order = np.ascontiguousarray(np.random.default_rng(int(seed)).permutation(n_batches), dtype=np.int32)
         losses = torch.zeros(n_batches, dtype=torch.float32, device=self.params.device)
         _check(load().supra_apod_epoch(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.step_count,
                                        self.lr, self.betas[0], self.betas[1], self.eps, int(total), n_batches,
-                                       order.ctypes.data, data.feat.data_ptr(), data.mask.data_ptr(),
+                                       int(chunk), order.ctypes.data, data.feat.data_ptr(), data.mask.data_ptr(),
                                        data.norm.data_ptr(), data.label.data_ptr(), self.grad.data_ptr(),
                                        losses.data_ptr(), self.ws.data_ptr(), self.ws.numel(), _stream_ptr(stream)),
                "supra_apod_epoch")

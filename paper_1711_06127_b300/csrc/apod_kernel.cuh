@@ -69,7 +69,8 @@ struct Args {
     const uint32_t *mask;
     const float *norm;
     const float *label;
-    long long n, stride;   // pixels; rows between consecutive pixels
+    long long n, stride;   // pixels; rows between consecutive pixels of a tile
+    long long tile_stride; // rows between the first pixels of consecutive 128-pixel tiles
     float *y;              // kForward: y = ||x|| * yh per pixel
     float *partial;        // kTrain: [gridDim.x][kPartStride]
     // kInfer
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     auto prefetch = [&](long long tl, int xo) {
         const long long pp = tl * kTile + row;
         nok = pp < a.n;
-        const long long rw = pp * a.stride;
+        const long long rw = tl * a.tile_stride + (long long)row * a.stride;
         if (nok) {
             const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + rw * kIn);
 #pragma unroll
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         uint32_t mk[4] = {0u, 0u, 0u, 0u};
         float nrm = 0.0f, tgt = 0.0f;
         bool row_ok;
-        long long p = 0;
+        long long p = 0, rw_out = 0;
         int line = 0, i = 0;
         if (MODE == kInfer) {
             line = (int)(tile / nblk);
@@ -427,7 +428,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         } else {
             p = tile * kTile + row;
             row_ok = p < a.n;
-            const long long rw = p * a.stride;
+            rw_out = tile * a.tile_stride + (long long)row * a.stride;
+            const long long rw = rw_out;
             if (row_ok) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + rw * kIn);
 #pragma unroll
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         const float yh = se > 0.0f ? sx / se : 0.0f;
         if (MODE == kForward) {
-            if (row_ok && half == 0) a.y[p * a.stride] = yh * nrm;
+            if (row_ok && half == 0) a.y[rw_out] = yh * nrm;
         } else if (MODE == kInfer) {
             if (row_ok && half == 0) a.rf[(long long)line * nd + i] = yh;
         } else {

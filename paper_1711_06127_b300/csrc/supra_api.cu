@@ -1172,6 +1172,7 @@ int supra_apod_forward(const float *params, int64_t n, int64_t stride, const uin
     if (!aligned16(feat) || !aligned16(mask)) return SUPRA_EINVAL;
     apod::Args a{};
     a.params = params, a.feat = feat, a.mask = mask, a.norm = norm, a.n = n, a.stride = stride, a.y = y;
+    a.tile_stride = apod::kTile * stride;
     return launch_apod<apod::kForward>(a, (n + apod::kTile - 1) / apod::kTile, 2, static_cast<cudaStream_t>(stream));
 }
 
@@ -1189,6 +1190,7 @@ int supra_apod_grad(const float *params, int64_t n, int64_t stride, const uint16
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     apod::Args a{};
     a.params = params, a.feat = feat, a.mask = mask, a.norm = norm, a.label = label, a.n = n, a.stride = stride;
+    a.tile_stride = apod::kTile * stride;
     a.partial = static_cast<float *>(workspace);
     const int rc = launch_apod<apod::kTrain>(a, tiles, 1, st);
     if (rc != SUPRA_OK) return rc;
@@ -1197,8 +1199,8 @@ int supra_apod_grad(const float *params, int64_t n, int64_t stride, const uint16
     return check_cuda(cudaGetLastError());
 }
 
-int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, float beta1, float beta2, float eps,
-                    int64_t n, int64_t stride, const uint16_t *feat, const uint32_t *mask, const float *norm,
+static int apod_step_impl(float *params, float *m, float *v, int32_t step, float lr, float beta1, float beta2,
+                          float eps, int64_t n, int64_t stride, int64_t tile_stride, const uint16_t *feat, const uint32_t *mask, const float *norm,
                     const float *label, float *grad, float *loss, void *workspace, size_t workspace_bytes,
                     void *stream) {
     if (!params || !m || !v || !feat || !mask || !norm || !label || !grad || !workspace || n <= 0 || stride < 1 ||
@@ -1214,6 +1216,7 @@ int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, f
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     apod::Args a{};
     a.params = params, a.feat = feat, a.mask = mask, a.norm = norm, a.label = label, a.n = n, a.stride = stride;
+    a.tile_stride = tile_stride;
     a.partial = static_cast<float *>(workspace);
     const int rc = launch_apod<apod::kTrain>(a, tiles, 1, st);
     if (rc != SUPRA_OK) return rc;
@@ -1225,19 +1228,39 @@ int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, f
     return check_cuda(cudaGetLastError());
 }
 
+int supra_apod_step(float *params, float *m, float *v, int32_t step, float lr, float beta1, float beta2, float eps,
+                    int64_t n, int64_t stride, const uint16_t *feat, const uint32_t *mask, const float *norm,
+                    const float *label, float *grad, float *loss, void *workspace, size_t workspace_bytes,
+                    void *stream) {
+    return apod_step_impl(params, m, v, step, lr, beta1, beta2, eps, n, stride, apod::kTile * stride, feat, mask,
+                          norm, label, grad, loss, workspace, workspace_bytes, stream);
+}
+
 int supra_apod_epoch(float *params, float *m, float *v, int32_t step0, float lr, float beta1, float beta2, float eps,
-                     int64_t n_rows, int32_t n_batches, const int32_t *order, const uint16_t *feat,
+                     int64_t n_rows, int32_t n_batches, int32_t chunk, const int32_t *order, const uint16_t *feat,
                      const uint32_t *mask, const float *norm, const float *label, float *grad, float *losses,
                      void *workspace, size_t workspace_bytes, void *stream) {
-    if (!order || !losses || n_batches < 1 || n_rows < n_batches || step0 < 0) return SUPRA_EINVAL;
+    if (!order || !losses || n_batches < 1 || step0 < 0 || (chunk != 1 && chunk != apod::kTile)) return SUPRA_EINVAL;
+    const int64_t n_chunks = (n_rows + chunk - 1) / chunk;   // the last one may be partial
+    if (n_rows < 1 || n_chunks < n_batches) return SUPRA_EINVAL;
     for (int b = 0; b < n_batches; ++b)
         if (order[b] < 0 || order[b] >= n_batches) return SUPRA_EINVAL;
     for (int b = 0; b < n_batches; ++b) {
         const int64_t k = order[b];
-        const int64_t n = (n_rows - k + n_batches - 1) / n_batches;   // rows k, k + n_batches, ...
-        const int rc = supra_apod_step(params, m, v, step0 + b + 1, lr, beta1, beta2, eps, n, n_batches,
-                                       feat + k * apod::kIn, mask + k * 4, norm + k, label + k, grad, losses + b,
-                                       workspace, workspace_bytes, stream);
+        // chunks k, k + n_batches, ... of `chunk` consecutive rows; only the dataset's last chunk can be
+        // partial, and it is then the minibatch's last
+        const int64_t nc = (n_chunks - k + n_batches - 1) / n_batches;
+        const int64_t last = k + (nc - 1) * n_batches;
+        const int64_t n = (nc - 1) * chunk + std::min<int64_t>(chunk, n_rows - last * chunk);
+        const int64_t r0 = k * chunk;
+        const int rc = chunk == 1
+                           ? supra_apod_step(params, m, v, step0 + b + 1, lr, beta1, beta2, eps, n, n_batches,
+                                             feat + r0 * apod::kIn, mask + r0 * 4, norm + r0, label + r0, grad,
+                                             losses + b, workspace, workspace_bytes, stream)
+                           : apod_step_impl(params, m, v, step0 + b + 1, lr, beta1, beta2, eps, n, 1,
+                                            (int64_t)n_batches * chunk, feat + r0 * apod::kIn, mask + r0 * 4,
+                                            norm + r0, label + r0, grad, losses + b, workspace, workspace_bytes,
+                                            stream);
         if (rc) return rc;
     }
     return SUPRA_OK;

@@ -236,6 +236,27 @@ def test_epoch_in_the_library_equals_the_steps_one_by_one():
         a.epoch(_data(dev), 0, seed=1)
 
 
+def test_epoch_of_row_blocks_equals_steps_on_the_gathered_blocks():
+    # chunk = 128: minibatch b takes the 128-row blocks order[b], order[b] + 5, ... (the dataset's
+    # last block is partial); each step equals a step on those rows gathered into one array
+    params = phantom.apod_init(66, out_scale=1.0, bias_scale=0.1)
+    dev, *_ = _rows(67, 3000)
+    a, b = apod.Trainer(params, lr=2e-3), apod.Trainer(params, lr=2e-3)
+    mean_loss = a.epoch(_data(dev), 5, seed=4, chunk=128)
+    losses = torch.zeros(5, dtype=torch.float32, device="cuda")
+    n_chunks = (3000 + 127) // 128
+    for j, k in enumerate(np.random.default_rng(4).permutation(5)):
+        rows = np.concatenate([np.arange(c * 128, min(c * 128 + 128, 3000)) for c in range(int(k), n_chunks, 5)])
+        idx = torch.as_tensor(rows).cuda()
+        sub = {name: v.index_select(0, idx).contiguous() for name, v in dev.items()}
+        b.step(_data(sub), loss_out=losses[j : j + 1])
+    for name in ("params", "m", "v", "grad"):
+        torch.testing.assert_close(getattr(a, name), getattr(b, name), rtol=0, atol=0)
+    assert mean_loss == float(losses.mean())
+    with pytest.raises(ValueError):
+        a.epoch(_data(dev), 25, seed=1, chunk=128)   # more minibatches than blocks
+
+
 def test_fused_inference_matches_the_oracle():
     s = small_linear(64, 8, 700)
     p = s.params()
