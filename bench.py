@@ -779,8 +779,11 @@ def run_ours(args):
     per_frame = s.n_tx * s.n_el * s.n_samples
     frames = BATCH * args.steps * world
     value = job_rate(per_frame * BATCH * args.steps, world, total_ms * 1e-3)
-    # the same steps one at a time on one stream: a batch's latency without a neighbour
-    one_ms, one_step_ms, _ = timed(step, args.steps, 1)
+    # the same steps one at a time on one stream: a batch's latency without a neighbour (at least
+    # 100 steps, so that the figure does not rest on a handful of launches)
+    n_one = max(args.steps, 100)
+    one_ms, one_step_ms, _ = timed(step, n_one, 1)
+    one_ms *= args.steps / n_one
 
     # ---- the dominant kernel alone: beamforming + envelope + log compression, same launch
     # shape, launches alternating over the two streams as above (and, beside it, on one stream)
@@ -960,7 +963,7 @@ def run_ours(args):
                                    f"over {n_str} streams (a step shares the GPU with its neighbours); the "
                                    f"{BATCH} frames of a step complete together"},
             "one_stream": {"ms_per_step": one_ms / args.steps, "latency_ms": {"p50": p50_one, "p99": p99_one},
-                           "note": "the same steps one after another on one stream"},
+                           "note": f"the same steps one after another on one stream ({n_one} of them)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": kernel_traffic(),
                          "kernel": f"das_kernel<{plan_lines.tile_shape['frames_per_group']},1> (beamform + envelope "
