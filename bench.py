@@ -306,7 +306,8 @@ def bench_table1(args, dev, stream):
     """The 2D configurations of the run-time table (64 channels, "n_tx / lines
     per transmit" 64/1, 64/2, 128/1, 128/2; 45 mm; 0.0225 mm isotropic output):
     per-node device time of the unfused chain (one launch per node, as the
-    paper times its nodes) and of the fused chain, single frames."""
+    paper times its nodes) and of the fused chain, single frames, each timed over
+    calls queued back to back on the device."""
     import torch
 
     import paper_1711_06127_b300 as supra
@@ -316,8 +317,14 @@ def bench_table1(args, dev, stream):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(fn, reps=20):
+        # These kernels take microseconds, less than the host needs to issue one call: the
+        # timed calls are queued behind a ~2 ms device-side wait (torch's sleep kernel, before
+        # the first event), so that the events measure the device running them back to back
+        # rather than the host's launch rate.
         for _ in range(3):
             fn()
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(4_000_000)
         ev[0].record(stream)
         for _ in range(reps):
             fn()

@@ -389,7 +389,7 @@ SUPRA_API int32_t supra_plan_get_max_group(const supra_plan *plan);
  * events on `stream` (reps timed calls after one warm-up each) for the shape
  * in effect and then for each frames-per-group class crossed with the
  * settings its launches use (stage shapes of 16-frame groups; depth segments
- * 0, 1, 2, 4, 8 of the others; CTAs per SM 0, 2, 3 of one-frame launches),
+ * 0 to 6 and 8 of the others; CTAs per SM 0, 2, 3 of one-frame launches),
  * keeps the fastest shape in the plan and returns it with its time per call
  * and the time of the shape in effect before (start_ms; may be NULL).  The
  * outputs do not depend on the shape.  Synchronizes the stream; on an error

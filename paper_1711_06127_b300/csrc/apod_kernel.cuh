@@ -801,6 +801,35 @@ __device__ __forceinline__ int param_of(int s) {
     }
     return s;
 }
+// Warp g's sums for column j: partials g, g + 8, g + 16, ... added in that order (and, on the
+// count lane, their pixel counts); the rows are loaded four at a time ahead of the adds.
+__device__ __forceinline__ void column_sum(const float *__restrict__ partial, int n_parts, int j, bool count_lane,
+                                           int g, float &s, float &cnt) {
+    constexpr int U = 4;
+    s = 0.0f, cnt = 0.0f;
+    const bool col = j <= kParams;
+    int c = g;
+    for (; c + (U - 1) * kReduceGroups < n_parts; c += U * kReduceGroups) {
+        float v[U], w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float *row = partial + (long long)(c + u * kReduceGroups) * kPartStride;
+            v[u] = col ? row[j] : 0.0f;
+            w[u] = count_lane ? row[kParams + 1] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            s += v[u];
+            cnt += w[u];
+        }
+    }
+    for (; c < n_parts; c += kReduceGroups) {
+        const float *row = partial + (long long)c * kPartStride;
+        if (col) s += row[j];
+        if (count_lane) cnt += row[kParams + 1];
+    }
+}
+
 __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(const float *__restrict__ partial,
                                                                             int n_parts, float *__restrict__ grad,
                                                                             float *__restrict__ loss) {
@@ -808,12 +837,8 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(con
     __shared__ float part_cnt[kReduceGroups];
     const int lane = threadIdx.x % kReduceCols, g = threadIdx.x / kReduceCols;
     const int j = blockIdx.x * kReduceCols + lane;
-    float s = 0.0f, cnt = 0.0f;
-    for (int c = g; c < n_parts; c += kReduceGroups) {
-        const float *row = partial + (long long)c * kPartStride;
-        if (j <= kParams) s += row[j];
-        if (lane == 0) cnt += row[kParams + 1];
-    }
+    float s, cnt;
+    column_sum(partial, n_parts, j, lane == 0, g, s, cnt);
     part_sum[g][lane] = s;
     if (lane == 0) part_cnt[g] = cnt;
     __syncthreads();
@@ -849,12 +874,8 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_adam_kerne
     __shared__ float part_cnt[kReduceGroups];
     const int lane = threadIdx.x % kReduceCols, g = threadIdx.x / kReduceCols;
     const int j = blockIdx.x * kReduceCols + lane;
-    float s = 0.0f, cnt = 0.0f;
-    for (int c = g; c < n_parts; c += kReduceGroups) {
-        const float *row = partial + (long long)c * kPartStride;
-        if (j <= kParams) s += row[j];
-        if (lane == 0) cnt += row[kParams + 1];
-    }
+    float s, cnt;
+    column_sum(partial, n_parts, j, lane == 0, g, s, cnt);
     part_sum[g][lane] = s;
     if (lane == 0) part_cnt[g] = cnt;
     __syncthreads();

@@ -41,6 +41,7 @@ struct DevPlan {
     int n_el, n_tx, n_lines, n_depth, n_s;
     int n_tiles;             // ceil(n_depth / kDepthTile)
     int regular, el_nx, el_ny;   // elements on a row-major nx x ny grid (e = iy * nx + ix)
+    int row_y;               // regular, and the elements of each grid row have the same (fp32) y
     int window;
     float win_a, win_b;      // apodization window A + B cos(pi u)
     int win_row;             // staged samples per element row (multiple of 8)

@@ -78,8 +78,11 @@ struct ElemMeta {
     int ws;                      // absolute sample index of the row's first staged sample
     int ia, ib;                  // depths (absolute indices) this staged window serves
     int flags;                   // bit 0 valid, bits 1-2 width class, bit 3 (slot 0): last stage of the tile,
-                                 // bits 4-15: compounded transmit of the stage
+                                 // bits 4-15: compounded transmit of the stage, bit 16 (slot 0): row stage
 };
+// A row stage (one-frame tiles of plans with a y window) holds elements of one row of the
+// matrix array, so its y window weight is the same for every element.
+constexpr int kRowStage = 1 << 16;
 __device__ __forceinline__ int meta_valid(const ElemMeta &m) { return m.flags & 1; }
 __device__ __forceinline__ int meta_widx(const ElemMeta &m) { return (m.flags >> 1) & 3; }
 __device__ __forceinline__ int meta_last(const ElemMeta &m) { return (m.flags >> 3) & 1; }
@@ -137,6 +140,18 @@ __device__ __forceinline__ uint32_t biased(uint32_t u16) { return (u16 ^ 0x8000u
 // Apodization window A + B cos(pi u): Hann (1/2, 1/2), Hamming (0.54, 0.46), rect (1, 0).
 __device__ __forceinline__ float window_weight(float A, float B, float u) {
     return fmaf(B, __cosf(3.14159265358979f * u), A);
+}
+
+// floor(s) and its integer value on the FMA and integer pipes (no rounding or
+// conversion instruction): s + 1.5 * 2^23 rounded toward -inf lands in [2^23, 2^24),
+// where the floats are the integers and consecutive ones have consecutive bit
+// patterns, so it is floor(s) + 1.5 * 2^23 exactly.  Exact for |s| < 2^22 (the
+// delays are a few thousand samples; lanes outside the aperture only clamp k).
+constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
+__device__ __forceinline__ float floor_split(float s, int &k) {
+    const float t = __fadd_rd(s, kFloorMagic);
+    k = __float_as_int(t) - __float_as_int(kFloorMagic);
+    return t - kFloorMagic;
 }
 
 // |o + r d - q| - r without cancellation: (gamma + 2 r beta) / (|p - q| + r),
@@ -461,16 +476,56 @@ __device__ __forceinline__ Geo element_geo(const ElemMeta &md, int i, float r, f
     const float r2 = fmaxf(fmaf(r, r, num), 1e-30f);                      // |p - x_e|^2
     const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);            // |p - x_e| + r
     const float s = fmaf(__fdividef(num, den), fsc, base);
-    const float fl = floorf(s);
+    int k;
+    const float fl = floor_split(s, k);
 #ifdef SUPRA_CHECKED
     // every sample pair an in-aperture depth reads lies inside the element's staged window
-    const int raw = kt + (int)fl - md.ws;
+    const int raw = kt + k - md.ws;
     SUPRA_CHECK(!in || !meta_valid(md) || (raw >= 0 && raw + 1 < width_of(meta_widx(md))));
 #endif
     g.w = w;
     g.w1 = w * (s - fl);
     g.w0 = w - g.w1;
-    g.idx = min(max(kt + (int)fl - md.ws, 0), width_of(kNumWidths - 1) - 2);
+    // (clamped for lanes outside the aperture, whose weights are 0; a negative index wraps high)
+    g.idx = (int)min((unsigned)(kt + k - md.ws), (unsigned)(width_of(kNumWidths - 1) - 2));
+    return g;
+}
+
+// The same for one-frame tiles, without the warp vote: an element's frame work is a few
+// instructions, less than the vote and branch that would skip it, so every slot is applied
+// and a lane outside the aperture, or a slot past the stage's valid prefix, has weight 0.
+// YM: 0 no y window (linear arrays), 1 the element's own, 2 the row stage's (wy, iny).
+template <int YM>
+__device__ __forceinline__ Geo element_geo1(const ElemMeta &md, int i, float r, float qx, float qy, float inv_a,
+                                            float base, int kt, float wa, float wb, float fsc, float wy, bool iny) {
+    Geo g;
+    const float ux = (md.ex - qx) * inv_a;
+    bool in = fabsf(ux) <= 1.0f && i >= md.ia && i <= md.ib && meta_valid(md);
+    float w = window_weight(wa, wb, ux);
+    if constexpr (YM == 1) {
+        const float uy = (md.ey - qy) * inv_a;
+        in = in && fabsf(uy) <= 1.0f;
+        w *= window_weight(wa, wb, uy);
+    } else if constexpr (YM == 2) {
+        in = in && iny;
+        w *= wy;
+    }
+    g.go = true;
+    w = in ? w : 0.0f;
+    const float num = fmaf(r, md.beta2, md.gamma);
+    const float r2 = fmaxf(fmaf(r, r, num), 1e-30f);
+    const float den = fmaxf(fmaf(r2, rsqrtf(r2), r), 1e-20f);
+    const float s = fmaf(__fdividef(num, den), fsc, base);
+    int k;
+    const float fl = floor_split(s, k);
+#ifdef SUPRA_CHECKED
+    const int raw = kt + k - md.ws;
+    SUPRA_CHECK(!in || (raw >= 0 && raw + 1 < width_of(meta_widx(md))));
+#endif
+    g.w = w;
+    g.w1 = w * (s - fl);
+    g.w0 = w - g.w1;
+    g.idx = (int)min((unsigned)(kt + k - md.ws), (unsigned)(width_of(kNumWidths - 1) - 2));
     return g;
 }
 
@@ -513,13 +568,48 @@ __device__ __forceinline__ void element_frames_w(const int16_t *rows, int widx, 
 
 constexpr int kSlotSamples = width_of(kNumWidths - 1);   // samples per frame row reserved in a slot
 
+// One-frame stages (32 slots): groups of four slots, their geometry first (independent
+// chains), then their samples; valid slots are a prefix.
+template <int YM>
+__device__ __forceinline__ void consume_one_frame(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int i,
+                                                  float r, float qx, float qy, float inv_a, float base, int kt,
+                                                  float wa, float wb, float fsc, float wy, bool iny, float &acc1,
+                                                  float &wsum) {
+    constexpr int kGrp = 4;
+    u64 unused[1];
+#pragma unroll 1
+    for (int e0 = 0; e0 < rows_of(1); e0 += kGrp) {
+        if (!meta_valid(meta[e0])) break;
+        Geo g[kGrp];
+#pragma unroll
+        for (int j = 0; j < kGrp; ++j)
+            g[j] = element_geo1<YM>(meta[e0 + j], i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, wy, iny);
+#pragma unroll
+        for (int j = 0; j < kGrp; ++j) {
+            element_frames<1, 0>(sbuf + (e0 + j) * kSlotSamples, g[j], unused, acc1);
+            wsum += g[j].w;
+        }
+    }
+}
+
 template <int G, int SH>
 __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int i, float r,
                                               float qx, float qy, float inv_a, float base, int kt,
                                               bool use_y, float wa, float wb, float fsc,
                                               u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1, float &wsum) {
     constexpr int E = rows_of(G, SH) / G;
-    if constexpr (E <= 4) {
+    if constexpr (G == 1) {
+        const int f0 = meta[0].flags;
+        if (!use_y) {
+            consume_one_frame<0>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1, wsum);
+        } else if (f0 & kRowStage) {
+            const float uy = (meta[0].ey - qy) * inv_a;
+            consume_one_frame<2>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, window_weight(wa, wb, uy),
+                                 fabsf(uy) <= 1.0f, acc1, wsum);
+        } else {
+            consume_one_frame<1>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1, wsum);
+        }
+    } else if constexpr (E <= 4) {
         // geometry of every slot first (independent chains), then the frame loops
         Geo g[E];
         int widx[E];
@@ -735,17 +825,31 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
     const int tid = threadIdx.x;
     const long long row_off = (long long)line * nd;
     if constexpr (G == 1) {
-        const int o = i0 - kLag + tid;
-        if (o < 0 || o >= nd || nf < 1) return;
-        float re = 0.f, im = 0.f;
+        // Two consecutive outputs per thread (threads 0..127): output t + 1 reads at tap k + 1
+        // the ring position that output t reads at tap k, so each tap loads one new position.
+        // An output's (I, Q) is one f32x2 pair updated with the tap pair (c_k, s_k) (taps4 holds
+        // (c, s, c, s) here), tap by tap in the same order as one output per thread.
+        if (tid >= kTD / 2 || nf < 1) return;
+        const int t0 = 2 * tid;
+        const float2 *cs = reinterpret_cast<const float2 *>(taps4);
+        u64 q0 = 0ull, q1 = 0ull;
+        float vb = ring[ring_addr(64 + t0)];   // output t0 + 1 at tap 0
 #pragma unroll 8
         for (int k = 0; k < kTapSlots; ++k) {
-            const float v = ring[ring_addr(63 + tid - k)];
-            const float4 t = taps4[k];
-            re = fmaf(t.x, v, re);
-            im = fmaf(t.z, v, im);
+            const float va = ring[ring_addr(63 + t0 - k)];   // output t0 at tap k
+            const float2 c = cs[2 * k];
+            const u64 C = pack2(c.x, c.y);
+            q0 = fma2(C, pack2(va, va), q0);
+            q1 = fma2(C, pack2(vb, vb), q1);
+            vb = va;
         }
-        static_cast<uint8_t *>(fg.out[0])[row_off + o] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
+        uint8_t *out = static_cast<uint8_t *>(fg.out[0]) + row_off;
+        const int o = i0 - kLag + t0;
+        float re, im;
+        unpack2(q0, re, im);
+        if (o >= 0 && o < nd) out[o] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
+        unpack2(q1, re, im);
+        if (o + 1 >= 0 && o + 1 < nd) out[o + 1] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
     } else {
         constexpr int NP = G / 2;
         constexpr int TPP = kConsumers / NP;
@@ -854,7 +958,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
     } else if (MODE == 1) {
         for (int k = tid; k < kTapSlots; k += (int)blockDim.x) {
             const float c = P->taps_c[k], s = P->taps_s[k];
-            taps4[k] = make_float4(c, c, s, s);
+            taps4[k] = G == 1 ? make_float4(c, s, c, s) : make_float4(c, c, s, s);
         }
         for (int k = tid; k < G * lay.ring_stride; k += (int)blockDim.x) ring[k] = 0.f;
     }
@@ -876,6 +980,10 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
         const int lane = tid & 31;
         const float lip = fmaxf(fabsf(lg.dx), fabsf(lg.dy)) + fabsf(lg.dz) * C.inv2f;
         const bool halves = C.a1 > 1.0f + 1e-6f;
+        // one-frame tiles of plans with a y window stage each row of the element box as its own
+        // stage (when the row fits one), so that the consumers weigh y once per stage
+        const bool y_win = G == 1 && !halves && P->row_y && (P->el_ny > 1 || P->ymax > P->ymin);
+        bool rows = false;      // the current tile stages row by row
         int n = 0;              // stages issued
         int slot = 0;           // filled slots of stage n
         uint32_t bytes = 0;     // bytes of stage n this lane has put in flight
@@ -888,9 +996,11 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
         auto finalize = [&](bool last) {
             const int sb = n % kStages;
             ElemMeta *meta = metas + sb * kRows;
-            if (lane >= slot && lane < E) meta[lane].flags = 0;
+            // unused slots: zero geometry too (one-frame consumers apply every slot with weight 0,
+            // and 0 times a delay made from uninitialised bytes could be NaN)
+            if (lane >= slot && lane < E) meta[lane] = ElemMeta{};
             __syncwarp();
-            if (lane == 0 && last) meta[0].flags |= 8;
+            if (lane == 0 && (last || rows)) meta[0].flags |= (last ? 8 : 0) | (rows ? kRowStage : 0);
             const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
             __syncwarp();
             if (lane == 0) mbar_arrive_expect_tx(&full[sb], total);
@@ -909,7 +1019,10 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
             const short4 b = __ldg(&C.ap_box[line * C.n_tiles + tile]);
             // a halo tile (before the segment's first) feeds the FIR its last kHalo depths only
             const int i_first = tile * kTD + (tile < T0 ? kTD - kHalo : 0);
-            const int nbox = (b.y - b.x + 1) * (b.w - b.z + 1) * (halves ? 2 : 1);
+            const int nbx = b.y - b.x + 1;
+            const int nbox = nbx * (b.w - b.z + 1) * (halves ? 2 : 1);
+            rows = y_win && nbx <= E;
+            const int step = rows ? nbx : 32;   // items per producer pass: a row, or 32 lanes
             // Stage the active elements, E per stage, and mark the tile's last stage.  With a few
             // elements per stage (G >= 8) a full stage is handed over when the next element
             // needs a slot or the pass ends, so the last stage is known then; with many (a
@@ -918,20 +1031,22 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
             constexpr bool kDefer = G >= 8;
             int nst = 0, emitted = 0;
             if constexpr (!kDefer) {
-                int nact = 0;
-                for (int jb = 0; jb < nbox; jb += 32) {
+                int nact = 0, nrows = 0;
+                for (int jb = 0; jb < nbox; jb += step) {
                     int e, ia, ib;
                     float4 xe;
-                    bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                    bool a = lane < step && element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
                     if (tile < T0) a = a && ib >= i_first;
-                    nact += __popc(__ballot_sync(0xffffffffu, a));
+                    const int c = __popc(__ballot_sync(0xffffffffu, a));
+                    nact += c;
+                    nrows += c > 0 ? 1 : 0;
                 }
-                nst = max(1, (nact + E - 1) / E);
+                nst = max(1, rows ? nrows : (nact + E - 1) / E);
             }
-            for (int jb = 0; jb < nbox && ok; jb += 32) {
+            for (int jb = 0; jb < nbox && ok; jb += step) {
                 int e, ia, ib;
                 float4 xe;
-                bool a = element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
+                bool a = lane < step && element_range(C, lg, lip, b, tile, halves, jb + lane, e, xe, ia, ib);
                 if (tile < T0) {   // halo tile: only depths from i_first on
                     a = a && ib >= i_first;
                     ia = max(ia, i_first);
@@ -976,6 +1091,10 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
                         ++emitted;
                         finalize(final_ci && emitted == nst);
                     }
+                }
+                if (!kDefer && rows && ok && slot > 0) {   // the row's stage
+                    ++emitted;
+                    finalize(final_ci && emitted == nst);
                 }
             }
             // the pass's last stage (an empty one when the tile's final pass staged nothing)

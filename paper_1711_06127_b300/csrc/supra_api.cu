@@ -547,6 +547,8 @@ int supra_plan_create(const supra_probe *probe, const supra_scan *scan, const su
     for (int e = 0; e < n_el; ++e)
         elem[e] = make_float4((float)probe->elem_pos[3 * e], (float)probe->elem_pos[3 * e + 1],
                               (float)probe->elem_pos[3 * e + 2], 0.f);
+    H.row_y = reg.ok;
+    for (int e = 0; e < n_el && H.row_y; ++e) H.row_y = elem[e].y == elem[e - e % H.el_nx].y;
     // transmit terms of a (line, transmit) pair: spherical (b = d.(o_l - o_t), g = |o_l - o_t|^2)
     // or plane wave (b = n.(o_l - o_t), g = n.d - 1)
     auto tx_term = [&](int l, int t) {
@@ -1086,14 +1088,14 @@ int supra_autotune_tile_shape(supra_plan *plan, int32_t n, const int16_t *const 
     supra_plan_get_tile_shape(plan, &before);
     // candidates: the shape in effect first (its time is start_ms), then every frames-per-group
     // class with the settings that class's launches use -- the stage shape for 16-frame groups,
-    // depth segments for the others (0 = automatic, then 1, 2, 4, 8 per line), resident CTAs
+    // depth segments for the others (0 = automatic, then 1 to 6 or 8 per line), resident CTAs
     // per SM for one-frame launches
     std::vector<supra_tile_shape> cand{before};
     for (int g : {16, 8, 4, 2, 1}) {
         if (g > 1 && g / 2 >= n) continue;   // same launches as a smaller class
         const bool tc = g == 16 && n > 8;     // 16-frame groups: whole lines, FIR on the tensor cores
         for (int sh = 0; sh < (tc ? kStageShapes : 1); ++sh)
-            for (int seg : {0, 1, 2, 4, 8}) {
+            for (int seg : {0, 1, 2, 3, 4, 5, 6, 8}) {
                 if (tc && seg) continue;
                 for (int c : {0, 2, 3}) {
                     if (c && g != 1) continue;
