@@ -344,6 +344,8 @@ def bench_table1(args, dev, stream):
         ws = torch.empty(max(1, supra.workspace_size([plan])), dtype=torch.uint8, device=dev)
 
         def chains():
+            # the workspace for the plan's tile shape in effect (depth-segment boundary records)
+            ws = torch.empty(max(1, supra.workspace_size([plan])), dtype=torch.uint8, device=dev)
             nodes = {"beamformer": timed(lambda: plan.beamform(ch, rf, stream)),
                      "envelope": timed(lambda: plan.envelope(rf, env, stream)),
                      "log_compression": timed(lambda: plan.logcompress(env, bm, stream)),

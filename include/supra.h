@@ -200,9 +200,16 @@ SUPRA_API int supra_logcompress(const supra_plan *plan, const float *env, uint8_
  *   bm: uint8 [n_lines][n_depth], img: uint8 [nz][ny][nx] (device)        */
 SUPRA_API int supra_scanconvert(const supra_plan *plan, const uint8_t *bm, uint8_t *img, void *stream);
 
-/* Bytes of device workspace the fused chain needs for these n frames (the
- * log-compressed lines of every frame that is scan converted, 256-byte
- * aligned each).  0 when no frame has a grid. */
+/* Bytes of device workspace for the fused chain of these n frames: the
+ * log-compressed lines of every frame that is scan converted (256-byte aligned
+ * each; frames of frequency-compounding plans also hold their RF and
+ * envelope), then the depth-segment boundary records (128 FP32 RF samples per
+ * line and boundary of frames whose one-frame launches split their lines
+ * along depth).  The lines are required; a workspace without room for the
+ * records makes each segment beamform the 64 depths before it that its first
+ * outputs filter (the same output bytes, more work).  The records follow the
+ * plans' tile shapes in effect: size the workspace after setting or tuning
+ * them.  0 when neither applies. */
 SUPRA_API size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *plans);
 
 /* Fused chain of one frame: beamforming, envelope and log compression in one
@@ -211,9 +218,10 @@ SUPRA_API size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *
  * supra_beamform(ch)))) up to floating-point rounding.
  *   ch:  int16 [n_tx][n_el][n_samples] (device)
  *   out: uint8 [nz][ny][nx] with a grid, else uint8 [n_lines][n_depth]
- *   workspace: device memory of at least supra_bmode_workspace_size(1, &plan)
- *   bytes, 256-byte aligned (may be NULL when that size is 0).  Calls that
- *   share a workspace must not overlap on the device.                     */
+ *   workspace: device memory of supra_bmode_workspace_size(1, &plan) bytes,
+ *   256-byte aligned; at least the frame's lines (else SUPRA_EWORKSPACE); may
+ *   be NULL when the plan has no grid.  Calls that share a workspace must not
+ *   overlap on the device.                                                */
 SUPRA_API int supra_bmode(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *workspace, size_t workspace_bytes,
                 void *stream);
 
@@ -392,8 +400,10 @@ SUPRA_API int32_t supra_plan_get_max_group(const supra_plan *plan);
  * 0 to 6 and 8 of the others; CTAs per SM 0, 2, 3 of one-frame launches),
  * keeps the fastest shape in the plan and returns it with its time per call
  * and the time of the shape in effect before (start_ms; may be NULL).  The
- * outputs do not depend on the shape.  Synchronizes the stream; on an error
- * the plan keeps its shape. */
+ * outputs do not depend on the shape.  Trials that need more workspace than
+ * the one given (shapes with more depth segments) run in a temporary one it
+ * allocates and frees.  Synchronizes the stream; on an error the plan keeps
+ * its shape. */
 SUPRA_API int supra_autotune_tile_shape(supra_plan *plan, int32_t n, const int16_t *const *ch, uint8_t *const *out,
                                         void *workspace, size_t workspace_bytes, int32_t reps, void *stream,
                                         supra_tile_shape *best, float *best_ms, float *start_ms);
@@ -486,11 +496,12 @@ SUPRA_API void supra_server_destroy(supra_server *s);
  * framework's pool.  It runs the same kernels as supra_bmode, taking the
  * scratch for the frame's log-compressed lines from a fixed 8 MiB array in the
  * library's device memory, and allocates nothing.
- *   - Frames whose workspace, supra_bmode_workspace_size(1, &plan), exceeds
- *     8 MiB (8388608 bytes) are rejected with SUPRA_EINVAL before anything is
- *     launched.  That is n_lines * n_depth bytes for one-band plans; plans
- *     with frequency compounding (n_bands > 1) also need two FP32 RF-sized
- *     buffers (9 bytes per line sample), so their frames may be 1/9 as large.
+ *   - Frames whose required workspace exceeds 8 MiB (8388608 bytes) are
+ *     rejected with SUPRA_EINVAL before anything is launched.  That is
+ *     n_lines * n_depth bytes for one-band plans with a grid; plans with
+ *     frequency compounding (n_bands > 1) also need two FP32 RF-sized buffers
+ *     (9 bytes per line sample), so their frames may be 1/9 as large.  The
+ *     depth-segment boundary records use the rest of the array when they fit.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and keeps it for that device's context; make that
  *     first call before any stream capture.  After a device reset the next

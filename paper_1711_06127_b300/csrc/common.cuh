@@ -104,6 +104,11 @@ struct LaunchGroups {
     int total_lines;
     int uniform;                         // every group uses the same plan
     int n_seg;                           // depth segments per line (0 or 1: whole lines); CTA = (item, segment)
+    // B-mode launches with depth segments: records of the RF around each segment boundary
+    // (float [item][frame < G][n_seg - 1][128]), from which a second kernel finishes the
+    // outputs there; nullptr: each segment beamforms the halo it needs itself
+    float *bnd;
+    long long bnd_floats;
     FrameGroup g[kMaxGroupsPerLaunch];
 };
 static_assert(sizeof(LaunchGroups) <= 32000, "kernel parameter space is 32 KB");

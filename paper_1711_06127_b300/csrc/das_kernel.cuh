@@ -818,10 +818,12 @@ __device__ __forceinline__ bool fir_tc_wait(uint64_t *bar, int tile, volatile in
 
 // Other group sizes: frame pairs with BO = G / 2 outputs per thread (G >= 2), or one
 // output per thread (G == 1); addresses computed at run time.
+// Outputs t < t_min of the tile are not written (a segment's first outputs, finished from
+// the boundary records).
 template <int G>
 __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int nf, int line, int i0, int nd,
                                                      const float *ring, int RS, const float4 *taps4, float a2,
-                                                     float b2) {
+                                                     float b2, int t_min) {
     const int tid = threadIdx.x;
     const long long row_off = (long long)line * nd;
     if constexpr (G == 1) {
@@ -829,8 +831,8 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
         // the ring position that output t reads at tap k, so each tap loads one new position.
         // An output's (I, Q) is one f32x2 pair updated with the tap pair (c_k, s_k) (taps4 holds
         // (c, s, c, s) here), tap by tap in the same order as one output per thread.
-        if (tid >= kTD / 2 || nf < 1) return;
         const int t0 = 2 * tid;
+        if (tid >= kTD / 2 || nf < 1 || t0 + 1 < t_min) return;
         const float2 *cs = reinterpret_cast<const float2 *>(taps4);
         u64 q0 = 0ull, q1 = 0ull;
         float vb = ring[ring_addr(64 + t0)];   // output t0 + 1 at tap 0
@@ -847,7 +849,7 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
         const int o = i0 - kLag + t0;
         float re, im;
         unpack2(q0, re, im);
-        if (o >= 0 && o < nd) out[o] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
+        if (o >= 0 && o < nd && t0 >= t_min) out[o] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
         unpack2(q1, re, im);
         if (o + 1 >= 0 && o + 1 < nd) out[o + 1] = (uint8_t)code_of(fmaf(re, re, im * im), a2, b2);
     } else {
@@ -874,7 +876,7 @@ __device__ __forceinline__ void fir_log_tile_generic(const FrameGroup &fg, int n
 #pragma unroll
         for (int j = 0; j < BO; ++j) {
             const int o = i0 - kLag + bq * BO + j;
-            if (o < 0 || o >= nd) continue;
+            if (o < 0 || o >= nd || bq * BO + j < t_min) continue;
             const u64 qq = fma2(re[j], re[j], mul2(im[j], im[j]));
             float qa, qb;
             unpack2(qq, qa, qb);
@@ -897,6 +899,9 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
     constexpr int E = kRows / G;
     constexpr bool kTcFir = (MODE == 1 && G == 16);   // FIR on the tensor cores; whole lines only
     extern __shared__ __align__(128) unsigned char smem[];
+    // a boundary kernel launched after this one as a programmatic dependent may be scheduled
+    // now: its CTAs are small and wait (griddepcontrol.wait) for this grid's completion
+    asm volatile("griddepcontrol.launch_dependents;");
     if constexpr (kTcFir) {
         if (L.n_seg > 1) {   // the host never splits these lines
             if (threadIdx.x == 0) set_status(SUPRA_EINVAL);
@@ -905,19 +910,24 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
     }
     int gi, line;
     const int n_seg = kTcFir ? 1 : max(L.n_seg, 1);
-    locate_item(L, kTcFir ? (int)blockIdx.x : (int)blockIdx.x / n_seg, gi, line);
+    const int item = kTcFir ? (int)blockIdx.x : (int)blockIdx.x / n_seg;
+    locate_item(L, item, gi, line);
     const FrameGroup &fg = L.g[gi];
     const DevPlan *P = fg.plan;
     const int nf = min(fg.n, G);
     const int NT = P->n_tiles;
     const int nd = P->n_depth;
-    // Depth segment: tiles [T0, T1) of the line emit their outputs.  With the envelope,
-    // a segment after the first also beamforms tile T0 - 1 (its RF becomes the FIR's
-    // leading halo; its outputs belong to the previous segment), and the last segment
-    // runs the lag tile after the last one.
+    // Depth segment: tiles [T0, T1) of the line emit their outputs.  With the envelope, the
+    // FIR outputs within kLag of a segment boundary need RF from both sides: either a segment
+    // after the first also beamforms the last kHalo depths of tile T0 - 1 (the FIR's leading
+    // halo; its outputs belong to the previous segment), or, given boundary records, the
+    // segments write the kHalo RF depths on their side of each boundary to its record and
+    // leave the 64 outputs around it to boundary_fir_kernel.  The last segment runs the lag
+    // tile after the last one.
     const int seg = kTcFir ? 0 : (int)blockIdx.x % n_seg;
     const int T0 = kTcFir ? 0 : seg * NT / n_seg, T1 = kTcFir ? NT : (seg + 1) * NT / n_seg;
-    const int tb = (MODE == 1 && T0 > 0) ? T0 - 1 : T0;
+    const bool records = !kTcFir && MODE == 1 && n_seg > 1 && L.bnd != nullptr;
+    const int tb = (MODE == 1 && T0 > 0 && !records) ? T0 - 1 : T0;
     const int te = T1 + ((MODE == 1 && seg == n_seg - 1) ? 1 : 0);
     const SmemLayout lay(G, MODE, kSlotSamples, SH);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bars);
@@ -1253,8 +1263,25 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
 #pragma unroll
             for (int g = 0; g < G; ++g) ring[g * lay.ring_stride + a] = v[g];
             consumer_sync();
+            const bool head = records && tile == T0 && seg > 0;           // RF depths B .. B + 63
+            const bool tail = records && tile == T1 - 1 && seg < n_seg - 1; // RF depths B' - 64 .. B' - 1
+            if (head || tail) {
+                // record of boundary b: slot u holds RF depth B_b - 64 + u (u < 128), as ring
+                // position u does in the tile that starts at B_b
+                const long long nb = n_seg - 1;
+                for (int k = m; k < nf * 2 * kHalo; k += kConsumers) {
+                    const int g = k / (2 * kHalo), j = k % (2 * kHalo);
+                    const bool hd = j < kHalo;
+                    if (hd ? !head : !tail) continue;
+                    const long long rec = (((long long)item * G + g) * nb + (hd ? seg - 1 : seg)) * (2 * kHalo);
+                    const int u = hd ? kHalo + j : j - kHalo;   // record slot
+                    const int p = hd ? kHalo + j : kTD + (j - kHalo);   // ring position
+                    if (SUPRA_CHECK(rec + u < L.bnd_floats)) L.bnd[rec + u] = ring[g * lay.ring_stride + ring_addr(p)];
+                }
+            }
             if (tile >= T0)   // a halo tile's outputs belong to the previous segment
-                fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, P->log_a2, P->log_b2);
+                fir_log_tile_generic<G>(fg, nf, line, i0, nd, ring, lay.ring_stride, taps4, P->log_a2, P->log_b2,
+                                        head ? kHalo : 0);
             consumer_sync();
             // keep the last kHalo RF samples as the next tile's leading halo
             for (int k = m; k < G * kHalo; k += kConsumers) {
@@ -1277,6 +1304,48 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
             tc::fence_after_sync();
             tc::tmem_free(tbase, kFirTmemCols);
         }
+    }
+}
+
+// The 64 outputs around each depth-segment boundary of a B-mode launch with boundary
+// records (one CTA of 64 threads per line and boundary, frames in turn): output
+// B - kLag + t from record slots 63 + t - k' with the taps, in the order, and the log code
+// of fir_log_tile_generic, so that the codes are those of an unsegmented launch bit for bit.
+constexpr int kBoundaryThreads = 2 * kLag;
+__global__ void __launch_bounds__(kBoundaryThreads) boundary_fir_kernel(const __grid_constant__ LaunchGroups L, int G) {
+    __shared__ float rec_s[2 * kHalo];
+    __shared__ float2 taps_s[kTapSlots];
+    const int nb = L.n_seg - 1;
+    if (nb < 1) return;
+    const int item = (int)blockIdx.x / nb, b = (int)blockIdx.x % nb;
+    int gi, line;
+    locate_item(L, item, gi, line);
+    const FrameGroup &fg = L.g[gi];
+    const DevPlan *P = fg.plan;
+    const int nf = min(fg.n, G), nd = P->n_depth;
+    const int B = (b + 1) * P->n_tiles / L.n_seg * kTD;   // first depth of segment b + 1
+    const int t = threadIdx.x, o = B - kLag + t;
+    for (int k = t; k < kTapSlots; k += kBoundaryThreads) taps_s[k] = make_float2(P->taps_c[k], P->taps_s[k]);
+    // launched as a programmatic dependent of the beamforming kernel: its records (and its
+    // other outputs) are complete and visible after this wait (a no-op in a plain launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int f = 0; f < nf; ++f) {
+        const long long rec = (((long long)item * G + f) * nb + b) * (2 * kHalo);
+        __syncthreads();
+        for (int u = t; u < 2 * kHalo; u += kBoundaryThreads)
+            rec_s[u] = SUPRA_CHECK(rec + u < L.bnd_floats) ? L.bnd[rec + u] : 0.0f;
+        __syncthreads();
+        float re = 0.f, im = 0.f;
+#pragma unroll 16
+        for (int k = 0; k < kTapSlots; ++k) {
+            const float v = rec_s[63 + t - k];
+            const float2 c = taps_s[k];
+            re = fmaf(c.x, v, re);
+            im = fmaf(c.y, v, im);
+        }
+        if (o < nd)
+            static_cast<uint8_t *>(fg.out[f])[(long long)line * nd + o] =
+                (uint8_t)code_of(fmaf(re, re, im * im), P->log_a2, P->log_b2);
     }
 }
 

@@ -14,6 +14,7 @@
 
 #include <mutex>
 
+#include "internal.h"
 #include "supra.h"
 
 namespace {
@@ -89,10 +90,15 @@ int scratch_on_current_device(void **out) {
 
 extern "C" SUPRA_API int supra_bmode_noalloc(const supra_plan *plan, const int16_t *ch, uint8_t *out, void *stream) {
     if (!plan || !ch || !out) return SUPRA_EINVAL;
-    const size_t need = supra_bmode_workspace_size(1, &plan);
+    const size_t need = supra::bmode_min_workspace(1, &plan);
     if (need > kNoAllocScratchBytes) return SUPRA_EINVAL;
+    // the scratch also holds depth-segment boundary records when they fit (else the
+    // segments beamform their halos: the same images)
+    const bool use = supra_bmode_workspace_size(1, &plan) > 0;
     void *scratch = nullptr;
-    const int rc = scratch_on_current_device(&scratch);
-    if (rc != SUPRA_OK) return rc;
-    return supra_bmode(plan, ch, out, need ? scratch : nullptr, need ? kNoAllocScratchBytes : 0, stream);
+    if (use) {
+        const int rc = scratch_on_current_device(&scratch);
+        if (rc != SUPRA_OK) return rc;
+    }
+    return supra_bmode(plan, ch, out, use ? scratch : nullptr, use ? kNoAllocScratchBytes : 0, stream);
 }

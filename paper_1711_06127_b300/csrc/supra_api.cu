@@ -16,6 +16,7 @@
 #include "mv_kernel.cuh"
 #include "apod_kernel.cuh"
 #include "render_kernel.cuh"
+#include "internal.h"
 
 using namespace supra;
 
@@ -824,12 +825,30 @@ static size_t frame_workspace(const supra_plan *p) {
     return b;
 }
 
-size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *plans) {
-    if (n < 1 || !plans) return 0;
+// The part of the workspace a batched chain cannot run without (the frames' workspaces).
+static size_t min_workspace(int32_t n, const supra_plan *const *plans) {
     size_t total = 0;
     for (int k = 0; k < n; ++k)
         if (plans[k]) total += frame_workspace(plans[k]);
     return total;
+}
+
+// Boundary records a frame's one-frame launch with depth segments uses (its plan's setting,
+// or the automatic split of a launch of its lines alone, which bounds that of any launch it
+// shares): 128 RF samples per line and boundary.
+static size_t frame_boundary_bytes(const supra_plan *p) {
+    if (p->host.n_bands > 1) return 0;
+    const int segs = depth_segments(p->host.n_lines, p->host.n_tiles, 1, 1, p->depth_segments.load());
+    return segs > 1 ? (size_t)p->host.n_lines * (size_t)(segs - 1) * 2 * kHalo * sizeof(float) : 0;
+}
+
+size_t supra_bmode_workspace_size(int32_t n, const supra_plan *const *plans) {
+    if (n < 1 || !plans) return 0;
+    size_t bnd = 0;
+    for (int k = 0; k < n; ++k)
+        if (plans[k]) bnd += frame_boundary_bytes(plans[k]);
+    const size_t need = min_workspace(n, plans);
+    return bnd ? align_up(need, 256) + bnd : need;
 }
 
 int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t *const *ch, uint8_t *const *out,
@@ -837,9 +856,17 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
     if (n < 1 || !plans || !ch || !out) return SUPRA_EINVAL;
     for (int k = 0; k < n; ++k)
         if (!plans[k] || !ch[k] || !out[k]) return SUPRA_EINVAL;
-    const size_t need = supra_bmode_workspace_size(n, plans);
+    const size_t need = min_workspace(n, plans);
     if (need > 0 && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)))
         return SUPRA_EWORKSPACE;
+    // what the workspace holds beyond the frames' own parts takes the depth-segment boundary
+    // records (launches run in stream order, so each launch reuses the region from its start)
+    float *bnd_base = nullptr;
+    size_t bnd_bytes = 0;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255) == 0 && workspace_bytes > align_up(need, 256)) {
+        bnd_base = reinterpret_cast<float *>(static_cast<char *>(workspace) + align_up(need, 256));
+        bnd_bytes = workspace_bytes - align_up(need, 256);
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // log-compressed lines of scan-converted frames go to the workspace; frames of
     // compounding plans run beamform -> envelope (band bank) -> log compression there
@@ -908,7 +935,27 @@ int supra_bmode_batched(int32_t n, const supra_plan *const *plans, const int16_t
                 LaunchShape S;
                 S.stage_shape = sh;
                 S.ctas_per_sm = first->ctas_per_sm.load();
-                const int rc = launch_das(Gc, 1, comp == 1, L, S, st);
+                const size_t rec_floats =
+                    L.n_seg > 1 ? (size_t)L.total_lines * Gc * (size_t)(L.n_seg - 1) * 2 * kHalo : 0;
+                if (rec_floats > 0 && rec_floats * sizeof(float) <= bnd_bytes) {
+                    L.bnd = bnd_base;
+                    L.bnd_floats = (long long)rec_floats;
+                }
+                int rc = launch_das(Gc, 1, comp == 1, L, S, st);
+                if (!rc && L.bnd) {
+                    // a programmatic dependent: scheduled while the beamforming grid runs, it
+                    // waits for that grid's completion on the device instead of a launch later
+                    cudaLaunchConfig_t cfg{};
+                    cfg.gridDim = dim3((unsigned)(L.total_lines * (L.n_seg - 1)));
+                    cfg.blockDim = dim3(kBoundaryThreads);
+                    cfg.stream = st;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    rc = check_cuda(cudaLaunchKernelEx(&cfg, boundary_fir_kernel, L, Gc));
+                }
                 L = LaunchGroups{};
                 L.uniform = 1;
                 min_tiles = 1 << 30;
@@ -1103,12 +1150,36 @@ int supra_autotune_tile_shape(supra_plan *plan, int32_t n, const int16_t *const 
                 }
             }
     }
+    // Trials of shapes with more depth segments than the shape in effect need more boundary
+    // records than a workspace sized for it holds: they run in a temporary workspace that
+    // holds the largest (the outputs do not depend on the workspace).
+    size_t trial_bytes = workspace_bytes;
+    for (const supra_tile_shape &c : cand) {
+        if (supra_plan_set_tile_shape(plan, &c)) continue;
+        trial_bytes = std::max(trial_bytes, supra_bmode_workspace_size(n, plans.data()));
+    }
+    supra_plan_set_tile_shape(plan, &before);
+    void *trial_ws = workspace;
+    const bool own = trial_bytes > workspace_bytes;
+    if (own && cudaMalloc(&trial_ws, trial_bytes) != cudaSuccess) return SUPRA_ENOMEM;
+    auto release = [&]() {
+        if (own) {
+            cudaStreamSynchronize(st);
+            cudaFree(trial_ws);
+        }
+    };
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return SUPRA_ECUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
+    if (cudaEventCreate(&e0) != cudaSuccess) {
+        release();
         return SUPRA_ECUDA;
     }
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        release();
+        return SUPRA_ECUDA;
+    }
+    workspace = trial_ws;
+    workspace_bytes = trial_bytes;
     int rc = SUPRA_OK;
     supra_tile_shape best = before;
     float best_t = INFINITY, first_t = INFINITY;
@@ -1134,6 +1205,7 @@ int supra_autotune_tile_shape(supra_plan *plan, int32_t n, const int16_t *const 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    release();
     supra_plan_set_tile_shape(plan, rc ? &before : &best);
     if (rc) return rc;
     if (best_shape) *best_shape = best;
@@ -1317,3 +1389,7 @@ int supra_device_status(int32_t clear) {
 }
 
 }  // extern "C"
+
+size_t supra::bmode_min_workspace(int32_t n, const supra_plan *const *plans) {
+    return n < 1 || !plans ? 0 : min_workspace(n, plans);
+}

@@ -365,6 +365,31 @@ def test_table1_multiline_frame_matches_oracle():
     assert_gray(img, ref, what="table-1 128/2 frame")
 
 
+@pytest.mark.parametrize("segments", [0, 3, 5])
+def test_segment_boundary_records_equal_halo_tiles(segments):
+    # One frame split along depth: with the workspace supra_bmode_workspace_size reports, the
+    # segments leave the outputs around their boundaries to the boundary kernel; with only the
+    # lines' workspace each segment beamforms the halo it needs.  Same codes byte for byte,
+    # whole-line codes too, and both the oracle's chain within the B-mode tolerance.
+    s = phantom.table1_setup(64, 1)
+    p = dict(s.params(), grid=None)
+    ch = phantom.synth_channels(s, phantom.make_phantom(s, 78, 3000, n_points=5), 78, device="cuda")
+    plan = supra.Plan(**p)
+    plan.tile_shape = dict(plan.tile_shape, frames_per_group=1, depth_segments=segments)
+    need = supra.workspace_size([plan])
+    assert need > 0   # lines out: only the boundary records
+    rec = plan.bmode(ch).cpu().numpy()
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    halo = plan.bmode(ch, workspace=small).cpu().numpy()
+    np.testing.assert_array_equal(rec, halo)
+    whole = supra.Plan(**p)
+    whole.tile_shape = dict(whole.tile_shape, frames_per_group=1, depth_segments=1)
+    np.testing.assert_array_equal(rec, whole.bmode(ch).cpu().numpy())
+    ref = oracle.logcompress(oracle.envelope(p, oracle.das(p, ch.cpu().numpy())), p["log_ref"], p["dyn_range_db"])
+    assert_gray(rec, ref, what=f"{segments} segments")
+    assert supra.device_status() == 0
+
+
 def _compounding(s):
     s.n_bands, s.band_step = 3, s.fc / 4
     return s
