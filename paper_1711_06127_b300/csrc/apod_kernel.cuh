@@ -63,6 +63,7 @@ static_assert(Smem<kTrain>::DZ1 == Smem<kTrain>::DZ2 + 16384 && Smem<kTrain>::DZ
 constexpr uint32_t kT64 = 0, kT128 = 64, kDW3 = 192, kDW2 = 272, kDW1 = 352;
 
 struct Args {
+    int rows_tma;          // kTrain: the feature rows come through the kernel's tensor map (else cp.async)
     const float *params;
     // kForward / kTrain: feature rows (bf16 [.][128]), masks (u32 [.][4]), norms, labels
     const uint16_t *feat;
@@ -95,6 +96,15 @@ __device__ __forceinline__ void unpack8(uint4 u, float *v) {
 __device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int row) {
     return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
 }
+// 3D tiled tensor copy global -> shared, completion counted on bar.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+
 // 16-byte global -> shared copy that completes asynchronously (cp.async), and its waits
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
@@ -214,11 +224,65 @@ __device__ __forceinline__ void stage_matrix(const float *__restrict__ w, int co
     }
 }
 
+// Threads per CTA: training and the fused beamformer split every pixel row over
+// two warpgroups (warps w and w + 4 share TMEM lanes 32 (w % 4).., each takes
+// half of every row's columns; in the beamformer each half gathers the elements
+// whose weights it computes), so that two warps per scheduler hide each other's
+// TMEM, shared-memory and MMA waits; the forward pass on stored rows keeps one
+// warpgroup.  The kernel takes any power-of-two number of parts H = threads /
+// 128 up to 4 (a training split over four measured the same per tile).
+template <int MODE>
+__host__ __device__ constexpr int apod_threads() { return MODE == kForward ? 128 : 256; }
+
+// Barrier of the H warps whose threads hold the parts of the same pixel rows (warps w, w + 4, ...:
+// the same tensor-memory lanes); named barriers 1..4, one per lane quarter.
+template <int H>
+__device__ __forceinline__ void row_parts_sync(int warp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (warp & 3)), "r"(32 * H) : "memory");
+}
+
+// The three matrices staged by the 256 threads of the training kernel with all of a thread's
+// 16-byte loads in flight at once (20 per thread), then their BF16 images; the same values as
+// stage_matrix.
+template <int LOG2_IN, int COUNT, int NT, int N0>
+__device__ __forceinline__ void put_matrix(const float4 (&q)[20], unsigned char *img, int jstride, int t) {
+    constexpr int kRow = 1 << LOG2_IN;
+#pragma unroll
+    for (int j = 0; j < COUNT / 4 / NT; ++j) {
+        const int k = 4 * (t + j * NT), n = k >> LOG2_IN, i = k & (kRow - 1);
+        *reinterpret_cast<uint2 *>(img + (i >> 3) * jstride + n * 16 + (i & 7) * 2) =
+            make_uint2(pack_bf16(q[N0 + j].x, q[N0 + j].y), pack_bf16(q[N0 + j].z, q[N0 + j].w));
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ void stage_weights(const float *__restrict__ prm, unsigned char *sm, int t, int nt) {
     using S = Smem<MODE>;
     // the matrices start at multiples of four floats, so one alignment test covers them
     const bool vec = (reinterpret_cast<uintptr_t>(prm) & 15) == 0;
+    constexpr int NT = apod_threads<MODE>();
+    if constexpr (MODE == kTrain && NT == 256) {   // (the inference kernel's registers have no room for 20)
+        constexpr int n1 = kH1 * kIn / 4 / NT, n2 = kH2 * kH1 / 4 / NT, n3 = kIn * kH2 / 4 / NT;
+        static_assert(n1 + n2 + n3 == 20, "loads per thread");
+        if (vec && nt == NT) {
+            float4 q[20];
+            const float4 *w1 = reinterpret_cast<const float4 *>(prm + kOffW1) + t;
+            const float4 *w2 = reinterpret_cast<const float4 *>(prm + kOffW2) + t;
+            const float4 *w3 = reinterpret_cast<const float4 *>(prm + kOffW3) + t;
+#pragma unroll
+            for (int j = 0; j < n1; ++j) q[j] = __ldg(w1 + j * NT);
+#pragma unroll
+            for (int j = 0; j < n2; ++j) q[n1 + j] = __ldg(w2 + j * NT);
+#pragma unroll
+            for (int j = 0; j < n3; ++j) q[n1 + n2 + j] = __ldg(w3 + j * NT);
+            const float bv = t < 64 ? prm[kOffB1 + t] : t < 128 ? prm[kOffB2 + t - 64] : prm[kOffB3 + t - 128];
+            put_matrix<7, kH1 * kIn, NT, 0>(q, sm + S::W1, 1024, t);
+            put_matrix<6, kH2 * kH1, NT, n1>(q, sm + S::W2, 1024, t);
+            put_matrix<6, kIn * kH2, NT, n1 + n2>(q, sm + S::W3, 2048, t);
+            reinterpret_cast<float *>(sm + S::BIAS)[t] = bv;
+            return;
+        }
+    }
     stage_matrix<7>(prm + kOffW1, kH1 * kIn, sm + S::W1, 1024, vec, t, nt);
     stage_matrix<6>(prm + kOffW2, kH2 * kH1, sm + S::W2, 1024, vec, t, nt);
     stage_matrix<6>(prm + kOffW3, kIn * kH2, sm + S::W3, 2048, vec, t, nt);
@@ -235,15 +299,6 @@ __device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t &phase) {
     return ok;
 }
 
-// Threads per CTA: training and the fused beamformer split every pixel row over
-// two warpgroups (warps w and w + 4 share TMEM lanes 32 (w % 4).., each takes
-// half of every row's columns; in the beamformer each half gathers the elements
-// whose weights it computes), so that two warps per scheduler hide each other's
-// TMEM, shared-memory and MMA waits; the forward pass on stored rows keeps one
-// warpgroup.  The kernel takes any power-of-two number of parts H = threads /
-// 128 up to 4 (a training split over four measured the same per tile).
-template <int MODE>
-__host__ __device__ constexpr int apod_threads() { return MODE == kForward ? 128 : 256; }
 
 // This thread's columns of a 64-wide accumulator: H parts of 64 / H columns, read in blocks of up to 32.
 template <int B>
@@ -253,13 +308,14 @@ __device__ __forceinline__ void tmem_ld_block(uint32_t taddr, float (&v)[B]) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) apod_kernel(const Args a) {
+__global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) apod_kernel(const Args a, const __grid_constant__ CUtensorMap rows_map) {
     using S = Smem<MODE>;
     constexpr int NT = apod_threads<MODE>(), H = NT / kTile;   // H halves per row
     constexpr uint32_t kCols = MODE == kTrain ? 512 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(8) uint64_t bar_dw1;   // training: completion of weight-gradient products (never waited on)
+    __shared__ __align__(8) uint64_t bar_rows;  // training with rows_tma: the next tile's feature rows have landed
     __shared__ uint32_t tmem_base;
     __shared__ float red[2][NT / 32];
     __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
@@ -270,21 +326,47 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     if (t == 0) {
         mbar_init(&bar, 1);
         mbar_init(&bar_dw1, 1);
+        mbar_init(&bar_rows, 1);
         fence_mbar_init();
+        if (MODE == kTrain && a.rows_tma)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&rows_map)) : "memory");
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
-    // Training: the next tile's feature rows are copied into the other X buffer (cp.async)
-    // while this tile runs; its masks, norms and labels wait in registers.  The copy into a
-    // buffer is issued after the next Z1 products complete, so the dW1 products of the tile
-    // before, which read that buffer, are complete too (one thread issues all products, and
-    // they complete in order).
+    // Training: the next tile's feature rows are copied into the other X buffer while this
+    // tile runs -- by the tensor-copy engine (one 3D copy, completing on bar_rows), else per
+    // thread (cp.async); its masks, norms and labels
+    // wait in registers.  The copy into a buffer is issued after the next Z1 products complete,
+    // so the dW1 products of the tile before, which read that buffer, are complete too (one
+    // thread issues all products, and they complete in order).  With the copy engine, rows past
+    // the pixel count keep whatever lands (real rows or the map's zero fill): they are masked
+    // out (no weight, no loss, a zero output gradient), as zeroed rows would be.
     uint32_t nmk[4] = {0u, 0u, 0u, 0u};
     float nnrm = 0.0f, nlab = 0.0f;   // raw loads: nothing uses them before the next tile
     bool nok = false;
+    uint32_t rows_phase = 0;          // completions of bar_rows waited for
+    bool rows_armed = false;          // a copy engine prefetch is in flight
     auto prefetch = [&](long long tl, int xo) {
         const long long pp = tl * kTile + row;
         nok = pp < a.n;
         const long long rw = tl * a.tile_stride + (long long)row * a.stride;
+        if (MODE == kTrain && a.rows_tma) {
+            if (t == 0) {   // one copy of the tile's 128 rows in the chunked layout
+                tc::fence_async_smem();   // this buffer's last generic reads precede the copy
+                mbar_arrive_expect_tx(&bar_rows, (uint32_t)(kTile * kIn * 2));
+                tma_load_3d(&chunk(sm, xo, 0, 0), &rows_map, 0, (int)(tl * a.tile_stride / a.stride), 0, &bar_rows);
+            }
+            rows_armed = true;
+            if (nok) {
+                const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + rw);
+                nmk[0] = m4.x, nmk[1] = m4.y, nmk[2] = m4.z, nmk[3] = m4.w;
+                nnrm = __ldg(a.norm + rw);
+                nlab = __ldg(a.label + rw);
+            } else {
+                nmk[0] = nmk[1] = nmk[2] = nmk[3] = 0u;
+                nnrm = nlab = 0.0f;
+            }
+            return;
+        }
         if (nok) {
             const uint4 *src = reinterpret_cast<const uint4 *>(a.feat + rw * kIn);
 #pragma unroll
@@ -419,7 +501,13 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             }
             nrm = n2v[0] + n2v[1];   // this half's share of ||x||^2 (square root below)
         } else if (MODE == kTrain) {
-            cp_async_wait_all();
+            if (rows_armed) {
+                ok = mbar_wait_bounded(&bar_rows, rows_phase & 1u, 1LL << 31) && ok;
+                ++rows_phase;
+                rows_armed = false;
+            } else {
+                cp_async_wait_all();
+            }
             p = tile * kTile + row;
             row_ok = nok;
             mk[0] = nmk[0], mk[1] = nmk[1], mk[2] = nmk[2], mk[3] = nmk[3];
@@ -527,7 +615,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
         if constexpr (H > 1) {   // the row's maximum over its parts
             xrow[0][half][row] = zmax;
-            __syncthreads();
+            if constexpr (MODE == kTrain) row_parts_sync<H>(warp);
+            else __syncthreads();
             zmax = xrow[0][0][row];
 #pragma unroll
             for (int h = 1; h < H; ++h) zmax = fmaxf(zmax, xrow[0][h][row]);
@@ -555,7 +644,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         if constexpr (H > 1) {   // the row's sums over its parts (pairwise, fixed order)
             xrow[1][half][row] = se;
             xrow[2][half][row] = sx;
-            __syncthreads();
+            if constexpr (MODE == kTrain) row_parts_sync<H>(warp);
+            else __syncthreads();
             if constexpr (H == 2) {
                 se = xrow[1][0][row] + xrow[1][1][row];
                 sx = xrow[2][0][row] + xrow[2][1][row];
@@ -674,6 +764,10 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     if (MODE == kTrain && !first) {   // every product issued so far, the last dW1 included
         if (t == 0) tc::mma_commit(&bar);
         ok = mma_wait(&bar, phase) && ok;
+    }
+    if (MODE == kTrain && rows_armed) {   // a prefetch that no tile waited for (an abort): let it land
+        mbar_wait_bounded(&bar_rows, rows_phase & 1u, 1LL << 27);
+        rows_armed = false;
     }
     ok = __syncthreads_and(ok);   // the last wait of a tile is not followed by a barrier
     if (!ok && t == 0) set_status(SUPRA_ETIMEOUT);

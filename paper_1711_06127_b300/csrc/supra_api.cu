@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -142,19 +144,67 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
+// cuTensorMapEncodeTiled is a pure function of its arguments and takes host time on every call
+// (a training step of one tile per CTA was host-bound on it): encoded maps are kept by their
+// arguments.  A map holds only an address, sizes and strides, so a kept map is the same map for
+// a freed and reallocated buffer at the same address.
+struct MapKey {
+    uintptr_t base;
+    int dtype, rank, interleave, swizzle, l2, oob;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5];
+    bool operator==(const MapKey &o) const { return std::memcmp(this, &o, sizeof(MapKey)) == 0; }
+};
+struct MapKeyHash {
+    size_t operator()(const MapKey &k) const {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(&k);
+        uint64_t h = 1469598103934665603ull;   // FNV-1a
+        for (size_t i = 0; i < sizeof(MapKey); ++i) h = (h ^ b[i]) * 1099511628211ull;
+        return (size_t)h;
+    }
+};
+bool encode_map(CUtensorMap *map, CUtensorMapDataType dtype, int rank, const void *base, const cuuint64_t *dims,
+                const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr, CUtensorMapL2promotion l2) {
+    if (rank < 1 || rank > 5) return false;
+    MapKey k;
+    std::memset(&k, 0, sizeof k);   // padding bytes too: keys compare as bytes
+    k.base = reinterpret_cast<uintptr_t>(base);
+    k.dtype = (int)dtype, k.rank = rank, k.interleave = (int)CU_TENSOR_MAP_INTERLEAVE_NONE;
+    k.swizzle = (int)CU_TENSOR_MAP_SWIZZLE_NONE, k.l2 = (int)l2, k.oob = (int)CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE;
+    for (int i = 0; i < rank; ++i) k.dims[i] = dims[i], k.box[i] = box[i], k.estr[i] = estr[i];
+    for (int i = 0; i + 1 < rank; ++i) k.strides[i] = strides[i];
+    static std::mutex mu;
+    static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> kept;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        const auto it = kept.find(k);
+        if (it != kept.end()) {
+            *map = it->second;
+            return true;
+        }
+    }
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || fn(map, dtype, (cuuint32_t)rank, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    std::lock_guard<std::mutex> g(mu);
+    if (kept.size() >= 16384) kept.clear();
+    kept.emplace(k, *map);
+    return true;
+}
+
 // 4D map over a group's records viewed as int32 sample pairs: (n_s / 2, n_el, n_tx, frames),
 // box (W / 2, 1, 1, G); reads outside the records fill zeros.
 bool make_frame_map(CUtensorMap *map, const void *base, long long frame_stride, int frames, const DevPlan &H,
                     int width, int G) {
-    EncodeTiledFn fn = encode_tiled();
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || frame_stride <= 0 || (frame_stride & 15)) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || frame_stride <= 0 || (frame_stride & 15)) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)H.n_s / 2, (cuuint64_t)H.n_el, (cuuint64_t)H.n_tx, (cuuint64_t)frames};
     const cuuint64_t strides[3] = {(cuuint64_t)H.n_s * 2, (cuuint64_t)H.n_s * 2 * H.n_el, (cuuint64_t)frame_stride};
     const cuuint32_t box[4] = {(cuuint32_t)width / 2, 1, 1, (cuuint32_t)G};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_L2_PROMOTION_NONE);
 }
 
 // Multiprocessors of the current device (queried once per device).
@@ -342,8 +392,30 @@ static int device_sms() {
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The feature rows of a training launch as a 3D tensor map for the kernel's prefetch by the
+// copy engine: (feature within an 8-feature chunk, virtual row, chunk), where virtual row v is
+// row v * stride of feat (tiles start at multiples of stride), up to the last pixel's row (rows
+// past it read the zero fill).  A box of 8 x 128 x 16 lands as the kernel's chunked layout
+// (chunk j of row r at j * 2048 + r * 16 bytes).  Leaves rows_tma 0 (per-thread copies) when
+// the rows do not fit that form.
+static void set_rows_map(apod::Args &a, CUtensorMap &map) {
+    a.rows_tma = 0;
+    if (a.n < 1 || a.stride < 1 || a.tile_stride < 1 || a.tile_stride % a.stride ||
+        (reinterpret_cast<uintptr_t>(a.feat) & 15))
+        return;
+    const long long last = a.n - 1;
+    const long long vmax = ((last / apod::kTile) * a.tile_stride + (last % apod::kTile) * a.stride) / a.stride;
+    if (vmax >= (1LL << 31) - apod::kTile) return;   // the kernel's row coordinates are int32
+    const cuuint64_t dims[3] = {8, (cuuint64_t)(vmax + 1), (cuuint64_t)apod::kIn / 8};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.stride * apod::kIn * 2, 16};
+    const cuuint32_t box[3] = {8, (cuuint32_t)apod::kTile, (cuuint32_t)apod::kIn / 8};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    a.rows_tma = encode_map(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, a.feat, dims, strides, box, estr,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+}
+
 template <int MODE>
-static int launch_apod(const apod::Args &a, long long n_tiles, int per_sm, cudaStream_t st, int *grid_out = nullptr) {
+static int launch_apod(const apod::Args &a0, long long n_tiles, int per_sm, cudaStream_t st, int *grid_out = nullptr) {
     const int sms = device_sms();
     if (sms <= 0) return SUPRA_ECUDA;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms * per_sm);
@@ -351,7 +423,11 @@ static int launch_apod(const apod::Args &a, long long n_tiles, int per_sm, cudaS
     const int smem = apod::Smem<MODE>::TOTAL;
     if (cudaFuncSetAttribute(apod::apod_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return SUPRA_ECUDA;
-    apod::apod_kernel<MODE><<<grid, apod::apod_threads<MODE>(), smem, st>>>(a);
+    apod::Args a = a0;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof map);
+    if (MODE == apod::kTrain) set_rows_map(a, map);
+    apod::apod_kernel<MODE><<<grid, apod::apod_threads<MODE>(), smem, st>>>(a, map);
     return check_cuda(cudaGetLastError());
 }
 
