@@ -896,31 +896,29 @@ __device__ __forceinline__ int param_of(int s) {
     return s;
 }
 // Warp g's sums for column j: partials g, g + 8, g + 16, ... added in that order (and, on the
-// count lane, their pixel counts); the rows are loaded four at a time ahead of the adds.
+// count lane, their pixel counts); the rows are loaded twenty at a time (all of them for up to
+// 160 partials) ahead of the adds.
 __device__ __forceinline__ void column_sum(const float *__restrict__ partial, int n_parts, int j, bool count_lane,
                                            int g, float &s, float &cnt) {
-    constexpr int U = 4;
+    constexpr int U = 20;
     s = 0.0f, cnt = 0.0f;
     const bool col = j <= kParams;
-    int c = g;
-    for (; c + (U - 1) * kReduceGroups < n_parts; c += U * kReduceGroups) {
+    for (int c = g; c < n_parts; c += U * kReduceGroups) {
         float v[U], w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const float *row = partial + (long long)(c + u * kReduceGroups) * kPartStride;
-            v[u] = col ? row[j] : 0.0f;
-            w[u] = count_lane ? row[kParams + 1] : 0.0f;
+            const int cc = c + u * kReduceGroups;
+            const float *row = partial + (long long)cc * kPartStride;
+            v[u] = (cc < n_parts && col) ? row[j] : 0.0f;
+            w[u] = (cc < n_parts && count_lane) ? row[kParams + 1] : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            s += v[u];
-            cnt += w[u];
+            if (c + u * kReduceGroups < n_parts) {
+                s += v[u];
+                cnt += w[u];
+            }
         }
-    }
-    for (; c < n_parts; c += kReduceGroups) {
-        const float *row = partial + (long long)c * kPartStride;
-        if (col) s += row[j];
-        if (count_lane) cnt += row[kParams + 1];
     }
 }
 
@@ -948,14 +946,20 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_kernel(con
     }
 }
 
-// One parameter's Adam update with bias correction (c1 = 1 / (1 - beta1^step), c2 = 1 / (1 - beta2^step)).
-__device__ __forceinline__ void adam_update(float *p, float *m, float *v, int j, float gj, float lr, float beta1,
-                                            float beta2, float eps, float c1, float c2) {
-    const float mj = fmaf(beta1, m[j], (1.0f - beta1) * gj);
-    const float vj = fmaf(beta2, v[j], (1.0f - beta2) * gj * gj);
+// One parameter's Adam update with bias correction (c1 = 1 / (1 - beta1^step), c2 = 1 / (1 - beta2^step))
+// from its current p, m, v (pj, mj0, vj0).
+__device__ __forceinline__ void adam_store(float *p, float *m, float *v, int j, float gj, float pj, float mj0,
+                                           float vj0, float lr, float beta1, float beta2, float eps, float c1,
+                                           float c2) {
+    const float mj = fmaf(beta1, mj0, (1.0f - beta1) * gj);
+    const float vj = fmaf(beta2, vj0, (1.0f - beta2) * gj * gj);
     m[j] = mj;
     v[j] = vj;
-    p[j] -= lr * (mj * c1) / (sqrtf(vj * c2) + eps);
+    p[j] = pj - lr * (mj * c1) / (sqrtf(vj * c2) + eps);
+}
+__device__ __forceinline__ void adam_update(float *p, float *m, float *v, int j, float gj, float lr, float beta1,
+                                            float beta2, float eps, float c1, float c2) {
+    adam_store(p, m, v, j, gj, p[j], m[j], v[j], lr, beta1, beta2, eps, c1, c2);
 }
 
 // reduce_kernel followed by the Adam update of each reduced parameter (one kernel for the
@@ -968,6 +972,10 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_adam_kerne
     __shared__ float part_cnt[kReduceGroups];
     const int lane = threadIdx.x % kReduceCols, g = threadIdx.x / kReduceCols;
     const int j = blockIdx.x * kReduceCols + lane;
+    // the parameter's current p, m, v are read while the partials load
+    const int jp = j < kParams ? param_of(j) : 0;
+    float pj = 0.0f, mj = 0.0f, vj = 0.0f;
+    if (g == 0 && j < kParams) pj = p[jp], mj = m[jp], vj = v[jp];
     float s, cnt;
     column_sum(partial, n_parts, j, lane == 0, g, s, cnt);
     part_sum[g][lane] = s;
@@ -981,9 +989,8 @@ __global__ void __launch_bounds__(kReduceCols * kReduceGroups) reduce_adam_kerne
         }
         const float gj = ct > 0.0f ? tot / ct : 0.0f;
         if (j < kParams) {
-            const int jp = param_of(j);
             grad[jp] = gj;
-            adam_update(p, m, v, jp, gj, lr, beta1, beta2, eps, c1, c2);
+            adam_store(p, m, v, jp, gj, pj, mj, vj, lr, beta1, beta2, eps, c1, c2);
         } else if (loss) {
             *loss = gj;
         }
