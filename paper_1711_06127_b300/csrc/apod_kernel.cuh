@@ -594,7 +594,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         ok = mma_wait(&bar, phase) && ok;
         // reductions over this thread's outputs in 4 independent partials (latency, not order, matters).
-        // Training reads its two 32-column blocks in one tensor-memory round trip per pass.
+        // Training reads its two 32-column blocks in one tensor-memory round trip and keeps z + b3
+        // in registers for the second pass.
         constexpr bool kPair = MODE == kTrain && 4 / H == 2;
         float vv[kPair ? 2 : 1][32];
         auto load_pair = [&]() {
@@ -609,8 +610,11 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
             const float *v = kPair ? vv[k] : vl;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], v[j] + b3[32 * q + j]);
+            for (int j = 0; j < 32; ++j) {
+                const float zb = v[j] + b3[32 * q + j];
+                if constexpr (kPair) vv[k][j] = zb;
+                if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], zb);
+            }
         }
         float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
         if constexpr (H > 1) {   // the row's maximum over its parts
@@ -622,7 +626,6 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             for (int h = 1; h < H; ++h) zmax = fmaxf(zmax, xrow[0][h][row]);
         }
         float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        load_pair();
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = q4 + k;
@@ -633,7 +636,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
+                const float zb = kPair ? v[j] : v[j] + b3[32 * q + j];   // (pairs: z + b3 from the first pass)
+                const float ez = ((mk[q] >> j) & 1u) ? __expf(zb - zmax) : 0.0f;
                 se4[j & 3] += ez;
                 sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
                 if constexpr (kPair) vv[k][j] = ez;   // kept for the output gradient below
