@@ -602,10 +602,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             if constexpr (kPair) tc::tmem_ld32x2(tm + lane + kT128 + 32 * q4, tm + lane + kT128 + 32 * (q4 + 1), vv[0], vv[1]);
         };
         float zm4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        // a 32-output block outside the aperture of all of the warp's 32 pixels (shallow depths)
+        // has no weight anywhere: the passes skip it (its exponentials and gradients are 0)
+        bool blk[4 / H];
+#pragma unroll
+        for (int k = 0; k < 4 / H; ++k) blk[k] = __any_sync(0xffffffffu, mk[q4 + k] != 0u);
         load_pair();
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = q4 + k;
+            if (!blk[k]) continue;
             float vl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
             const float *v = kPair ? vv[k] : vl;
@@ -629,6 +635,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = q4 + k;
+            if (!blk[k]) continue;
             float vl[32], x[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
             const float *v = kPair ? vv[k] : vl;
@@ -673,6 +680,11 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
             for (int k = 0; k < 4 / H; ++k) {
                 const int q = q4 + k;
+                if (!blk[k]) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = make_uint4(0u, 0u, 0u, 0u);
+                    continue;
+                }
                 float vl[32], x[32], dz[32];
                 if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
 #pragma unroll
