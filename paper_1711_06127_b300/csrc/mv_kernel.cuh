@@ -105,11 +105,17 @@ __global__ void __launch_bounds__(mv_warps<T>() * 32, sizeof(T) == 8 ? 1 : 4) mv
     const int L = min(Lreq, M), K = M - L + 1;
     const float *x = xs[warp];
     T(*R)[kMvMaxL + 1] = Rm[warp];
-    // covariance: lane d walks the d-th diagonal, R[a][a+d] = R[a-1][a-1+d] + x[a-1+K] x[a-1+K+d] - x[a-1] x[a-1+d]
+    // covariance: lane d walks the d-th diagonal, R[a][a+d] = R[a-1][a-1+d] + x[a-1+K] x[a-1+K+d] - x[a-1] x[a-1+d];
+    // its first pass also sums lane d's entry of the averaged subaperture (sum_l x[l + d])
+    T xb = 0;
     if (lane < L) {
         const int d = lane;
         T acc = 0;
-        for (int l = 0; l < K; ++l) acc += (T)x[l] * (T)x[l + d];
+        for (int l = 0; l < K; ++l) {
+            const T xd = (T)x[l + d];
+            acc += (T)x[l] * xd;
+            xb += xd;
+        }
         R[0][d] = acc;
         R[d][0] = acc;
         for (int a = 1; a + d < L; ++a) {
@@ -194,11 +200,7 @@ __global__ void __launch_bounds__(mv_warps<T>() * 32, sizeof(T) == 8 ? 1 : 4) mv
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
     T part = 0;
-    if (lane < L) {
-        T xb = 0;
-        for (int l = 0; l < K; ++l) xb += (T)x[l + lane];
-        part = (zv / zs) * (xb / (T)K);
-    }
+    if (lane < L) part = (zv / zs) * (xb / (T)K);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) {
