@@ -284,7 +284,9 @@ struct ProdConst {
 // depths; the left side minus a changes by at most lip per metre of r (q is a
 // clamp of a point moving along d, a grows at d_z / (2F)), so a depth within
 // 16 samples of a test point can pass only if that point is within
-// lip * 16 * depth_step of passing.  Returns false if no depth can.
+// lip * 16 * depth_step of passing (plus the consumers' rounding): [ia, ib]
+// holds every depth of the tile whose aperture test passes.  Returns false if
+// no depth can.
 // With `halves`, item j is half j % 2 of box element j / 2 (depth steps coarser
 // than c / (2 fs) make a whole tile's window too wide for one slot).
 __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo &lg, float lip, short4 b, int tile,
@@ -301,6 +303,8 @@ __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo 
         else i1 = min(i1, i0 + kTD / 2 - 1);
         if (i0 > i1) return false;
     }
+    // (+ 2e-6 a: the consumers' test |x_e - q_x| / a <= 1 passes up to a few float roundings
+    // beyond a, so every depth whose test passes lies in [ia, ib])
     const float margin = lip * 16.0f * C.depth_step * 1.001f + 1e-9f;
     int first = -1, last = -1;
 #pragma unroll
@@ -312,7 +316,7 @@ __device__ __forceinline__ bool element_range(const ProdConst &C, const LineGeo 
         const float qx = fminf(fmaxf(px, C.xmin), C.xmax), qy = fminf(fmaxf(py, C.ymin), C.ymax);
         const float a = fmaxf(pz * C.inv2f, C.amin);
         const float g = fmaxf(fabsf(xe.x - qx), fabsf(xe.y - qy)) - a;
-        if (g <= margin) {
+        if (g <= fmaf(2e-6f, a, margin)) {
             if (first < 0) first = k;
             last = k;
         }
@@ -495,12 +499,18 @@ __device__ __forceinline__ Geo element_geo(const ElemMeta &md, int i, float r, f
 // instructions, less than the vote and branch that would skip it, so every slot is applied
 // and a lane outside the aperture, or a slot past the stage's valid prefix, has weight 0.
 // YM: 0 no y window (linear arrays), 1 the element's own, 2 the row stage's (wy, iny).
-template <int YM>
+// RANGE: test the depth against the slot's depth range [ia, ib] -- needed when an element is
+// staged as two half-tile slots (depth steps coarser than c / (2 fs)); otherwise every depth of
+// the record inside the aperture lies in its slot's range (element_range), and depths past the
+// record's end (nd: the last tile's padding threads, whose values are discarded) are skipped by
+// the checked build's window test, which verifies the rest.
+template <int YM, bool RANGE>
 __device__ __forceinline__ Geo element_geo1(const ElemMeta &md, int i, float r, float qx, float qy, float inv_a,
-                                            float base, int kt, float wa, float wb, float fsc, float wy, bool iny) {
+                                            float base, int kt, float wa, float wb, float fsc, float wy, bool iny,
+                                            int nd) {
     Geo g;
     const float ux = (md.ex - qx) * inv_a;
-    bool in = fabsf(ux) <= 1.0f && i >= md.ia && i <= md.ib && meta_valid(md);
+    bool in = fabsf(ux) <= 1.0f && (!RANGE || (i >= md.ia && i <= md.ib)) && meta_valid(md);
     float w = window_weight(wa, wb, ux);
     if constexpr (YM == 1) {
         const float uy = (md.ey - qy) * inv_a;
@@ -520,7 +530,9 @@ __device__ __forceinline__ Geo element_geo1(const ElemMeta &md, int i, float r, 
     const float fl = floor_split(s, k);
 #ifdef SUPRA_CHECKED
     const int raw = kt + k - md.ws;
-    SUPRA_CHECK(!in || (raw >= 0 && raw + 1 < width_of(meta_widx(md))));
+    SUPRA_CHECK(!in || i >= nd || (raw >= 0 && raw + 1 < width_of(meta_widx(md))));
+#else
+    (void)nd;
 #endif
     g.w = w;
     g.w1 = w * (s - fl);
@@ -570,11 +582,11 @@ constexpr int kSlotSamples = width_of(kNumWidths - 1);   // samples per frame ro
 
 // One-frame stages (32 slots): groups of four slots, their geometry first (independent
 // chains), then their samples; valid slots are a prefix.
-template <int YM>
+template <int YM, bool RANGE>
 __device__ __forceinline__ void consume_one_frame(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int i,
                                                   float r, float qx, float qy, float inv_a, float base, int kt,
                                                   float wa, float wb, float fsc, float wy, bool iny, float &acc1,
-                                                  float &wsum) {
+                                                  float &wsum, int nd) {
     constexpr int kGrp = 4;
     u64 unused[1];
 #pragma unroll 1
@@ -583,7 +595,7 @@ __device__ __forceinline__ void consume_one_frame(const int16_t *__restrict__ sb
         Geo g[kGrp];
 #pragma unroll
         for (int j = 0; j < kGrp; ++j)
-            g[j] = element_geo1<YM>(meta[e0 + j], i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, wy, iny);
+            g[j] = element_geo1<YM, RANGE>(meta[e0 + j], i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, wy, iny, nd);
 #pragma unroll
         for (int j = 0; j < kGrp; ++j) {
             element_frames<1, 0>(sbuf + (e0 + j) * kSlotSamples, g[j], unused, acc1);
@@ -596,18 +608,28 @@ template <int G, int SH>
 __device__ __forceinline__ void consume_stage(const int16_t *__restrict__ sbuf, const ElemMeta *meta, int i, float r,
                                               float qx, float qy, float inv_a, float base, int kt,
                                               bool use_y, float wa, float wb, float fsc,
-                                              u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1, float &wsum) {
+                                              u64 (&acc2)[G / 2 > 0 ? G / 2 : 1], float &acc1, float &wsum,
+                                              bool halves, int nd) {
     constexpr int E = rows_of(G, SH) / G;
     if constexpr (G == 1) {
         const int f0 = meta[0].flags;
         if (!use_y) {
-            consume_one_frame<0>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1, wsum);
-        } else if (f0 & kRowStage) {
+            if (halves)
+                consume_one_frame<0, true>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1,
+                                           wsum, nd);
+            else
+                consume_one_frame<0, false>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1,
+                                            wsum, nd);
+        } else if (f0 & kRowStage) {   // (row stages only without halves)
             const float uy = (meta[0].ey - qy) * inv_a;
-            consume_one_frame<2>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, window_weight(wa, wb, uy),
-                                 fabsf(uy) <= 1.0f, acc1, wsum);
+            consume_one_frame<2, false>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc,
+                                        window_weight(wa, wb, uy), fabsf(uy) <= 1.0f, acc1, wsum, nd);
+        } else if (halves) {
+            consume_one_frame<1, true>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1, wsum,
+                                       nd);
         } else {
-            consume_one_frame<1>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1, wsum);
+            consume_one_frame<1, false>(sbuf, meta, i, r, qx, qy, inv_a, base, kt, wa, wb, fsc, 1.0f, true, acc1,
+                                        wsum, nd);
         }
     } else if constexpr (E <= 4) {
         // geometry of every slot first (independent chains), then the frame loops
@@ -1146,6 +1168,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
     // ---------------------------------------------------------------------- consumer warps
     const int m = tid;
     const bool use_y = P->el_ny > 1 || P->ymax > P->ymin;
+    const bool halves = P->a1 > 1.0f + 1e-6f;   // as the producer decides it
     const float wa = P->win_a, wb = P->win_b;
     const float fsc = P->fsc;
     int sb = 0;                 // stage buffer of the next stage
@@ -1193,7 +1216,7 @@ __global__ void __launch_bounds__(das_threads<G, MODE>(), MINB) das_kernel(const
                 // a halo tile's depths before its last kHalo are not needed (warp-uniform)
                 if (tile >= T0 || warp >= (kTD - kHalo) / 32)
                     consume_stage<G, SH>(stages + sb * stage_elems, meta, i, r, qx, qy, inv_a, base, kt, use_y, wa, wb,
-                                     fsc, acc2, acc1, wsum);
+                                     fsc, acc2, acc1, wsum, halves, nd);
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(&empty[sb]);
                 if (++sb == kStages) {
