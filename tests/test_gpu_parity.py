@@ -365,6 +365,26 @@ def test_table1_multiline_frame_matches_oracle():
     assert_gray(img, ref, what="table-1 128/2 frame")
 
 
+def test_batched_mixed_plans_records_equal_halo_tiles():
+    # An uneven batch (two plans, one with a grid, one with lines out) whose one-frame launches are
+    # split along depth: with the recommended workspace (boundary records) and with the lines'
+    # workspace only (each segment beamforms its halo), the same bytes.
+    a = phantom.linear_setup(32, 0.3e-3, 40, 600, fc=7e6, fs=40e6, grid_n=(100, 120))
+    b = phantom.sector_setup(24, 0.3e-3, 30, 35.0, 500, fc=3.5e6, fs=20e6)
+    pa, pb = supra.Plan(**a.params()), supra.Plan(**b.params())
+    plans = [pa, pb, pa, pa, pb, pa]
+    chs = [torch.as_tensor(phantom.random_channels(a if pl is pa else b, 150 + k)).cuda() for k, pl in enumerate(plans)]
+    need = supra.workspace_size(plans)
+    lines = sum(-(-pl.line_shape[0] * pl.line_shape[1] // 256) * 256 for pl in plans if pl is pa)
+    assert need > lines   # room for the records
+    rec = [o.cpu().numpy() for o in supra.bmode_batched(plans, chs)]
+    halo = [o.cpu().numpy() for o in
+            supra.bmode_batched(plans, chs, workspace=torch.empty(lines, dtype=torch.uint8, device="cuda"))]
+    for k, (x, y) in enumerate(zip(rec, halo)):
+        np.testing.assert_array_equal(x, y, err_msg=f"frame {k}")
+    assert supra.device_status() == 0
+
+
 @pytest.mark.parametrize("segments", [0, 3, 5])
 def test_segment_boundary_records_equal_halo_tiles(segments):
     # One frame split along depth: with the workspace supra_bmode_workspace_size reports, the
