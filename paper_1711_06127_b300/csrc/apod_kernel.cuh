@@ -632,13 +632,15 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             for (int h = 1; h < H; ++h) zmax = fmaxf(zmax, xrow[0][h][row]);
         }
         float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float xk[kPair ? 2 : 1][32];
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = q4 + k;
             if (!blk[k]) continue;
-            float vl[32], x[32];
+            float vl[32], xl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
             const float *v = kPair ? vv[k] : vl;
+            float *x = kPair ? xk[k] : xl;   // training keeps the samples for the output gradient
 #pragma unroll
             for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
 #pragma unroll
@@ -685,10 +687,15 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                     for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = make_uint4(0u, 0u, 0u, 0u);
                     continue;
                 }
-                float vl[32], x[32], dz[32];
-                if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
+                float vl[32], xl[32], dz[32];
+                const float *x = xl;
+                if constexpr (kPair) {
+                    x = xk[k];
+                } else {
+                    tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
+                    for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), xl + 8 * c);
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     // w_e = exp(z_e - zmax) / sum: the exponentials of the pass above (the same values)
