@@ -190,11 +190,14 @@ __device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict
 }
 
 // K steps of one MMA chain, issued by one thread (2 core matrices along K per step).
+// (The descriptors of successive K steps differ only in their start-address field, by
+// 2 * lbo / 16 per step, which stays inside the field for addresses below 256 KB.)
 __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t a_lbo, uint32_t a_sbo, uint32_t b,
                                           uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc, int ksteps, bool acc) {
-    for (int s = 0; s < ksteps; ++s)
-        tc::mma_bf16(d, tc::smem_desc(a + 2u * s * a_lbo, a_lbo, a_sbo), tc::smem_desc(b + 2u * s * b_lbo, b_lbo, b_sbo),
-                     idesc, acc || s > 0);
+    const uint64_t da = tc::smem_desc(a, a_lbo, a_sbo), db = tc::smem_desc(b, b_lbo, b_sbo);
+    const uint64_t ia = (uint64_t)((2u * a_lbo) >> 4), ib = (uint64_t)((2u * b_lbo) >> 4);
+#pragma unroll
+    for (int s = 0; s < ksteps; ++s) tc::mma_bf16(d, da + s * ia, db + s * ib, idesc, acc || s > 0);
 }
 
 // Weights [n][i] (row-major, i fastest) of one matrix into its shared-memory image: element
