@@ -93,6 +93,13 @@ __device__ __forceinline__ void unpack8(uint4 u, float *v) {
     v[0] = bf_lo(u.x), v[1] = bf_hi(u.x), v[2] = bf_lo(u.y), v[3] = bf_hi(u.y);
     v[4] = bf_lo(u.z), v[5] = bf_hi(u.z), v[6] = bf_lo(u.w), v[7] = bf_hi(u.w);
 }
+// 2^x (the special-function unit's approximation; exp(z) = 2^(z log2 e))
+constexpr float kLog2e = 1.44269504088896341f;
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int row) {
     return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
 }
@@ -232,10 +239,15 @@ __device__ __forceinline__ void stage_matrix(const float *__restrict__ w, int co
 // half of every row's columns; in the beamformer each half gathers the elements
 // whose weights it computes), so that two warps per scheduler hide each other's
 // TMEM, shared-memory and MMA waits; the forward pass on stored rows keeps one
-// warpgroup.  The kernel takes any power-of-two number of parts H = threads /
-// 128 up to 4 (a training split over four measured the same per tile).
+// warpgroup.  The kernel takes any power-of-two number of parts H = compute
+// threads / 128 up to 4 (a training split over four measured the same per tile).
+// Training adds one warp that only issues the tensor-core products (an MMA
+// instruction holds its issuing thread for tens of cycles, which the pixel
+// warps would otherwise wait for at the next barrier).
 template <int MODE>
-__host__ __device__ constexpr int apod_threads() { return MODE == kForward ? 128 : 256; }
+__host__ __device__ constexpr int apod_compute_threads() { return MODE == kForward ? 128 : 256; }
+template <int MODE>
+__host__ __device__ constexpr int apod_threads() { return apod_compute_threads<MODE>() + (MODE == kTrain ? 32 : 0); }
 
 // Barrier of the H warps whose threads hold the parts of the same pixel rows (warps w, w + 4, ...:
 // the same tensor-memory lanes); named barriers 1..4, one per lane quarter.
@@ -263,7 +275,7 @@ __device__ __forceinline__ void stage_weights(const float *__restrict__ prm, uns
     using S = Smem<MODE>;
     // the matrices start at multiples of four floats, so one alignment test covers them
     const bool vec = (reinterpret_cast<uintptr_t>(prm) & 15) == 0;
-    constexpr int NT = apod_threads<MODE>();
+    constexpr int NT = apod_compute_threads<MODE>();
     if constexpr (MODE == kTrain && NT == 256) {   // (the inference kernel's registers have no room for 20)
         constexpr int n1 = kH1 * kIn / 4 / NT, n2 = kH2 * kH1 / 4 / NT, n3 = kIn * kH2 / 4 / NT;
         static_assert(n1 + n2 + n3 == 20, "loads per thread");
@@ -313,20 +325,23 @@ __device__ __forceinline__ void tmem_ld_block(uint32_t taddr, float (&v)[B]) {
 template <int MODE>
 __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) apod_kernel(const Args a, const __grid_constant__ CUtensorMap rows_map) {
     using S = Smem<MODE>;
-    constexpr int NT = apod_threads<MODE>(), H = NT / kTile;   // H halves per row
+    // NC threads own the pixel rows (H parts per row); training adds the issuing warp
+    constexpr int NT = apod_threads<MODE>(), NC = apod_compute_threads<MODE>(), H = NC / kTile;
     constexpr uint32_t kCols = MODE == kTrain ? 512 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(8) uint64_t bar_dw1;   // training: completion of weight-gradient products (never waited on)
     __shared__ __align__(8) uint64_t bar_rows;  // training with rows_tma: the next tile's feature rows have landed
     __shared__ uint32_t tmem_base;
-    __shared__ float red[2][NT / 32];
+    __shared__ float red[2][NC / 32];
     __shared__ float xrow[H > 1 ? 3 : 1][H][kTile];   // per-row partials of the softmax (max, sum, weighted sum)
     __shared__ int win_ws[MODE == kInfer ? kWinSlots : 1];   // fused beamformer: staged window starts
     __shared__ float win_bg[MODE == kInfer ? kWinSlots : 1][2];   // and the elements' beta, gamma
     const int t = threadIdx.x, warp = t >> 5;
     const int row = t & (kTile - 1), half = t / kTile;
-    if (t == 0) {
+    const bool issuer = MODE == kTrain && t >= NC;   // the warp that issues the products
+    // (training: the issuing warp's lane 0, which then starts the first tile's row copy)
+    if (t == (MODE == kTrain ? NC : 0)) {
         mbar_init(&bar, 1);
         mbar_init(&bar_dw1, 1);
         mbar_init(&bar_rows, 1);
@@ -336,13 +351,14 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
     // Training: the next tile's feature rows are copied into the other X buffer while this
-    // tile runs -- by the tensor-copy engine (one 3D copy, completing on bar_rows), else per
-    // thread (cp.async); its masks, norms and labels
-    // wait in registers.  The copy into a buffer is issued after the next Z1 products complete,
-    // so the dW1 products of the tile before, which read that buffer, are complete too (one
-    // thread issues all products, and they complete in order).  With the copy engine, rows past
-    // the pixel count keep whatever lands (real rows or the map's zero fill): they are masked
-    // out (no weight, no loss, a zero output gradient), as zeroed rows would be.
+    // tile runs -- by the tensor-copy engine (one 3D copy that the issuing warp starts,
+    // completing on bar_rows), else per thread (cp.async); its masks, norms and labels wait in
+    // registers.  The copy into a buffer starts once the next Z2 products are complete (the
+    // issuing warp: after the barrier that follows their wait): the dW1 products of the tile
+    // before, which read that buffer, are issued right after the next Z1 products, so the
+    // commit that signals Z2 covers them too (one thread issues all products).  With the copy
+    // engine, rows past the pixel count keep whatever lands (real rows or the map's zero fill):
+    // they are masked out (no weight, no loss, a zero output gradient), as zeroed rows would be.
     uint32_t nmk[4] = {0u, 0u, 0u, 0u};
     float nnrm = 0.0f, nlab = 0.0f;   // raw loads: nothing uses them before the next tile
     bool nok = false;
@@ -352,12 +368,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         const long long pp = tl * kTile + row;
         nok = pp < a.n;
         const long long rw = tl * a.tile_stride + (long long)row * a.stride;
-        if (MODE == kTrain && a.rows_tma) {
-            if (t == 0) {   // one copy of the tile's 128 rows in the chunked layout
-                tc::fence_async_smem();   // this buffer's last generic reads precede the copy
-                mbar_arrive_expect_tx(&bar_rows, (uint32_t)(kTile * kIn * 2));
-                tma_load_3d(&chunk(sm, xo, 0, 0), &rows_map, 0, (int)(tl * a.tile_stride / a.stride), 0, &bar_rows);
-            }
+        if (MODE == kTrain && a.rows_tma) {   // (the issuing warp starts the copy)
             rows_armed = true;
             if (nok) {
                 const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(a.mask) + rw);
@@ -386,10 +397,19 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         cp_async_commit();
     };
+    // one copy of a tile's 128 rows in the chunked layout (the issuing warp's lane 0)
+    auto copy_rows = [&](long long tl, int xo) {
+        tc::fence_async_smem();   // this buffer's last generic reads precede the copy
+        mbar_arrive_expect_tx(&bar_rows, (uint32_t)(kTile * kIn * 2));
+        tma_load_3d(&chunk(sm, xo, 0, 0), &rows_map, 0, (int)(tl * a.tile_stride / a.stride), 0, &bar_rows);
+    };
     // the first tile's rows are requested before the weights are staged (the two latencies overlap)
-    if (MODE == kTrain && (long long)blockIdx.x < (a.n + kTile - 1) / kTile) prefetch(blockIdx.x, S::X);
-    stage_weights<MODE>(a.params, sm, t, NT);
-    if (MODE == kTrain && half == 0) {
+    if (MODE == kTrain && (long long)blockIdx.x < (a.n + kTile - 1) / kTile) {
+        if (!issuer) prefetch(blockIdx.x, S::X);
+        else if (a.rows_tma && (t & 31) == 0) copy_rows(blockIdx.x, S::X);
+    }
+    if (!issuer) stage_weights<MODE>(a.params, sm, t, NC);
+    if (MODE == kTrain && !issuer && half == 0) {
         const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
         chunk(sm, S::X, 16, row) = ones;
         chunk(sm, S::X, 17, row) = ones;
@@ -404,7 +424,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tm = tmem_base, lane = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tm = __shfl_sync(0xffffffffu, tmem_base, 0), lane = (uint32_t)(32 * (warp & 3)) << 16;
     // 64-wide layers: this thread's columns c64 .. c64 + C64, in NB64 blocks of BW64
     constexpr int C64 = 64 / H, BW64 = C64 < 32 ? C64 : 32, NB64 = C64 / BW64;
     const int c64 = C64 * half;
@@ -426,11 +446,88 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     uint32_t phase = 0;
     bool ok = true, first = true;
     float loss_acc = 0.0f, cnt_acc = 0.0f;
+    // Training's issuing warp: lane 0 issues every product and commit (a commit covers all of
+    // that thread's earlier products).  The dW1 products of a tile wait for the next tile's Z1
+    // products, so that they run while the pixel warps form H1 instead of delaying Z1.
+    const bool lead = issuer && (t & 31) == 0;
+    int x_prev = S::X;        // the X buffer of the tile whose dW1 products are pending
+    bool dw1_acc = false;     // whether they add to earlier tiles' sums
+    auto issue_dw1 = [&]() {
+        mma_chain(tm + kDW1, sb + S::DZ1, 128, 2048, sb + x_prev, 128, 2048, tc::idesc_bf16(128, 144, true, true), 8,
+                  dw1_acc);
+        dw1_acc = true;
+    };
+    // End of a step: the threads' shared-memory operands published to the products that read
+    // them (and to the issuing warp, which meets the same barrier); false when some thread failed.
+    auto step_end = [&]() -> bool {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) return false;
+        tc::fence_after_sync();
+        return true;
+    };
 
 
     int iter = 0;
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
         const int xo = (MODE == kTrain && (iter & 1)) ? S::X2 : S::X;   // this tile's X buffer
+        if (MODE == kTrain && issuer) {
+            // each group of products after the barrier that publishes its operands (the first
+            // also the tile before's dZ1, for its dW1 products)
+            if (a.rows_tma) {   // (the pixel warps wait for the rows too)
+                ok = mbar_wait_bounded(&bar_rows, rows_phase & 1u, 1LL << 31) && ok;
+                ++rows_phase;
+            }
+            if (!step_end()) break;
+            if (lead) {
+                mma_chain(tm + kT64, sb + xo, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
+                tc::mma_commit(&bar);
+                if (!first) {   // the tile before's [dW1 | db1] += dZ1^T [X | 1]
+                    issue_dw1();
+                    tc::mma_commit(&bar_dw1);
+                }
+            }
+            __syncwarp();
+            if (!step_end()) break;
+            if (lead) {
+                mma_chain(tm + kT64, sb + S::H1, 2048, 128, sb + S::W2, 1024, 128, kI64, 4, false);
+                tc::mma_commit(&bar);
+            }
+            __syncwarp();
+            if (!step_end()) break;
+            if (lead) {
+                mma_chain(tm + kT128, sb + S::H2, 2048, 128, sb + S::W3, 2048, 128, kI128, 4, false);
+                tc::mma_commit(&bar);
+                // the next tile's rows into the tile before's X buffer (its dW1 products, covered
+                // by the Z2 commit that the pixel warps waited for before this barrier, are complete)
+                if (a.rows_tma && tile + gridDim.x < n_tiles) copy_rows(tile + gridDim.x, xo == S::X ? S::X2 : S::X);
+            }
+            __syncwarp();
+            if (!step_end()) break;
+            if (lead) {   // dH2 = dZ3 W3 (waited for);  [dW3 | db3] += dZ3^T [H2 | 1]
+                mma_chain(tm + kT64, sb + S::DZ3, 2048, 128, sb + S::W3, 128, 2048,
+                          tc::idesc_bf16(128, 64, false, true), 8, false);
+                tc::mma_commit(&bar);
+                mma_chain(tm + kDW3, sb + S::DZ3, 128, 2048, sb + S::H2, 128, 2048,
+                          tc::idesc_bf16(128, 80, true, true), 8, !first);
+                tc::mma_commit(&bar_dw1);
+            }
+            __syncwarp();
+            if (!step_end()) break;
+            if (lead) {   // dH1 = dZ2 W2 (waited for);  [dW2 | db2] += dZ2^T [H1 | 1]
+                mma_chain(tm + kT64, sb + S::DZ2, 2048, 128, sb + S::W2, 128, 1024,
+                          tc::idesc_bf16(128, 64, false, true), 4, false);
+                tc::mma_commit(&bar);
+                mma_chain(tm + kDW2, sb + S::DZ2, 128, 2048, sb + S::H1, 128, 2048,
+                          tc::idesc_bf16(128, 80, true, true), 8, !first);
+                tc::mma_commit(&bar_dw1);
+            }
+            __syncwarp();
+            x_prev = xo;
+            first = false;
+            continue;
+        }
         // ---- inputs: one row of X per pixel (each half writes its chunks)
         uint32_t mk[4] = {0u, 0u, 0u, 0u};
         float nrm = 0.0f, tgt = 0.0f;
@@ -536,21 +633,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             }
         }
         if constexpr (MODE == kInfer && H > 1) xrow[0][half][row] = nrm;
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc::fence_after_sync();
+        if (!step_end()) break;
         if constexpr (MODE == kInfer) nrm = sqrtf(H > 1 ? xrow[0][0][row] + xrow[0][1][row] : nrm);
         const bool valid = row_ok && nrm > 0.0f;
 
-        // ---- Z1 = X W1^T
-        if (t == 0) {
+        // ---- Z1 = X W1^T (training: issued by the issuing warp, as all products below)
+        if (MODE != kTrain && t == 0) {
             mma_chain(tm + kT64, sb + xo, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
             tc::mma_commit(&bar);
         }
         ok = mma_wait(&bar, phase) && ok;
-        if (MODE == kTrain && tile + gridDim.x < n_tiles) prefetch(tile + gridDim.x, xo == S::X ? S::X2 : S::X);
         const float scale = (MODE == kInfer) ? (nrm > 0.0f ? 1.0f / nrm : 0.0f) : 1.0f;
 #pragma unroll
         for (int bk = 0; bk < NB64; ++bk) {
@@ -562,18 +654,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
             for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::H1, col / 8 + c, row) = pack8(v + 8 * c);
         }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc::fence_after_sync();
+        if (!step_end()) break;
 
         // ---- Z2 = H1 W2^T
-        if (t == 0) {
+        if (MODE != kTrain && t == 0) {
             mma_chain(tm + kT64, sb + S::H1, 2048, 128, sb + S::W2, 1024, 128, kI64, 4, false);
             tc::mma_commit(&bar);
         }
         ok = mma_wait(&bar, phase) && ok;
+        // (the tile before's dW1 products, issued before Z2, are complete: its X buffer is free)
+        if (MODE == kTrain && tile + gridDim.x < n_tiles) prefetch(tile + gridDim.x, xo == S::X ? S::X2 : S::X);
 #pragma unroll
         for (int bk = 0; bk < NB64; ++bk) {
             const int col = c64 + BW64 * bk;
@@ -584,14 +674,10 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
             for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::H2, col / 8 + c, row) = pack8(v + 8 * c);
         }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc::fence_after_sync();
+        if (!step_end()) break;
 
         // ---- Z3 = H2 W3^T, masked softmax, output (and its gradient)
-        if (t == 0) {
+        if (MODE != kTrain && t == 0) {
             mma_chain(tm + kT128, sb + S::H2, 2048, 128, sb + S::W3, 2048, 128, kI128, 4, false);
             tc::mma_commit(&bar);
         }
@@ -618,11 +704,30 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             float vl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
             const float *v = kPair ? vv[k] : vl;
+            const float4 *b34 = reinterpret_cast<const float4 *>(b3 + 32 * q);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float zb = v[j] + b3[32 * q + j];
-                if constexpr (kPair) vv[k][j] = zb;
-                if ((mk[q] >> j) & 1u) zm4[j & 3] = fmaxf(zm4[j & 3], zb);
+            for (int j4 = 0; j4 < 8; ++j4) {
+                const float4 bq = b34[j4];
+                const float bj[4] = {bq.x, bq.y, bq.z, bq.w};
+                float zs[4];   // z + b3 (pairs: two outputs per packed add)
+                if constexpr (kPair) {
+                    unpack2(add2(pack2(v[4 * j4], v[4 * j4 + 1]), pack2(bj[0], bj[1])), zs[0], zs[1]);
+                    unpack2(add2(pack2(v[4 * j4 + 2], v[4 * j4 + 3]), pack2(bj[2], bj[3])), zs[2], zs[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) zs[u] = v[4 * j4 + u] + bj[u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = 4 * j4 + u;
+                    const bool on = (mk[q] >> j) & 1u;
+                    if constexpr (kPair) {   // outputs outside the aperture as -inf: exponential 0 below
+                        vv[k][j] = on ? zs[u] : -INFINITY;
+                        zm4[u] = fmaxf(zm4[u], vv[k][j]);
+                    } else if (on) {
+                        zm4[u] = fmaxf(zm4[u], zs[u]);
+                    }
+                }
             }
         }
         float zmax = fmaxf(fmaxf(zm4[0], zm4[1]), fmaxf(zm4[2], zm4[3]));
@@ -635,7 +740,11 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             for (int h = 1; h < H; ++h) zmax = fmaxf(zmax, xrow[0][h][row]);
         }
         float se4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        float xk[kPair ? 2 : 1][32];
+        // exp(z - zmax) = 2^(z log2 e - zmax log2 e) (a row without any output in the aperture
+        // has zmax = -inf and every z = -inf: offset 0 keeps its exponentials 0)
+        const float c2 = zmax > -INFINITY ? -zmax * kLog2e : 0.0f;
+        // pairs: the partial sums se4 / sx4 [0, 1] and [2, 3] as two packed accumulators each
+        u64 se2[2] = {0ull, 0ull}, sx2[2] = {0ull, 0ull};
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = q4 + k;
@@ -643,17 +752,36 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             float vl[32], xl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
             const float *v = kPair ? vv[k] : vl;
-            float *x = kPair ? xk[k] : xl;   // training keeps the samples for the output gradient
+            float *x = xl;
 #pragma unroll
             for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), x + 8 * c);
+            if constexpr (kPair) {   // (masked z + b3 from the first pass), two outputs per packed operation
+                const u64 L2 = pack2(kLog2e, kLog2e), C2 = pack2(c2, c2);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float zb = kPair ? v[j] : v[j] + b3[32 * q + j];   // (pairs: z + b3 from the first pass)
-                const float ez = ((mk[q] >> j) & 1u) ? __expf(zb - zmax) : 0.0f;
-                se4[j & 3] += ez;
-                sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
-                if constexpr (kPair) vv[k][j] = ez;   // kept for the output gradient below
+                for (int j2 = 0; j2 < 16; ++j2) {
+                    const int j = 2 * j2;
+                    float a0, a1;
+                    unpack2(fma2(pack2(v[j], v[j + 1]), L2, C2), a0, a1);
+                    vv[k][j] = ex2_approx(a0);   // kept for the output gradient below
+                    vv[k][j + 1] = ex2_approx(a1);
+                    const u64 ep = pack2(vv[k][j], vv[k][j + 1]);
+                    se2[j2 & 1] = add2(se2[j2 & 1], ep);
+                    sx2[j2 & 1] = fma2(ep, pack2(x[j], x[j + 1]), sx2[j2 & 1]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
+                    se4[j & 3] += ez;
+                    sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
+                }
             }
+        }
+        if constexpr (kPair) {
+            unpack2(se2[0], se4[0], se4[1]);
+            unpack2(se2[1], se4[2], se4[3]);
+            unpack2(sx2[0], sx4[0], sx4[1]);
+            unpack2(sx2[1], sx4[2], sx4[3]);
         }
         float se = (se4[0] + se4[1]) + (se4[2] + se4[3]);
         float sx = (sx4[0] + sx4[1]) + (sx4[2] + sx4[3]);
@@ -681,7 +809,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 loss_acc = fmaf(r, r, loss_acc);
                 cnt_acc += valid ? 1.0f : 0.0f;
             }
-            const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f;
+            const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f, gs = g * inv_se;
 #pragma unroll
             for (int k = 0; k < 4 / H; ++k) {
                 const int q = q4 + k;
@@ -693,42 +821,38 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 float vl[32], xl[32], dz[32];
                 const float *x = xl;
                 if constexpr (kPair) {
-                    x = xk[k];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), xl + 8 * c);
                 } else {
                     tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) unpack8(chunk(sm, xo, 4 * q + c, row), xl + 8 * c);
                 }
+                // dz_e = w_e (x_e - yh) g, w_e = exp(z_e - zmax) / sum: pairs reuse the
+                // exponentials of the pass above (the same values), two outputs per packed operation
+                if constexpr (kPair) {
+                    const u64 GS = pack2(gs, gs), NYH = pack2(-yh, -yh);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    // w_e = exp(z_e - zmax) / sum: the exponentials of the pass above (the same values)
-                    float pe;
-                    if constexpr (kPair) pe = vv[k][j] * inv_se;
-                    else pe = ((mk[q] >> j) & 1u) ? __expf(vl[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
-                    dz[j] = pe * (x[j] - yh) * g;
+                    for (int j = 0; j < 32; j += 2)
+                        unpack2(mul2(mul2(pack2(vv[k][j], vv[k][j + 1]), GS), add2(pack2(x[j], x[j + 1]), NYH)),
+                                dz[j], dz[j + 1]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float pe = ((mk[q] >> j) & 1u) ? __expf(vl[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
+                        dz[j] = pe * (x[j] - yh) * g;
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = pack8(dz + 8 * c);
             }
         }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc::fence_after_sync();
+        if (!step_end()) break;
         if (MODE != kTrain) continue;
 
         // ---- dH2 = dZ3 W3;  [dW3 | db3] += dZ3^T [H2 | 1].  Only dH2 is waited for: the
         // weight-gradient products run while the threads form dZ2 (they read dZ3 and H2, which
         // nothing writes before the next tile's products, issued after them, complete)
-        if (t == 0) {
-            mma_chain(tm + kT64, sb + S::DZ3, 2048, 128, sb + S::W3, 128, 2048, tc::idesc_bf16(128, 64, false, true), 8,
-                      false);
-            tc::mma_commit(&bar);
-            mma_chain(tm + kDW3, sb + S::DZ3, 128, 2048, sb + S::H2, 128, 2048, tc::idesc_bf16(128, 80, true, true), 8,
-                      !first);
-            tc::mma_commit(&bar_dw1);
-        }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
         for (int bk = 0; bk < NB64; ++bk) {
@@ -742,22 +866,10 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
             for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::DZ2, col / 8 + c, row) = pack8(v + 8 * c);
         }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc::fence_after_sync();
+        if (!step_end()) break;
 
         // ---- dH1 = dZ2 W2;  [dW2 | db2] += dZ2^T [H1 | 1], dW2 not waited for (as dW3; its
         // discarded rows 64..127 read the DZ1 bytes that the threads write meanwhile)
-        if (t == 0) {
-            mma_chain(tm + kT64, sb + S::DZ2, 2048, 128, sb + S::W2, 128, 1024, tc::idesc_bf16(128, 64, false, true), 4,
-                      false);
-            tc::mma_commit(&bar);
-            mma_chain(tm + kDW2, sb + S::DZ2, 128, 2048, sb + S::H1, 128, 2048, tc::idesc_bf16(128, 80, true, true), 8,
-                      !first);
-            tc::mma_commit(&bar_dw1);
-        }
         ok = mma_wait(&bar, phase) && ok;
 #pragma unroll
         for (int bk = 0; bk < NB64; ++bk) {
@@ -771,25 +883,23 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
             for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::DZ1, col / 8 + c, row) = pack8(v + 8 * c);
         }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc::fence_after_sync();
-
-        // ---- [dW1 | db1] += dZ1^T [X | 1]; not waited for: the next tile's Z1 products complete
-        // after it (before this X buffer is refilled or DZ1 rewritten), and the final commit below
-        // covers the last tile
-        if (t == 0) {
-            mma_chain(tm + kDW1, sb + S::DZ1, 128, 2048, sb + xo, 128, 2048, tc::idesc_bf16(128, 144, true, true), 8,
-                      !first);
-            tc::mma_commit(&bar_dw1);
-        }
+        // ---- [dW1 | db1] += dZ1^T [X | 1]: dZ1 is published by the next tile's first barrier (or
+        // the one after the loop); the products are issued after the next tile's Z1 products and
+        // covered by the commit of its Z2 (before this X buffer is refilled or DZ1 rewritten); the
+        // final commit below covers the last tile's
         first = false;
     }
-    if (MODE == kTrain && !first) {   // every product issued so far, the last dW1 included
-        if (t == 0) tc::mma_commit(&bar);
-        ok = mma_wait(&bar, phase) && ok;
+    if (MODE == kTrain && !first) {   // the last tile's dW1 (unless abandoned), then a commit of all
+        const bool done = step_end();    // (publishes the last dZ1)
+        if (issuer) {
+            if (lead) {
+                if (done) issue_dw1();
+                tc::mma_commit(&bar);
+            }
+            __syncwarp();
+        } else {
+            ok = mma_wait(&bar, phase) && ok;
+        }
     }
     if (MODE == kTrain && rows_armed) {   // a prefetch that no tile waited for (an abort): let it land
         mbar_wait_bounded(&bar_rows, rows_phase & 1u, 1LL << 27);
@@ -805,7 +915,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         // column by column (see param_of), so that a warp's store covers 32 consecutive floats.
         float v[32], w[16], vb[BW64];
         const bool low = (warp & 3) < 2;   // rows 0..63: the 64-row accumulators dW2, dW1
-        if (ok && !first) {
+        if (!issuer && ok && !first) {
             for (int bk = 0; bk < NB64; ++bk) {
                 const int col = c64 + BW64 * bk;
                 tmem_ld_block<BW64>(tm + lane + kDW3 + col, vb);
@@ -835,19 +945,19 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                     part[kOffB1 + row] = w[0];
                 }
             }
-        } else {
-            for (int k = t; k < kParams; k += NT) part[k] = 0.0f;
+        } else if (!issuer) {
+            for (int k = t; k < kParams; k += NC) part[k] = 0.0f;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
             cnt_acc += __shfl_xor_sync(0xffffffffu, cnt_acc, o);
         }
-        if ((t & 31) == 0) red[0][warp] = loss_acc, red[1][warp] = cnt_acc;
+        if ((t & 31) == 0 && !issuer) red[0][warp] = loss_acc, red[1][warp] = cnt_acc;
         __syncthreads();
         if (t == 0) {
             float ls = 0.0f, cs = 0.0f;
-            for (int k = 0; k < NT / 32; ++k) ls += red[0][k], cs += red[1][k];
+            for (int k = 0; k < NC / 32; ++k) ls += red[0][k], cs += red[1][k];
             part[kParams] = ls;
             part[kParams + 1] = cs;
         }
