@@ -743,17 +743,21 @@ def run_ours(args):
 
             dist.barrier()
 
-    def timed(fn, n, ns, clocks=False):
+    def timed(fn, n, ns, clocks=False, warm=0):
         """n calls fn(k, ns), call k on stream k % ns.  Returns the total ms, each call's ms
-        (from the point its stream reached it to its end) and the clock sampler."""
+        (from the point its stream reached it to its end) and the clock sampler.  The clock
+        sampler starts first (it takes a moment to start); `warm` untimed calls queued after it
+        keep the GPU busy up to the timed region, which a barrier and a synchronize open."""
         es = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
         ee = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize()
         clk = ClockSampler(dev.index) if clocks else None
         if clk:
             clk.__enter__()
+        for k in range(warm):
+            fn(k, ns)
+        barrier()
+        torch.cuda.synchronize()
         e0.record(stream)
         for st in streams[1:ns]:
             st.wait_stream(stream)
@@ -784,8 +788,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     assert supra.device_status() == 0
 
-    # ---- timed region: exactly K steps
-    total_ms, step_ms, clk = timed(step, args.steps, n_str, clocks=True)
+    # ---- timed region: exactly K steps (the W warm-up steps again right before it, untimed, so
+    # that the GPU does not sit idle while the clock sampler starts)
+    total_ms, step_ms, clk = timed(step, args.steps, n_str, clocks=True, warm=max(3, args.warmup))
     total_ms = max_over_ranks(total_ms, world, dev)
     per_frame = s.n_tx * s.n_el * s.n_samples
     frames = BATCH * args.steps * world

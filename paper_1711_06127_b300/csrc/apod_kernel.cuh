@@ -103,6 +103,58 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int row) {
     return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
 }
+// pack_bf16(max(lo, 0), max(hi, 0)): the conversion's ReLU (rounding keeps the sign, so rounding and
+// clamping commute)
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// A layer's activations for this thread's BW columns: relu(v * scale + bias) in BF16 into
+// chunks c0.. of row `row` of a buffer, two columns per packed FMA.
+template <int BW>
+__device__ __forceinline__ void bias_relu_rows(const float (&v)[BW], const float *bias, float scale,
+                                               unsigned char *sm, int buf, int c0, int row) {
+    const u64 S2 = pack2(scale, scale);
+    const float4 *b4 = reinterpret_cast<const float4 *>(bias);
+#pragma unroll
+    for (int c = 0; c < BW / 8; ++c) {
+        const float4 ba = b4[2 * c], bb = b4[2 * c + 1];
+        const float bj[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float lo, hi;
+            unpack2(fma2(pack2(v[8 * c + 2 * u], v[8 * c + 2 * u + 1]), S2, pack2(bj[2 * u], bj[2 * u + 1])), lo, hi);
+            w[u] = pack_bf16_relu(lo, hi);
+        }
+        chunk(sm, buf, c0 + c, row) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// A ReLU layer's pre-activation gradient for this thread's BW columns: v where the layer's stored
+// output h (BF16, >= 0) is positive, else 0, in BF16.  Per BF16 pair of h, bit 15 of each 16-bit
+// lane of (h & 0x7fff7fff) + 0x7fff7fff is set exactly when that lane is not zero (no carry
+// crosses lanes), and a byte permute replicates it over the lane: a mask for the packed gradient.
+template <int BW>
+__device__ __forceinline__ void relu_grad_rows(const float (&v)[BW], unsigned char *sm, int hbuf, int dbuf, int c0,
+                                               int row) {
+#pragma unroll
+    for (int c = 0; c < BW / 8; ++c) {
+        const uint4 h = chunk(sm, hbuf, c0 + c, row);
+        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t nz = (hw[u] & 0x7fff7fffu) + 0x7fff7fffu;
+            uint32_t m;
+            asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(m) : "r"(nz));
+            w[u] = pack_bf16(v[8 * c + 2 * u], v[8 * c + 2 * u + 1]) & m;
+        }
+        chunk(sm, dbuf, c0 + c, row) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
 // 3D tiled tensor copy global -> shared, completion counted on bar.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
     asm volatile(
@@ -446,10 +498,18 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     uint32_t phase = 0;
     bool ok = true, first = true;
     float loss_acc = 0.0f, cnt_acc = 0.0f;
-    // Training's issuing warp: lane 0 issues every product and commit (a commit covers all of
-    // that thread's earlier products).  The dW1 products of a tile wait for the next tile's Z1
-    // products, so that they run while the pixel warps form H1 instead of delaying Z1.
-    const bool lead = issuer && (t & 31) == 0;
+    // The products are issued by one elected lane of a converged warp (training: the issuing
+    // warp; else warp 0).  A commit covers the earlier products of the thread that makes it, so
+    // every product and commit must come from the same lane: the lowest, which elect.sync picks
+    // in a converged warp; another leader is reported as an internal error.  In training the dW1
+    // products of a tile wait for the next tile's Z1 products, so that they run while the pixel
+    // warps form H1 instead of delaying Z1.
+    uint32_t leader = 0, bad_leader = 0;
+    auto lead = [&]() {
+        const bool e = tc::elect_one(&leader);
+        bad_leader |= leader;
+        return e;
+    };
     int x_prev = S::X;        // the X buffer of the tile whose dW1 products are pending
     bool dw1_acc = false;     // whether they add to earlier tiles' sums
     auto issue_dw1 = [&]() {
@@ -480,7 +540,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 ++rows_phase;
             }
             if (!step_end()) break;
-            if (lead) {
+            if (lead()) {
                 mma_chain(tm + kT64, sb + xo, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
                 tc::mma_commit(&bar);
                 if (!first) {   // the tile before's [dW1 | db1] += dZ1^T [X | 1]
@@ -490,13 +550,13 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             }
             __syncwarp();
             if (!step_end()) break;
-            if (lead) {
+            if (lead()) {
                 mma_chain(tm + kT64, sb + S::H1, 2048, 128, sb + S::W2, 1024, 128, kI64, 4, false);
                 tc::mma_commit(&bar);
             }
             __syncwarp();
             if (!step_end()) break;
-            if (lead) {
+            if (lead()) {
                 mma_chain(tm + kT128, sb + S::H2, 2048, 128, sb + S::W3, 2048, 128, kI128, 4, false);
                 tc::mma_commit(&bar);
                 // the next tile's rows into the tile before's X buffer (its dW1 products, covered
@@ -505,7 +565,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             }
             __syncwarp();
             if (!step_end()) break;
-            if (lead) {   // dH2 = dZ3 W3 (waited for);  [dW3 | db3] += dZ3^T [H2 | 1]
+            if (lead()) {   // dH2 = dZ3 W3 (waited for);  [dW3 | db3] += dZ3^T [H2 | 1]
                 mma_chain(tm + kT64, sb + S::DZ3, 2048, 128, sb + S::W3, 128, 2048,
                           tc::idesc_bf16(128, 64, false, true), 8, false);
                 tc::mma_commit(&bar);
@@ -515,7 +575,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             }
             __syncwarp();
             if (!step_end()) break;
-            if (lead) {   // dH1 = dZ2 W2 (waited for);  [dW2 | db2] += dZ2^T [H1 | 1]
+            if (lead()) {   // dH1 = dZ2 W2 (waited for);  [dW2 | db2] += dZ2^T [H1 | 1]
                 mma_chain(tm + kT64, sb + S::DZ2, 2048, 128, sb + S::W2, 128, 1024,
                           tc::idesc_bf16(128, 64, false, true), 4, false);
                 tc::mma_commit(&bar);
@@ -638,7 +698,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         const bool valid = row_ok && nrm > 0.0f;
 
         // ---- Z1 = X W1^T (training: issued by the issuing warp, as all products below)
-        if (MODE != kTrain && t == 0) {
+        if (MODE != kTrain && warp == 0 && lead()) {
             mma_chain(tm + kT64, sb + xo, 2048, 128, sb + S::W1, 1024, 128, kI64, 8, false);
             tc::mma_commit(&bar);
         }
@@ -649,15 +709,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const int col = c64 + BW64 * bk;
             float v[BW64];
             tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
-#pragma unroll
-            for (int j = 0; j < BW64; ++j) v[j] = fmaxf(fmaf(v[j], scale, b1[col + j]), 0.0f);
-#pragma unroll
-            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::H1, col / 8 + c, row) = pack8(v + 8 * c);
+            bias_relu_rows<BW64>(v, b1 + col, scale, sm, S::H1, col / 8, row);
         }
         if (!step_end()) break;
 
         // ---- Z2 = H1 W2^T
-        if (MODE != kTrain && t == 0) {
+        if (MODE != kTrain && warp == 0 && lead()) {
             mma_chain(tm + kT64, sb + S::H1, 2048, 128, sb + S::W2, 1024, 128, kI64, 4, false);
             tc::mma_commit(&bar);
         }
@@ -669,15 +726,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const int col = c64 + BW64 * bk;
             float v[BW64];
             tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
-#pragma unroll
-            for (int j = 0; j < BW64; ++j) v[j] = fmaxf(v[j] + b2[col + j], 0.0f);
-#pragma unroll
-            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::H2, col / 8 + c, row) = pack8(v + 8 * c);
+            bias_relu_rows<BW64>(v, b2 + col, 1.0f, sm, S::H2, col / 8, row);
         }
         if (!step_end()) break;
 
         // ---- Z3 = H2 W3^T, masked softmax, output (and its gradient)
-        if (MODE != kTrain && t == 0) {
+        if (MODE != kTrain && warp == 0 && lead()) {
             mma_chain(tm + kT128, sb + S::H2, 2048, 128, sb + S::W3, 2048, 128, kI128, 4, false);
             tc::mma_commit(&bar);
         }
@@ -857,14 +911,9 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
         for (int bk = 0; bk < NB64; ++bk) {
             const int col = c64 + BW64 * bk;
-            float v[BW64], h[BW64];
+            float v[BW64];
             tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
-#pragma unroll
-            for (int c = 0; c < BW64 / 8; ++c) unpack8(chunk(sm, S::H2, col / 8 + c, row), h + 8 * c);
-#pragma unroll
-            for (int j = 0; j < BW64; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
-#pragma unroll
-            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::DZ2, col / 8 + c, row) = pack8(v + 8 * c);
+            relu_grad_rows<BW64>(v, sm, S::H2, S::DZ2, col / 8, row);
         }
         if (!step_end()) break;
 
@@ -874,14 +923,9 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
         for (int bk = 0; bk < NB64; ++bk) {
             const int col = c64 + BW64 * bk;
-            float v[BW64], h[BW64];
+            float v[BW64];
             tmem_ld_block<BW64>(tm + lane + kT64 + col, v);
-#pragma unroll
-            for (int c = 0; c < BW64 / 8; ++c) unpack8(chunk(sm, S::H1, col / 8 + c, row), h + 8 * c);
-#pragma unroll
-            for (int j = 0; j < BW64; ++j) v[j] = h[j] > 0.0f ? v[j] : 0.0f;
-#pragma unroll
-            for (int c = 0; c < BW64 / 8; ++c) chunk(sm, S::DZ1, col / 8 + c, row) = pack8(v + 8 * c);
+            relu_grad_rows<BW64>(v, sm, S::H1, S::DZ1, col / 8, row);
         }
         // ---- [dW1 | db1] += dZ1^T [X | 1]: dZ1 is published by the next tile's first barrier (or
         // the one after the loop); the products are issued after the next tile's Z1 products and
@@ -892,7 +936,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     if (MODE == kTrain && !first) {   // the last tile's dW1 (unless abandoned), then a commit of all
         const bool done = step_end();    // (publishes the last dZ1)
         if (issuer) {
-            if (lead) {
+            if (lead()) {
                 if (done) issue_dw1();
                 tc::mma_commit(&bar);
             }
@@ -907,6 +951,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     }
     ok = __syncthreads_and(ok);   // the last wait of a tile is not followed by a barrier
     if (!ok && t == 0) set_status(SUPRA_ETIMEOUT);
+    if (bad_leader != 0 && (t & 31) == 0) set_status(SUPRA_EINTERNAL);   // (see lead above)
 
     if (MODE == kTrain) {
         float *part = a.partial + (long long)blockIdx.x * kPartStride;

@@ -67,6 +67,17 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// One lane of the calling warp, which must be converged (elect.sync): true in the elected lane, whose
+// lane id every lane receives in *leader.  Products issued under it let the compiler keep their
+// descriptors on the warp's uniform datapath (about half the issue time of a per-thread branch).
+__device__ __forceinline__ bool elect_one(uint32_t *leader) {
+    uint32_t e, l;
+    asm volatile("{\n\t.reg .pred P;\n\telect.sync %1|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}"
+                 : "=r"(e), "=r"(l));
+    *leader = l;
+    return e != 0;
+}
+
 // D[tmem] (+)= A * B^T, M x N x 16, issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          bool accumulate) {
