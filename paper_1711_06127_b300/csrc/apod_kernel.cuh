@@ -231,14 +231,16 @@ __device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict
     act = fabsf((xe.x - g.qx) * g.inv_a) <= 1.0f && fabsf((xe.y - g.qy) * g.inv_a) <= 1.0f;
     if (!act) return 0.0f;
     const float s = g.base + path_excess(g.r, beta, gamma) * P->fsc;
-    const float fl = floorf(s);
+    int ks;
+    const float fl = floor_split(s, ks);   // (|s| is far below 2^22 inside the aperture)
     const float phi = s - fl;
-    const long long k = (long long)g.kt + (long long)fl;
+    const long long k = (long long)g.kt + ks;
     const long long d = k - ws;
     float x0, x1;
-    if (d >= 0 && d + 1 < kWinW) {
-        x0 = (float)win[d];
-        x1 = (float)win[d + 1];
+    if (d >= 0 && d + 1 < kWinW) {   // int16 -> float exactly, without the conversion pipe
+        const uint16_t *w16 = reinterpret_cast<const uint16_t *>(win) + d;
+        x0 = __uint_as_float(biased(w16[0])) - kMagic;
+        x1 = __uint_as_float(biased(w16[1])) - kMagic;
     } else {
         const int n_s = P->n_s;
         const int16_t *rec = g.rec0 + (long long)e * n_s;
