@@ -1,6 +1,6 @@
 // mv_kernel.cuh -- exact minimum-variance (Capon) beamformer.  Not in the
 // paper: it labels the data the learned apodization is trained on, is the
-// fallback beamformer and the judge of the learned weights.
+// fallback beamformer and the yardstick for the learned weights' error.
 //
 // Per pixel (one warp): the delayed, interpolated samples x of the active
 // aperture (same delays and aperture rule as delay-and-sum, no apodization),
