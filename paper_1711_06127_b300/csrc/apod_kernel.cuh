@@ -223,16 +223,17 @@ __device__ __forceinline__ int tile_window(const DevPlan *__restrict__ P, const 
 }
 
 // element_sample with the element's receive terms given and the two samples read from the
-// staged window when it holds them.
+// staged window when it holds them.  The sample is formed for depths outside the aperture too
+// (and then weighted 0): the lanes of a warp are consecutive depths of one element, which
+// enter the aperture at different depths, and a branch on it would only serialise them.  The
+// window covers the delays of every depth of the tile, so those lanes read inside it as well.
 __device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict__ P, const PixelGeo &g, int e,
                                                        bool &act, const int16_t *win, int ws, float beta,
-                                                       float gamma) {
-    const float4 xe = __ldg(&P->elem[e]);
-    act = fabsf((xe.x - g.qx) * g.inv_a) <= 1.0f && fabsf((xe.y - g.qy) * g.inv_a) <= 1.0f;
-    if (!act) return 0.0f;
+                                                       float gamma, float ex, float ey) {
+    act = fabsf((ex - g.qx) * g.inv_a) <= 1.0f && fabsf((ey - g.qy) * g.inv_a) <= 1.0f;
     const float s = g.base + path_excess(g.r, beta, gamma) * P->fsc;
     int ks;
-    const float fl = floor_split(s, ks);   // (|s| is far below 2^22 inside the aperture)
+    const float fl = floor_split(s, ks);   // (|s| is far below 2^22 for the tile's depths)
     const float phi = s - fl;
     const long long k = (long long)g.kt + ks;
     const long long d = k - ws;
@@ -247,7 +248,7 @@ __device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict
         x0 = (k >= 0 && k < n_s) ? (float)__ldg(rec + k) : 0.0f;
         x1 = (k + 1 >= 0 && k + 1 < n_s) ? (float)__ldg(rec + k + 1) : 0.0f;
     }
-    return fmaf(phi, x1 - x0, x0);
+    return act ? fmaf(phi, x1 - x0, x0) : 0.0f;
 }
 
 // K steps of one MMA chain, issued by one thread (2 core matrices along K per step).
@@ -612,8 +613,16 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const int n_slots = min(box.hi - box.lo + 1, kWinSlots);
             const bool staged = a.plan->bulk_ok && (reinterpret_cast<uintptr_t>(a.ch) & 15) == 0 && lgt.plane == 0;
             int16_t *win = reinterpret_cast<int16_t *>(sm + S::H1);
+            // the slots' element positions, in the softmax exchange rows (free until the softmax)
+            static_assert(MODE != kInfer || (H > 1 && H * kTile >= kWinSlots), "element positions in the exchange rows");
+            float *win_x = &xrow[H > 1 ? 1 : 0][0][0], *win_y = &xrow[H > 1 ? 2 : 0][0][0];
             if (staged) {
-                if (t < n_slots) win_ws[t] = tile_window(a.plan, lgt, box.lo + t, i_a, i_b, win_bg[t][0], win_bg[t][1]);
+                if (t < n_slots) {
+                    win_ws[t] = tile_window(a.plan, lgt, box.lo + t, i_a, i_b, win_bg[t][0], win_bg[t][1]);
+                    const float4 xe = __ldg(&a.plan->elem[box.lo + t]);
+                    win_x[t] = xe.x;
+                    win_y[t] = xe.y;
+                }
                 __syncthreads();
                 const int n_s = a.plan->n_s;
                 const int16_t *rec_base = a.ch + (long long)lgt.tx * n_el * n_s;
@@ -651,7 +660,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                         const int jw = e - box.lo;
                         v[j] = (staged && jw < n_slots && win_ws[jw] != kNoWin)
                                    ? element_sample_staged(a.plan, g, e, act, win + jw * kWinW, win_ws[jw],
-                                                           win_bg[jw][0], win_bg[jw][1])
+                                                           win_bg[jw][0], win_bg[jw][1], win_x[jw], win_y[jw])
                                    : element_sample(a.plan, g, e, act);
                     } else {
                         v[j] = 0.0f;
