@@ -645,8 +645,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 cp_async_wait_all();
                 __syncthreads();
             }
+            // The row's 8-element chunks alternate between its H parts, so that each part gathers
+            // about the same share of the box's elements wherever the box lies on the array (the
+            // aperture of a line near the array's edge fills one end of the row); the mask bits of
+            // a part's output blocks that another part found are exchanged after the gather.
 #pragma unroll 1
-            for (int c = half * (16 / H); c < (half + 1) * (16 / H); ++c) {
+            for (int c = half; c < 16; c += H) {
                 if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
                     chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
                     continue;
@@ -703,8 +707,20 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                     chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
             }
         }
-        if constexpr (MODE == kInfer && H > 1) xrow[0][half][row] = nrm;
+        // (H == 2: mask word w of a row, needed by part w / 2, is sent by the other part through the
+        // softmax exchange rows, free until the softmax)
+        static_assert(MODE != kInfer || H <= 2, "the fused beamformer's mask exchange takes two parts");
+        uint32_t *mx = reinterpret_cast<uint32_t *>(&xrow[H > 1 ? 1 : 0][0][0]);
+        if constexpr (MODE == kInfer && H > 1) {
+            xrow[0][half][row] = nrm;
+            mx[(2 * (1 - half)) * kTile + row] = mk[2 * (1 - half)];
+            mx[(2 * (1 - half) + 1) * kTile + row] = mk[2 * (1 - half) + 1];
+        }
         if (!step_end()) break;
+        if constexpr (MODE == kInfer && H > 1) {
+            mk[2 * half] |= mx[(2 * half) * kTile + row];
+            mk[2 * half + 1] |= mx[(2 * half + 1) * kTile + row];
+        }
         if constexpr (MODE == kInfer) nrm = sqrtf(H > 1 ? xrow[0][0][row] + xrow[0][1][row] : nrm);
         const bool valid = row_ok && nrm > 0.0f;
 
