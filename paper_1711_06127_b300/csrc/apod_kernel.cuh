@@ -486,8 +486,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
     const uint32_t sb = tc::smem_u32(sm);
     const float *b1 = reinterpret_cast<const float *>(sm + S::BIAS), *b2 = b1 + 64, *b3 = b1 + 128;
     constexpr uint32_t kI64 = tc::idesc_bf16(128, 64, false, false), kI128 = tc::idesc_bf16(128, 128, false, false);
-    // this thread's column blocks of 32 of the 128 outputs: q in [q4, q4 + 4/H)
+    // this thread's column blocks of 32 of the 128 outputs in the softmax: q = half + H k, k < 4/H --
+    // interleaved, so that the parts of a row share its aperture's blocks evenly wherever the
+    // aperture lies (a block outside every pixel's aperture of a warp is skipped); the partial
+    // gradients are written out by the blocks q4 .. q4 + 4/H - 1
     const int q4 = half * (4 / H);
+    auto qb = [&](int k) { return half + H * k; };
 
     long long n_tiles;
     int nblk = 1, nd = 0;
@@ -707,19 +711,18 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                     chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
             }
         }
-        // (H == 2: mask word w of a row, needed by part w / 2, is sent by the other part through the
-        // softmax exchange rows, free until the softmax)
+        // (H == 2: mask word w of a row, needed by part w % 2, whose softmax blocks are w and w + 2, is
+        // sent by the other part through the softmax exchange rows xrow[1..2]: written after the
+        // barrier that ends the gather, since the gather reads the slots' element positions from
+        // those rows, and read after the next barrier; the softmax writes them only after the one
+        // after that)
         static_assert(MODE != kInfer || H <= 2, "the fused beamformer's mask exchange takes two parts");
         uint32_t *mx = reinterpret_cast<uint32_t *>(&xrow[H > 1 ? 1 : 0][0][0]);
-        if constexpr (MODE == kInfer && H > 1) {
-            xrow[0][half][row] = nrm;
-            mx[(2 * (1 - half)) * kTile + row] = mk[2 * (1 - half)];
-            mx[(2 * (1 - half) + 1) * kTile + row] = mk[2 * (1 - half) + 1];
-        }
+        if constexpr (MODE == kInfer && H > 1) xrow[0][half][row] = nrm;
         if (!step_end()) break;
         if constexpr (MODE == kInfer && H > 1) {
-            mk[2 * half] |= mx[(2 * half) * kTile + row];
-            mk[2 * half + 1] |= mx[(2 * half + 1) * kTile + row];
+            mx[(1 - half) * kTile + row] = mk[1 - half];
+            mx[(3 - half) * kTile + row] = mk[3 - half];
         }
         if constexpr (MODE == kInfer) nrm = sqrtf(H > 1 ? xrow[0][0][row] + xrow[0][1][row] : nrm);
         const bool valid = row_ok && nrm > 0.0f;
@@ -739,6 +742,10 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             bias_relu_rows<BW64>(v, b1 + col, scale, sm, S::H1, col / 8, row);
         }
         if (!step_end()) break;
+        if constexpr (MODE == kInfer && H > 1) {   // (the mask words sent above)
+            mk[half] |= mx[half * kTile + row];
+            mk[half + 2] |= mx[(half + 2) * kTile + row];
+        }
 
         // ---- Z2 = H1 W2^T
         if (MODE != kTrain && warp == 0 && lead()) {
@@ -769,18 +776,18 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         constexpr bool kPair = MODE == kTrain && 4 / H == 2;
         float vv[kPair ? 2 : 1][32];
         auto load_pair = [&]() {
-            if constexpr (kPair) tc::tmem_ld32x2(tm + lane + kT128 + 32 * q4, tm + lane + kT128 + 32 * (q4 + 1), vv[0], vv[1]);
+            if constexpr (kPair) tc::tmem_ld32x2(tm + lane + kT128 + 32 * qb(0), tm + lane + kT128 + 32 * qb(1), vv[0], vv[1]);
         };
         float zm4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
         // a 32-output block outside the aperture of all of the warp's 32 pixels (shallow depths)
         // has no weight anywhere: the passes skip it (its exponentials and gradients are 0)
         bool blk[4 / H];
 #pragma unroll
-        for (int k = 0; k < 4 / H; ++k) blk[k] = __any_sync(0xffffffffu, mk[q4 + k] != 0u);
+        for (int k = 0; k < 4 / H; ++k) blk[k] = __any_sync(0xffffffffu, mk[qb(k)] != 0u);
         load_pair();
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
-            const int q = q4 + k;
+            const int q = qb(k);
             if (!blk[k]) continue;
             float vl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
@@ -828,7 +835,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         u64 se2[2] = {0ull, 0ull}, sx2[2] = {0ull, 0ull};
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
-            const int q = q4 + k;
+            const int q = qb(k);
             if (!blk[k]) continue;
             float vl[32], xl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
@@ -893,7 +900,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             const float g = 2.0f * r, inv_se = se > 0.0f ? 1.0f / se : 0.0f, gs = g * inv_se;
 #pragma unroll
             for (int k = 0; k < 4 / H; ++k) {
-                const int q = q4 + k;
+                const int q = qb(k);
                 if (!blk[k]) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = make_uint4(0u, 0u, 0u, 0u);

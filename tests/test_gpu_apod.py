@@ -279,6 +279,20 @@ def test_fused_inference_matches_the_oracle():
     assert supra.device_status() == 0
 
 
+def test_fused_inference_is_deterministic():
+    # several 128-depth tiles per CTA (64 lines x 16 tiles over two CTAs per SM), and lines near the
+    # array's edges, whose aperture boxes sit at one end of a pixel row (the two warpgroups of a row
+    # then exchange mask bits): repeated calls give the same bits
+    s = small_linear(128, 64, 2048)
+    ch = phantom.random_channels(s, 95).cuda()
+    plan = supra.Plan(**s.params())
+    params = torch.as_tensor(_params(96, out_scale=2.0, bias_scale=0.1)).cuda()
+    outs = [plan.apod(ch, params) for _ in range(3)]
+    assert all(torch.equal(outs[0], o) for o in outs[1:])
+    assert torch.isfinite(outs[0]).all()
+    assert supra.device_status() == 0
+
+
 def test_zero_output_layer_is_rectangular_das_on_the_gpu():
     s = small_linear(40, 6, 500)
     p = s.params()
