@@ -5,7 +5,10 @@ on the device at most.
 
     python -m paper_1711_06127_b300.profile_cases CASE
 
-CASE: apod_train   gradient of 151552 feature rows (tcgen05 forward + backward)
+CASE: apod_train   gradient of 151552 feature rows (tcgen05 forward + backward), random rows
+      apod_train_frames the same on the feature rows of a phantom frame (every third row of the
+                   128-element / 256-line / 2048-sample frame: tiles of nearby depths of one line,
+                   whose apertures leave whole output blocks empty, as in training on frames)
       apod_minibatch eight training steps (gradient, reduction, Adam) of 65536-pixel
                    minibatches of 1.57 M feature rows
       apod_infer   fused gather + network beamformer, 128 el x 256 lines x 2048 samples
@@ -43,6 +46,21 @@ def main(case: str) -> int:
         tr = apod.Trainer(phantom.apod_init(2, out_scale=1.0, bias_scale=0.05))
         for _ in range(2):
             tr.compute_grad(data)
+    elif case == "apod_train_frames":
+        s = phantom.config2()
+        plan = supra.Plan(**dict(s.params(), grid=None))
+        P = plan.n_lines * plan.n_depth
+        feat = torch.empty((P, supra.APOD_INPUTS), dtype=torch.bfloat16, device=dev)
+        mask = torch.empty((P, 4), dtype=torch.int32, device=dev)
+        norm = torch.empty((P,), dtype=torch.float32, device=dev)
+        label = torch.empty((P,), dtype=torch.float32, device=dev)
+        ch, _ = phantom.apod_frame(s, 4000, device=dev)
+        plan.apod_features(ch, feat, mask, norm)
+        plan.beamform(ch, label.view(plan.line_shape))
+        data = apod.Dataset(feat, mask, norm, label)
+        tr = apod.Trainer(phantom.apod_init(2, out_scale=1.0, bias_scale=0.05))
+        for _ in range(2):
+            tr.compute_grad(data, 0, 3, 148 * 128 * 8)
     elif case == "apod_minibatch":
         n = 65536 * 24
         X, mask, norm, t = phantom.apod_random_batch(1, n)
