@@ -6,11 +6,14 @@
 //   xh = x / ||x||,  h1 = relu(W1 xh + b1),  h2 = relu(W2 h1 + b2),
 //   z = W3 h2 + b3,  w = softmax of z over the aperture,  y = sum_e w_e x_e.
 //
-// One CTA = 128 threads = one tile of 128 pixels; thread t owns pixel t, which
-// is also TMEM lane t of every M = 128 accumulator.  The three layers and, in
-// training, the two activation-gradient products and the three weight-gradient
-// products run as BF16 tcgen05 MMAs with FP32 accumulators in tensor memory;
-// ReLU, the masked softmax and its backward pass run per thread between them.
+// A CTA works on tiles of 128 pixels; pixel p of a tile is TMEM lane p of every
+// M = 128 accumulator, and its row is held by the threads p, p + 128, ... (one
+// part of its columns each; one warpgroup for the forward pass on stored rows,
+// two for training and the fused beamformer, training adding a warp that only
+// issues the products).  The three layers and, in training, the two
+// activation-gradient products and the three weight-gradient products run as
+// BF16 tcgen05 MMAs with FP32 accumulators in tensor memory; ReLU, the masked
+// softmax and its backward pass run per thread between them.
 // Weight gradients accumulate in tensor memory across all tiles of a CTA and
 // are written once, as per-CTA partials (deterministic reduction afterwards).
 //
