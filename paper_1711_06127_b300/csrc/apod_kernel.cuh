@@ -538,7 +538,6 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         return true;
     };
 
-
     int iter = 0;
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
         const int xo = (MODE == kTrain && (iter & 1)) ? S::X2 : S::X;   // this tile's X buffer
