@@ -9,6 +9,8 @@ CASE: apod_train   gradient of 151552 feature rows (tcgen05 forward + backward),
       apod_train_frames the same on the feature rows of a phantom frame (every third row of the
                    128-element / 256-line / 2048-sample frame: tiles of nearby depths of one line,
                    whose apertures leave whole output blocks empty, as in training on frames)
+      apod_step    eight training steps as training runs them (supra_apod_step: the gradient, then
+                   the reduction fused with Adam) of eight 128-pixel tile rounds each
       apod_minibatch eight training steps (gradient, reduction, Adam) of 65536-pixel
                    minibatches of 1.57 M feature rows
       apod_infer   fused gather + network beamformer, 128 el x 256 lines x 2048 samples
@@ -61,6 +63,19 @@ def main(case: str) -> int:
         tr = apod.Trainer(phantom.apod_init(2, out_scale=1.0, bias_scale=0.05))
         for _ in range(2):
             tr.compute_grad(data, 0, 3, 148 * 128 * 8)
+    elif case == "apod_step":
+        n = 148 * 128 * 8
+        X, mask, norm, t = phantom.apod_random_batch(1, 4 * n)
+        xh = np.divide(X, norm[:, None], out=np.zeros_like(X), where=norm[:, None] > 0)
+        words = np.stack([(mask[:, 32 * w:32 * (w + 1)].astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(1)
+                          for w in range(4)], 1).astype(np.uint32)
+        data = apod.Dataset(torch.as_tensor(xh).to(torch.bfloat16).to(dev),
+                            torch.as_tensor(words.view(np.int32)).to(dev),
+                            torch.as_tensor(norm.astype(np.float32)).to(dev),
+                            torch.as_tensor((t * norm).astype(np.float32)).to(dev))
+        tr = apod.Trainer(phantom.apod_init(2, out_scale=1.0, bias_scale=0.05))
+        for k in range(8):
+            tr.step(data, k % 4, 4, n=n)
     elif case == "apod_minibatch":
         n = 65536 * 24
         X, mask, norm, t = phantom.apod_random_batch(1, n)
