@@ -24,6 +24,9 @@
 // M = 128; rows 64..127 read the next buffer and are discarded.
 #pragma once
 #include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "common.cuh"
 #include "gather.cuh"
 #include "tc.cuh"
@@ -230,16 +233,18 @@ __device__ __forceinline__ int tile_window(const DevPlan *__restrict__ P, const 
 // (and then weighted 0): the lanes of a warp are consecutive depths of one element, which
 // enter the aperture at different depths, and a branch on it would only serialise them.  The
 // window covers the delays of every depth of the tile, so those lanes read inside it as well.
+// Y: the array has more than one row of elements (else the aperture's y test always passes).
+template <bool Y>
 __device__ __forceinline__ float element_sample_staged(const DevPlan *__restrict__ P, const PixelGeo &g, int e,
                                                        bool &act, const int16_t *win, int ws, float beta,
                                                        float gamma, float ex, float ey) {
-    act = fabsf((ex - g.qx) * g.inv_a) <= 1.0f && fabsf((ey - g.qy) * g.inv_a) <= 1.0f;
+    act = fabsf((ex - g.qx) * g.inv_a) <= 1.0f && (!Y || fabsf((ey - g.qy) * g.inv_a) <= 1.0f);
     const float s = g.base + path_excess(g.r, beta, gamma) * P->fsc;
     int ks;
     const float fl = floor_split(s, ks);   // (|s| is far below 2^22 for the tile's depths)
     const float phi = s - fl;
-    const long long k = (long long)g.kt + ks;
-    const long long d = k - ws;
+    const int k = g.kt + ks;               // (sample indices of a record: far below 2^31)
+    const int d = k - ws;
     float x0, x1;
     if (d >= 0 && d + 1 < kWinW) {   // int16 -> float exactly, without the conversion pipe
         const uint16_t *w16 = reinterpret_cast<const uint16_t *>(win) + d;
@@ -655,31 +660,39 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             // about the same share of the box's elements wherever the box lies on the array (the
             // aperture of a line near the array's edge fills one end of the row); the mask bits of
             // a part's output blocks that another part found are exchanged after the gather.
+            // (one instance per array kind: a single row of elements needs no y test)
+            auto gather = [&](auto y_rows) {
+                constexpr bool Y = decltype(y_rows)::value;
 #pragma unroll 1
-            for (int c = half; c < 16; c += H) {
-                if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
-                    chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
-                    continue;
-                }
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int e = 8 * c + j;
-                    bool act = false;
-                    if (row_ok && e < n_el && box.has(e)) {
-                        const int jw = e - box.lo;
-                        v[j] = (staged && jw < n_slots && win_ws[jw] != kNoWin)
-                                   ? element_sample_staged(a.plan, g, e, act, win + jw * kWinW, win_ws[jw],
-                                                           win_bg[jw][0], win_bg[jw][1], win_x[jw], win_y[jw])
-                                   : element_sample(a.plan, g, e, act);
-                    } else {
-                        v[j] = 0.0f;
+                for (int c = half; c < 16; c += H) {
+                    if (!box.any(8 * c, 8 * c + 7)) {   // CTA-uniform: the whole chunk is outside the box
+                        chunk(sm, S::X, c, row) = make_uint4(0u, 0u, 0u, 0u);
+                        continue;
                     }
-                    n2v[j & 1] = fmaf(v[j], v[j], n2v[j & 1]);
-                    if (act) mk[e >> 5] |= 1u << (e & 31);
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int e = 8 * c + j;
+                        bool act = false;
+                        if (row_ok && e < n_el && box.has(e)) {
+                            const int jw = e - box.lo;
+                            v[j] = (staged && jw < n_slots && win_ws[jw] != kNoWin)
+                                       ? element_sample_staged<Y>(a.plan, g, e, act, win + jw * kWinW, win_ws[jw],
+                                                                  win_bg[jw][0], win_bg[jw][1], win_x[jw], win_y[jw])
+                                       : element_sample(a.plan, g, e, act);
+                        } else {
+                            v[j] = 0.0f;
+                        }
+                        n2v[j & 1] = fmaf(v[j], v[j], n2v[j & 1]);
+                        if (act) mk[e >> 5] |= 1u << (e & 31);
+                    }
+                    chunk(sm, S::X, c, row) = pack8(v);
                 }
-                chunk(sm, S::X, c, row) = pack8(v);
-            }
+            };
+            if (a.plan->el_ny > 1 || a.plan->ymax > a.plan->ymin)
+                gather(std::true_type{});
+            else
+                gather(std::false_type{});
             nrm = n2v[0] + n2v[1];   // this half's share of ||x||^2 (square root below)
         } else if (MODE == kTrain) {
             if (rows_armed) {
