@@ -106,6 +106,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// mk[i] for a run-time i < 4 by selects (indexing the array at run time would put it in local memory)
+__device__ __forceinline__ uint32_t word_of(const uint32_t (&mk)[4], int i) {
+    return i == 0 ? mk[0] : i == 1 ? mk[1] : i == 2 ? mk[2] : mk[3];
+}
 __device__ __forceinline__ uint4 &chunk(unsigned char *sm, int buf, int j, int row) {
     return *reinterpret_cast<uint4 *>(sm + buf + j * 2048 + row * 16);
 }
@@ -670,6 +674,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                         continue;
                     }
                     float v[8];
+                    uint32_t cb = 0u;   // the chunk's aperture bits (bit j: element 8 c + j)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int e = 8 * c + j;
@@ -684,8 +689,11 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                             v[j] = 0.0f;
                         }
                         n2v[j & 1] = fmaf(v[j], v[j], n2v[j & 1]);
-                        if (act) mk[e >> 5] |= 1u << (e & 31);
+                        cb |= act ? 1u << j : 0u;
                     }
+                    // (into word c / 4 by selects: an index computed at run time would put mk in local memory)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) mk[w] |= (c >> 2) == w ? cb << (8 * (c & 3)) : 0u;
                     chunk(sm, S::X, c, row) = pack8(v);
                 }
             };
@@ -736,8 +744,8 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         if constexpr (MODE == kInfer && H > 1) xrow[0][half][row] = nrm;
         if (!step_end()) break;
         if constexpr (MODE == kInfer && H > 1) {
-            mx[(1 - half) * kTile + row] = mk[1 - half];
-            mx[(3 - half) * kTile + row] = mk[3 - half];
+            mx[(1 - half) * kTile + row] = word_of(mk, 1 - half);
+            mx[(3 - half) * kTile + row] = word_of(mk, 3 - half);
         }
         if constexpr (MODE == kInfer) nrm = sqrtf(H > 1 ? xrow[0][0][row] + xrow[0][1][row] : nrm);
         const bool valid = row_ok && nrm > 0.0f;
@@ -758,8 +766,11 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         }
         if (!step_end()) break;
         if constexpr (MODE == kInfer && H > 1) {   // (the mask words sent above)
-            mk[half] |= mx[half * kTile + row];
-            mk[half + 2] |= mx[(half + 2) * kTile + row];
+            const uint32_t m0 = mx[half * kTile + row], m2 = mx[(half + 2) * kTile + row];
+            mk[0] |= half == 0 ? m0 : 0u;
+            mk[1] |= half == 1 ? m0 : 0u;
+            mk[2] |= half == 0 ? m2 : 0u;
+            mk[3] |= half == 1 ? m2 : 0u;
         }
 
         // ---- Z2 = H1 W2^T
@@ -798,11 +809,12 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
         // has no weight anywhere: the passes skip it (its exponentials and gradients are 0)
         bool blk[4 / H];
 #pragma unroll
-        for (int k = 0; k < 4 / H; ++k) blk[k] = __any_sync(0xffffffffu, mk[qb(k)] != 0u);
+        for (int k = 0; k < 4 / H; ++k) blk[k] = __any_sync(0xffffffffu, word_of(mk, qb(k)) != 0u);
         load_pair();
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = qb(k);
+            const uint32_t mq = word_of(mk, q);
             if (!blk[k]) continue;
             float vl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
@@ -823,7 +835,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int j = 4 * j4 + u;
-                    const bool on = (mk[q] >> j) & 1u;
+                    const bool on = (mq >> j) & 1u;
                     if constexpr (kPair) {   // outputs outside the aperture as -inf: exponential 0 below
                         vv[k][j] = on ? zs[u] : -INFINITY;
                         zm4[u] = fmaxf(zm4[u], vv[k][j]);
@@ -851,6 +863,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
         for (int k = 0; k < 4 / H; ++k) {
             const int q = qb(k);
+            const uint32_t mq = word_of(mk, q);
             if (!blk[k]) continue;
             float vl[32], xl[32];
             if constexpr (!kPair) tc::tmem_ld32(tm + lane + kT128 + 32 * q, vl);
@@ -874,7 +887,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
             } else {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float ez = ((mk[q] >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
+                    const float ez = ((mq >> j) & 1u) ? __expf(v[j] + b3[32 * q + j] - zmax) : 0.0f;
                     se4[j & 3] += ez;
                     sx4[j & 3] = fmaf(ez, x[j], sx4[j & 3]);
                 }
@@ -916,6 +929,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
 #pragma unroll
             for (int k = 0; k < 4 / H; ++k) {
                 const int q = qb(k);
+                const uint32_t mq = word_of(mk, q);
                 if (!blk[k]) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) chunk(sm, S::DZ3, 4 * q + c, row) = make_uint4(0u, 0u, 0u, 0u);
@@ -942,7 +956,7 @@ __global__ void __launch_bounds__(apod_threads<MODE>(), MODE == kTrain ? 1 : 2) 
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float pe = ((mk[q] >> j) & 1u) ? __expf(vl[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
+                        const float pe = ((mq >> j) & 1u) ? __expf(vl[j] + b3[32 * q + j] - zmax) * inv_se : 0.0f;
                         dz[j] = pe * (x[j] - yh) * g;
                     }
                 }
