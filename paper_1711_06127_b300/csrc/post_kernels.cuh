@@ -106,10 +106,32 @@ __device__ __forceinline__ bool scan_coords(const DevPlan *P, float x, float y, 
            v <= (float)(P->n_depth - 1) + kInsideEps;
 }
 
+// The scan conversion's floors and byte conversions stay off the conversion pipe (the kernels
+// are bound by it otherwise): x + 1.5 * 2^23 rounded toward -inf is floor(x) + 1.5 * 2^23
+// exactly for |x| < 2^22, whose bits give the integer; a byte placed in the mantissa of 2^23
+// is that byte plus 2^23 exactly.
+constexpr float kScanMagic = 12582912.0f;   // 1.5 * 2^23
+__device__ __forceinline__ float scan_floor(float x, int &k) {
+    const float t = __fadd_rd(x, kScanMagic);
+    k = __float_as_int(t) - __float_as_int(kScanMagic);
+    return t - kScanMagic;
+}
+__device__ __forceinline__ float byte_f(uint32_t b) { return __uint_as_float(0x4B000000u | b) - 8388608.0f; }
+// floor(y) clamped to [0, 255] (y finite, within the interpolated bytes' range)
+__device__ __forceinline__ uint8_t floor_byte(float y) {
+    int k;
+    scan_floor(y, k);
+    return (uint8_t)min(max(k, 0), 255);
+}
+
+// u clamped to [0, n - 1] -> cell i0 <= max(n - 2, 0) and the fraction f = u - i0 (f = 1 at u = n - 1)
 __device__ __forceinline__ void lerp_axis(float u, int n, int &i0, float &f) {
     u = fminf(fmaxf(u, 0.0f), (float)(n - 1));
-    i0 = min((int)floorf(u), max(n - 2, 0));
-    f = u - (float)i0;
+    int k;
+    const float fl = scan_floor(u, k);
+    const int top = max(n - 2, 0);
+    i0 = min(k, top);
+    f = u - (k > top ? fl - 1.0f : fl);   // (k > top only at u = n - 1: i0 = k - 1)
 }
 
 // Scan conversion of one output tile per CTA: 2D tiles are 64 (x) x 32 (z) pixels,
@@ -136,19 +158,19 @@ __device__ __forceinline__ uint8_t lerp_lines(const DevPlan *P, const uint8_t *s
         lerp_axis(w, P->lines_y, iy, fy);
         const int dy = iy + 1 < P->lines_y ? sy : 0;
         const uint8_t *b = src + ix * sx + iy * sy + iv * sv;
-        const float c00 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
-        const float c01 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
-        const float c10 = fmaf(fv, (float)b[dy + dv] - (float)b[dy], (float)b[dy]);
-        const float c11 = fmaf(fv, (float)b[dy + dx + dv] - (float)b[dy + dx], (float)b[dy + dx]);
+        const float c00 = fmaf(fv, byte_f(b[dv]) - byte_f(b[0]), byte_f(b[0]));
+        const float c01 = fmaf(fv, byte_f(b[dx + dv]) - byte_f(b[dx]), byte_f(b[dx]));
+        const float c10 = fmaf(fv, byte_f(b[dy + dv]) - byte_f(b[dy]), byte_f(b[dy]));
+        const float c11 = fmaf(fv, byte_f(b[dy + dx + dv]) - byte_f(b[dy + dx]), byte_f(b[dy + dx]));
         const float c0 = fmaf(fx, c01 - c00, c00), c1 = fmaf(fx, c11 - c10, c10);
         val = fmaf(fy, c1 - c0, c0);
     } else {
         const uint8_t *b = src + ix * sx + iv * sv;
-        const float c0 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
-        const float c1 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
+        const float c0 = fmaf(fv, byte_f(b[dv]) - byte_f(b[0]), byte_f(b[0]));
+        const float c1 = fmaf(fv, byte_f(b[dx + dv]) - byte_f(b[dx]), byte_f(b[dx]));
         val = fmaf(fx, c1 - c0, c0);
     }
-    return (uint8_t)fminf(fmaxf(floorf(val + 0.5f), 0.0f), 255.0f);
+    return floor_byte(val + 0.5f);
 }
 
 __global__ void __launch_bounds__(256) scanconvert_kernel(const __grid_constant__ ScanLaunch L) {
@@ -339,8 +361,10 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
         for (int k = threadIdx.x; k < nf * nL * nC; k += blockDim.x) {
             const int f = k / (nL * nC), r = k - f * (nL * nC), l = r / nC, c = r - l * nC;
             const long long a = (((long long)(lo_l + l) * nd + lo_d) & ~15LL) + 16 * c;
+            static_assert(kScanGroup == 4, "frame pointer by selects");   // (a run-time index: local memory)
+            const uint8_t *src = f == 0 ? bm[0] : f == 1 ? bm[1] : f == 2 ? bm[2] : bm[3];
             if (a < frame_bytes)   // chunks past the frame's last byte are never read
-                *reinterpret_cast<uint4 *>(&stg[f][l][16 * c]) = __ldg(reinterpret_cast<const uint4 *>(bm[f] + a));
+                *reinterpret_cast<uint4 *>(&stg[f][l][16 * c]) = __ldg(reinterpret_cast<const uint4 *>(src + a));
         }
         __syncthreads();
 #pragma unroll
@@ -373,9 +397,9 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
                                     o0 + iv + dv < kLinStageRow && o1 + iv + dv < kLinStageRow)) {
                         const uint8_t *b0 = &stg[f][ix - lo_l][o0 + iv];
                         const uint8_t *b1 = &stg[f][ix1 - lo_l][o1 + iv];
-                        const float c0 = fmaf(fv, (float)b0[dv] - (float)b0[0], (float)b0[0]);
-                        const float c1 = fmaf(fv, (float)b1[dv] - (float)b1[0], (float)b1[0]);
-                        out = (uint8_t)fminf(fmaxf(floorf(fmaf(fx, c1 - c0, c0) + 0.5f), 0.0f), 255.0f);
+                        const float c0 = fmaf(fv, byte_f(b0[dv]) - byte_f(b0[0]), byte_f(b0[0]));
+                        const float c1 = fmaf(fv, byte_f(b1[dv]) - byte_f(b1[0]), byte_f(b1[0]));
+                        out = floor_byte(fmaf(fx, c1 - c0, c0) + 0.5f);
                     }
                     tile[f][zl][xl] = out;
                 }
@@ -407,9 +431,9 @@ __global__ void __launch_bounds__(256) scanconvert_linear_kernel(const __grid_co
                 uint8_t out = 0;
                 if (in && f < nf) {
                     const uint8_t *b = bm[f] + lo + iv;
-                    const float c0 = fmaf(fv, (float)b[dv] - (float)b[0], (float)b[0]);
-                    const float c1 = fmaf(fv, (float)b[dx + dv] - (float)b[dx], (float)b[dx]);
-                    out = (uint8_t)fminf(fmaxf(floorf(fmaf(fx, c1 - c0, c0) + 0.5f), 0.0f), 255.0f);
+                    const float c0 = fmaf(fv, byte_f(b[dv]) - byte_f(b[0]), byte_f(b[0]));
+                    const float c1 = fmaf(fv, byte_f(b[dx + dv]) - byte_f(b[dx]), byte_f(b[dx]));
+                    out = floor_byte(fmaf(fx, c1 - c0, c0) + 0.5f);
                 }
                 tile[f][zl][xl] = out;
             }
